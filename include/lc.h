@@ -1,0 +1,187 @@
+/*
+ * lc.h -- C ABI of the GB300 learned compressor for sorted integer keys
+ * (arXiv 2412.10770, "Learned Data Compression: Challenges and Opportunities
+ * for the Future").
+ *
+ * Problem contract (Def. 1, Sec. I): given sorted keys K[0..N), build a compact
+ * encoding K^c and a decoder with Dec(K^c)[i] = K[i] for every i; the
+ * compression ratio is r = size(K^c) / size(K).
+ *
+ * Model (Def. 2, Eq. (1), Sec. II-A): an eps-PLA f whose segments
+ * (s_j, alpha_j, beta_j) keep |K[i] - floor(f(i))| <= eps, stored with the
+ * residuals Delta[i] = K[i] - floor(f(i)) (Sec. I, Fig. 2).  This library's
+ * reading:
+ *   - segments are anchored (beta_j = K[s_j]) with an int64 Q32 slope M_j;
+ *     floor(f(i)) = K[s_j] + floor(M_j (i - s_j) / 2^32) in exact integer
+ *     arithmetic (128-bit product, arithmetic shift);
+ *   - they come from a greedy shrinking-cone fit inside fixed chunks of
+ *     2^chunk_log2 keys (the paper's O'Rourke fit, Sec. II-A, is replaced);
+ *     the slope is the floor midpoint of the final cone (0 for one key);
+ *   - residuals are zigzag-coded and bit-packed LSB-first at a width chosen per
+ *     segment, w_j <= ceil(log2(2 eps + 1)) (Sec. II-A); the anchor's residual
+ *     (always 0) is not stored;
+ *   - the byte layout "LCF1" is identical on the CPU and the GPU: a 64-byte
+ *     header, the chunk directory (key, segment and payload-word offsets), the
+ *     per-segment model (intercept, slope, bit offset, start, width) and the
+ *     payload words.  lc_serialize returns exactly these bytes.
+ *
+ * Conventions
+ *   - Every function returns an int status: LC_OK (0) or a negative LC_ERR_*.
+ *     No function throws, aborts, or prints.
+ *   - "_dev" pointers are device memory owned by the caller; they must stay
+ *     valid until the work queued on `stream` has finished.  "host" pointers
+ *     are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are asynchronous on it unless marked "synchronous".
+ *   - Keys are unsigned integers of key_bytes = 4 or 8 bytes, little-endian.
+ *   - An lc_column owns its device memory; free it with lc_free.  A column may
+ *     be read (decode, access, lower_bound) from several streams at once.
+ *   - Device-side errors (an index >= N in lc_access) are recorded in the
+ *     column's status word and reported by lc_status.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LC_OK = 0,
+    LC_ERR_INVALID_ARG = -1,  /* null pointer, key_bytes not 4/8, eps > 2^30, chunk_log2 not in [8,16] */
+    LC_ERR_UNSORTED = -2,     /* keys are not non-decreasing */
+    LC_ERR_OUT_OF_RANGE = -3, /* index >= N, or begin + count > N */
+    LC_ERR_NOMEM = -4,        /* device or host allocation failed */
+    LC_ERR_CORRUPT = -5,      /* lc_deserialize: bytes are not a valid LCF1 blob */
+    LC_ERR_CUDA = -6,         /* a CUDA runtime call failed */
+    LC_ERR_TIMEOUT = -7,      /* a bounded device or host wait gave up */
+    LC_ERR_BUSY = -8,         /* serving: no slot or HBM budget free right now */
+    LC_ERR_UNSUPPORTED = -10, /* operation not defined for this column (lower_bound on a list column) */
+    LC_ERR_INTERNAL = -9
+};
+
+typedef struct lc_column lc_column;
+
+/* Fit parameters.  eps: the error bound of Def. 2, 0 <= eps <= 2^30.
+ * chunk_log2: log2 of the chunk length in keys, 8..16 (16 by default). */
+typedef struct {
+    uint64_t eps;
+    uint32_t chunk_log2;
+} lc_params;
+
+/* Header facts of a column (synchronous, host-side copy). */
+typedef struct {
+    uint64_t n;          /* keys */
+    uint64_t chunks;     /* C */
+    uint64_t segments;   /* L, the number of eps-PLA segments */
+    uint64_t words;      /* W, 64-bit payload words */
+    uint64_t lists;      /* lists in list mode, 0 for one column */
+    uint64_t bytes;      /* size(K^c) in bytes (Def. 1) */
+    uint64_t eps;        /* eps (0 in list mode) */
+    uint32_t key_bytes;  /* 4 or 8 */
+    uint32_t chunk_log2; /* 0 in list mode */
+} lc_info_t;
+
+/* ------------------------------------------------------------ compression */
+
+/* K^c of one sorted column (Def. 1 encoding stage; Def. 2; Fig. 2 encoding).
+ * keys_dev: n keys of key_bytes bytes, non-decreasing, device memory, not
+ * modified.  params may be NULL (eps = 0, chunk_log2 = 16).  On success *out
+ * is a new column.  Synchronous with respect to `stream`: it returns once the
+ * column is complete (the totals of segments and payload words are read back
+ * to size the allocation).  LC_ERR_UNSORTED if a key is smaller than its
+ * predecessor. */
+int lc_compress(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params,
+                void* stream, lc_column** out);
+
+/* K^c of many sorted lists stored back to back (inverted-index posting lists,
+ * Sec. III-A).  ids_dev: all keys, device memory.  list_begin: nlists+1
+ * non-decreasing offsets (host memory), list l is ids[list_begin[l],
+ * list_begin[l+1]), each list non-decreasing on its own.  eps and chunk_log2:
+ * one entry per list (host memory), or NULL for 0 and 16.  Every list is
+ * compressed as its own column (chunks restart at each list), all lists in
+ * one launch of each kernel.  Synchronous like lc_compress. */
+int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists,
+                      int key_bytes, const uint64_t* eps, const uint8_t* chunk_log2,
+                      void* stream, lc_column** out);
+
+/* ------------------------------------------------------------ decoding */
+
+/* Dec(K^c)[begin .. begin+count) (Fig. 2 decoding stage:
+ * K[i] = floor(f_j(i)) + Delta[i]) into out_dev (count keys of key_bytes
+ * bytes, device memory).  The full column is (0, N); in list mode list l is
+ * (list_begin[l], list_begin[l+1] - list_begin[l]).  Asynchronous.
+ * LC_ERR_OUT_OF_RANGE if begin + count > N. */
+int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream);
+
+/* Several ranges in one launch: range r is keys [begin[r], begin[r] +
+ * count[r]) written to out_dev at out_off[r] keys.  begin_dev, count_dev and
+ * out_off_dev are device arrays of m uint64 values (validated on the device;
+ * a range past N is recorded in the status word and skipped).  Asynchronous. */
+int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
+                     const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream);
+
+/* Every key of every list (list mode) or of the column.  Same as
+ * lc_decode(col, 0, N, ...). */
+int lc_decode_batch(const lc_column* col, void* out_dev, void* stream);
+
+/* Rank access (Sec. III-C, the quantile query f(i) + Delta[i]): out[q] =
+ * K[idx[q]] for q < m.  idx_dev: m uint64 indices (device).  out_dev: m keys
+ * of key_bytes bytes (device).  An index >= N yields 0 and sets
+ * LC_ERR_OUT_OF_RANGE in the status word.  Asynchronous. */
+int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* out_dev,
+              void* stream);
+
+/* Value lower_bound through the segment directory (Sec. III-A segment
+ * pruning, Table 2 binary search over segments): out[q] = first i with
+ * K[i] >= v[q], or N when every key is smaller.  v_dev: m values of key_bytes
+ * bytes (device).  out_dev: m uint64 (device).  Single columns only
+ * (LC_ERR_UNSUPPORTED in list mode).  Asynchronous. */
+int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t* out_dev,
+                   void* stream);
+
+/* Scalar conveniences (synchronous, legacy default stream). */
+int lc_access1(const lc_column* col, uint64_t i, uint64_t* key);
+int lc_lower_bound1(const lc_column* col, uint64_t v, uint64_t* pos);
+
+/* ------------------------------------------------------------ size, bytes, status */
+
+/* r = size(K^c) / size(K) with size(K) = N * key_bytes (Def. 1).  Returns a
+ * negative value for a NULL column and 0 for N = 0.  Synchronous, host only. */
+double lc_ratio(const lc_column* col);
+
+/* size(K^c) in bytes.  Synchronous, host only. */
+int lc_size(const lc_column* col, uint64_t* bytes);
+
+int lc_info(const lc_column* col, lc_info_t* info);
+
+/* Copy the exact K^c bytes (the LCF1 blob) into host memory.  cap: capacity
+ * of `host`; *len receives the blob length (also when cap is too small, in
+ * which case LC_ERR_INVALID_ARG is returned).  Synchronous. */
+int lc_serialize(const lc_column* col, void* host, uint64_t cap, uint64_t* len);
+
+/* Validate an LCF1 blob held in host memory and upload it as a new column.
+ * LC_ERR_CORRUPT if any structural fact of the format fails.  Synchronous. */
+int lc_deserialize(const void* host, uint64_t len, void* stream, lc_column** out);
+
+/* Wait for `stream`, then return and clear the column's device-side status
+ * (LC_OK or the first LC_ERR_* recorded by a kernel).  Synchronous. */
+int lc_status(const lc_column* col, void* stream);
+
+void lc_free(lc_column* col);
+
+const char* lc_strerror(int status);
+
+/* Version of the library (major * 10000 + minor * 100 + patch). */
+int lc_version(void);
+
+/* Diagnostics: kernels this process has launched through the library so far. */
+uint64_t lc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LC_H */

@@ -1,0 +1,502 @@
+// lc_api.cu -- the C ABI declared in include/lc.h: argument checks, column
+// ownership, the LCF1 header and directories, and host-side validation of
+// serialized blobs.  Every compute step runs in the kernels of lc_compress.cu
+// and lc_query.cu.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lc_internal.h"
+
+namespace lcx {
+
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return LC_OK;
+    if (e == cudaErrorMemoryAllocation) return LC_ERR_NOMEM;
+    return LC_ERR_CUDA;
+}
+
+static uint64_t pad16(uint64_t x) { return (x + 15) & ~(uint64_t)15; }
+
+Layout make_layout(int kb, uint64_t C, uint64_t L, uint64_t W, uint64_t NL, bool list_mode) {
+    Layout y;
+    uint64_t off = 64;
+    y.lkb = y.lcb = y.leps = y.llog = 0;
+    if (list_mode) {
+        y.lkb = off; off += pad16(8 * (NL + 1));
+        y.lcb = off; off += pad16(8 * (NL + 1));
+        y.leps = off; off += pad16(8 * NL);
+        y.llog = off; off += pad16(NL);
+    }
+    y.ckb = off; off += pad16(8 * (C + 1));
+    y.csb = off; off += pad16(8 * (C + 1));
+    y.cwb = off; off += pad16(8 * (C + 1));
+    y.icpt = off; off += pad16((uint64_t)kb * L);
+    y.slope = off; off += pad16(8 * L);
+    y.bitoff = off; off += pad16(4 * L);
+    y.start = off; off += pad16(2 * L);
+    y.width = off; off += pad16(L);
+    y.payload = off; off += 8 * W;
+    y.total = off;
+    return y;
+}
+
+static void put(uint8_t* p, uint64_t v, int bytes) {
+    for (int b = 0; b < bytes; ++b) p[b] = (uint8_t)(v >> (8 * b));
+}
+static uint64_t get(const uint8_t* p, int bytes) {
+    uint64_t v = 0;
+    for (int b = 0; b < bytes; ++b) v |= (uint64_t)p[b] << (8 * b);
+    return v;
+}
+
+// Header, list directory and chunk_key_begin: everything in front of
+// chunk_seg_begin, padding included.
+static std::vector<uint8_t> build_prefix(const lc_column* col, const uint64_t* list_begin, const uint64_t* list_chunk_begin,
+                                         const uint64_t* list_eps, const uint8_t* list_log2) {
+    const Layout& y = col->lay;
+    std::vector<uint8_t> b(y.csb, 0);
+    memcpy(b.data(), "LCF1", 4);
+    put(&b[4], 1, 2);
+    put(&b[6], col->list_mode ? 1 : 0, 2);
+    put(&b[8], col->key_bytes, 4);
+    put(&b[12], col->chunk_log2, 4);
+    put(&b[16], col->N, 8);
+    put(&b[24], col->eps, 8);
+    put(&b[32], col->C, 8);
+    put(&b[40], col->L, 8);
+    put(&b[48], col->W, 8);
+    put(&b[56], col->NL, 8);
+    if (col->list_mode) {
+        for (uint64_t l = 0; l <= col->NL; ++l) {
+            put(&b[y.lkb + 8 * l], list_begin[l], 8);
+            put(&b[y.lcb + 8 * l], list_chunk_begin[l], 8);
+        }
+        for (uint64_t l = 0; l < col->NL; ++l) {
+            put(&b[y.leps + 8 * l], list_eps[l], 8);
+            b[y.llog + l] = list_log2[l];
+        }
+    }
+    for (uint64_t c = 0; c <= col->C; ++c) put(&b[y.ckb + 8 * c], col->h_ckb[c], 8);
+    return b;
+}
+
+static lc_column* new_column() {
+    lc_column* c = new (std::nothrow) lc_column;
+    if (!c) return nullptr;
+    memset((void*)c, 0, sizeof(*c));
+    return c;
+}
+
+static unsigned bit_length(uint64_t x) {
+    unsigned n = 0;
+    while (x) { ++n; x >>= 1; }
+    return n;
+}
+
+// Payload words if every residual of a chunk of n keys took the paper's
+// ceil(log2(2 eps + 1)) bits (the largest any segment width can be).
+static uint64_t bound_words(uint64_t n, uint64_t eps) {
+    const uint64_t bits = (uint64_t)bit_length(2 * eps) * (n ? n - 1 : 0);
+    const uint64_t w = (bits + 63) / 64;
+    return w + (w & 1);
+}
+
+// Builds the empty-N or full column from a finished device blob.
+static int finish_column(lc_column* col, cudaStream_t st, const uint64_t* lb, const uint64_t* lcb, const uint64_t* le,
+                         const uint8_t* lg) {
+    std::vector<uint8_t> prefix = build_prefix(col, lb, lcb, le, lg);
+    int rc = finish_blob(col, prefix.data(), prefix.size(), st);
+    if (rc) return rc;
+    return build_derived(col, st);
+}
+
+static int alloc_empty_blob(lc_column* col, cudaStream_t st) {
+    col->lay = make_layout((int)col->key_bytes, col->C, 0, 0, col->NL, col->list_mode != 0);
+    col->blob_cap = col->lay.total;
+    if (cudaMallocAsync((void**)&col->blob, col->lay.total, st) != cudaSuccess) {
+        col->blob = nullptr;
+        return LC_ERR_NOMEM;
+    }
+    return cuda_status(cudaMemsetAsync(col->blob, 0, col->lay.total, st));
+}
+
+}  // namespace lcx
+
+using namespace lcx;
+
+extern "C" {
+
+int lc_version(void) { return 10000; }
+
+uint64_t lc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* lc_strerror(int s) {
+    switch (s) {
+        case LC_OK: return "ok";
+        case LC_ERR_INVALID_ARG: return "invalid argument";
+        case LC_ERR_UNSORTED: return "keys are not sorted";
+        case LC_ERR_OUT_OF_RANGE: return "index out of range";
+        case LC_ERR_NOMEM: return "out of memory";
+        case LC_ERR_CORRUPT: return "corrupt blob";
+        case LC_ERR_CUDA: return "CUDA error";
+        case LC_ERR_TIMEOUT: return "timed out";
+        case LC_ERR_BUSY: return "busy";
+        case LC_ERR_UNSUPPORTED: return "unsupported for this column";
+        case LC_ERR_INTERNAL: return "internal error";
+        default: return "unknown status";
+    }
+}
+
+void lc_free(lc_column* col) {
+    if (!col) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != col->device) cudaSetDevice(col->device);
+    cudaDeviceSynchronize();
+    if (col->blob) cudaFree(col->blob);
+    if (col->chunk_tile_begin) cudaFree(col->chunk_tile_begin);
+    if (cur != col->device) cudaSetDevice(cur);
+    delete[] col->h_ckb;
+    delete[] col->h_ctb;
+    delete col;
+}
+
+int lc_compress(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
+                lc_column** out) {
+    if (!out || (n && !keys_dev)) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (key_bytes != 4 && key_bytes != 8) return LC_ERR_INVALID_ARG;
+    const uint64_t eps = params ? params->eps : 0;
+    const uint32_t log2 = params ? params->chunk_log2 : 16;
+    if (eps > (1ull << 30) || log2 < 8 || log2 > 16) return LC_ERR_INVALID_ARG;
+    if (n > (1ull << 40)) return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    lc_column* col = new_column();
+    if (!col) return LC_ERR_NOMEM;
+    cudaGetDevice(&col->device);
+    col->key_bytes = (uint32_t)key_bytes;
+    col->chunk_log2 = log2;
+    col->list_mode = 0;
+    col->N = n;
+    col->eps = eps;
+    const uint64_t cs = 1ull << log2;
+    col->C = (n + cs - 1) / cs;
+    col->NL = 0;
+    col->h_ckb = new (std::nothrow) uint64_t[col->C + 1];
+    if (!col->h_ckb) { lc_free(col); return LC_ERR_NOMEM; }
+    for (uint64_t c = 0; c <= col->C; ++c) col->h_ckb[c] = std::min(n, c * cs);
+    int rc;
+    if (n == 0) {
+        rc = alloc_empty_blob(col, st);
+    } else {
+        std::vector<ChunkDesc> ch(col->C);
+        uint64_t bound = 0;
+        for (uint64_t c = 0; c < col->C; ++c) {
+            ch[c].key_begin = c * cs;
+            ch[c].bitword_begin = c * (cs / 32);
+            ch[c].n = (uint32_t)(col->h_ckb[c + 1] - col->h_ckb[c]);
+            ch[c].eps = (uint32_t)eps;
+            ch[c].check_prev = c > 0;
+            ch[c].pad = 0;
+            bound += bound_words(ch[c].n, eps);
+        }
+        rc = compress_impl(keys_dev, key_bytes, ch.data(), col->C, col->C * (cs / 32), bound, st, col);
+    }
+    if (!rc) rc = finish_column(col, st, nullptr, nullptr, nullptr, nullptr);
+    if (rc) { lc_free(col); return rc; }
+    *out = col;
+    return LC_OK;
+}
+
+int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists, int key_bytes,
+                      const uint64_t* eps, const uint8_t* chunk_log2, void* stream, lc_column** out) {
+    if (!out || !list_begin) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (key_bytes != 4 && key_bytes != 8) return LC_ERR_INVALID_ARG;
+    if (list_begin[0] != 0) return LC_ERR_INVALID_ARG;
+    for (uint64_t l = 0; l < nlists; ++l) {
+        if (list_begin[l + 1] < list_begin[l]) return LC_ERR_INVALID_ARG;
+        if (eps && eps[l] > (1ull << 30)) return LC_ERR_INVALID_ARG;
+        if (chunk_log2 && (chunk_log2[l] < 8 || chunk_log2[l] > 16)) return LC_ERR_INVALID_ARG;
+    }
+    const uint64_t n = list_begin[nlists];
+    if (n && !ids_dev) return LC_ERR_INVALID_ARG;
+    if (n > (1ull << 40)) return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    lc_column* col = new_column();
+    if (!col) return LC_ERR_NOMEM;
+    cudaGetDevice(&col->device);
+    col->key_bytes = (uint32_t)key_bytes;
+    col->chunk_log2 = 0;
+    col->list_mode = 1;
+    col->N = n;
+    col->eps = 0;
+    col->NL = nlists;
+    std::vector<uint64_t> le(nlists), lcb(nlists + 1, 0);
+    std::vector<uint8_t> lg(nlists);
+    uint64_t C = 0;
+    for (uint64_t l = 0; l < nlists; ++l) {
+        le[l] = eps ? eps[l] : 0;
+        lg[l] = chunk_log2 ? chunk_log2[l] : 16;
+        const uint64_t cs = 1ull << lg[l];
+        lcb[l] = C;
+        C += (list_begin[l + 1] - list_begin[l] + cs - 1) / cs;
+    }
+    lcb[nlists] = C;
+    col->C = C;
+    col->h_ckb = new (std::nothrow) uint64_t[C + 1];
+    if (!col->h_ckb) { lc_free(col); return LC_ERR_NOMEM; }
+    std::vector<ChunkDesc> ch(C);
+    uint64_t bitwords = 0, bound = 0, c = 0;
+    for (uint64_t l = 0; l < nlists; ++l) {
+        const uint64_t cs = 1ull << lg[l];
+        for (uint64_t b = list_begin[l]; b < list_begin[l + 1]; b += cs, ++c) {
+            const uint64_t e = std::min(b + cs, list_begin[l + 1]);
+            col->h_ckb[c] = b;
+            ch[c].key_begin = b;
+            ch[c].bitword_begin = bitwords;
+            ch[c].n = (uint32_t)(e - b);
+            ch[c].eps = (uint32_t)le[l];
+            ch[c].check_prev = b > list_begin[l];
+            ch[c].pad = 0;
+            bitwords += (e - b + 31) / 32;
+            bound += bound_words(e - b, le[l]);
+        }
+    }
+    col->h_ckb[C] = n;
+    int rc = C == 0 ? alloc_empty_blob(col, st)
+                    : compress_impl(ids_dev, key_bytes, ch.data(), C, bitwords, bound, st, col);
+    if (!rc) rc = finish_column(col, st, list_begin, lcb.data(), le.data(), lg.data());
+    if (rc) { lc_free(col); return rc; }
+    *out = col;
+    return LC_OK;
+}
+
+int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream) {
+    if (!col || (count && !out_dev)) return LC_ERR_INVALID_ARG;
+    if (begin > col->N || count > col->N - begin) return LC_ERR_OUT_OF_RANGE;
+    return decode_range(col, begin, count, out_dev, (cudaStream_t)stream);
+}
+
+int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
+                     const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream) {
+    if (!col || (m && (!begin_dev || !count_dev || !out_off_dev || !out_dev))) return LC_ERR_INVALID_ARG;
+    if (col->N == 0) return LC_OK;
+    return decode_ranges(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
+}
+
+int lc_decode_batch(const lc_column* col, void* out_dev, void* stream) {
+    if (!col) return LC_ERR_INVALID_ARG;
+    return lc_decode(col, 0, col->N, out_dev, stream);
+}
+
+int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* out_dev, void* stream) {
+    if (!col || (m && (!idx_dev || !out_dev))) return LC_ERR_INVALID_ARG;
+    if (col->N == 0) {
+        if (m) {
+            cudaMemsetAsync(out_dev, 0, m * col->key_bytes, (cudaStream_t)stream);
+            uint32_t bit = kStOutOfRange;
+            cudaMemcpyAsync(col->status, &bit, 4, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+            cudaStreamSynchronize((cudaStream_t)stream);
+        }
+        return LC_OK;
+    }
+    return access(col, idx_dev, m, out_dev, (cudaStream_t)stream);
+}
+
+int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t* out_dev, void* stream) {
+    if (!col || (m && (!v_dev || !out_dev))) return LC_ERR_INVALID_ARG;
+    if (col->list_mode) return LC_ERR_UNSUPPORTED;
+    return lower_bound(col, v_dev, m, out_dev, (cudaStream_t)stream);
+}
+
+int lc_access1(const lc_column* col, uint64_t i, uint64_t* key) {
+    if (!col || !key) return LC_ERR_INVALID_ARG;
+    if (i >= col->N) return LC_ERR_OUT_OF_RANGE;
+    uint64_t* buf = nullptr;
+    if (cudaMalloc((void**)&buf, 16) != cudaSuccess) return LC_ERR_NOMEM;
+    int rc = cuda_status(cudaMemcpy(buf, &i, 8, cudaMemcpyHostToDevice));
+    if (!rc) rc = access(col, buf, 1, buf + 1, nullptr);
+    uint64_t v = 0;
+    if (!rc) rc = cuda_status(cudaMemcpy(&v, buf + 1, 8, cudaMemcpyDeviceToHost));
+    cudaFree(buf);
+    if (!rc) *key = col->key_bytes == 4 ? (uint32_t)v : v;
+    return rc;
+}
+
+int lc_lower_bound1(const lc_column* col, uint64_t x, uint64_t* pos) {
+    if (!col || !pos) return LC_ERR_INVALID_ARG;
+    if (col->list_mode) return LC_ERR_UNSUPPORTED;
+    if (col->key_bytes == 4 && x > 0xFFFFFFFFull) {
+        *pos = col->N;
+        return LC_OK;
+    }
+    uint64_t* buf = nullptr;
+    if (cudaMalloc((void**)&buf, 16) != cudaSuccess) return LC_ERR_NOMEM;
+    int rc = cuda_status(cudaMemcpy(buf, &x, col->key_bytes, cudaMemcpyHostToDevice));
+    if (!rc) rc = lower_bound(col, buf, 1, buf + 1, nullptr);
+    if (!rc) rc = cuda_status(cudaMemcpy(pos, buf + 1, 8, cudaMemcpyDeviceToHost));
+    cudaFree(buf);
+    return rc;
+}
+
+double lc_ratio(const lc_column* col) {
+    if (!col) return -1.0;
+    if (col->N == 0) return 0.0;
+    return (double)col->lay.total / ((double)col->N * (double)col->key_bytes);
+}
+
+int lc_size(const lc_column* col, uint64_t* bytes) {
+    if (!col || !bytes) return LC_ERR_INVALID_ARG;
+    *bytes = col->lay.total;
+    return LC_OK;
+}
+
+int lc_info(const lc_column* col, lc_info_t* info) {
+    if (!col || !info) return LC_ERR_INVALID_ARG;
+    info->n = col->N;
+    info->chunks = col->C;
+    info->segments = col->L;
+    info->words = col->W;
+    info->lists = col->NL;
+    info->bytes = col->lay.total;
+    info->eps = col->eps;
+    info->key_bytes = col->key_bytes;
+    info->chunk_log2 = col->chunk_log2;
+    return LC_OK;
+}
+
+int lc_serialize(const lc_column* col, void* host, uint64_t cap, uint64_t* len) {
+    if (!col || !len) return LC_ERR_INVALID_ARG;
+    *len = col->lay.total;
+    if (!host || cap < col->lay.total) return LC_ERR_INVALID_ARG;
+    return cuda_status(cudaMemcpy(host, col->blob, col->lay.total, cudaMemcpyDeviceToHost));
+}
+
+// Structural validation of an LCF1 blob on the host: every fact of the format
+// is checked before anything is uploaded.
+static int validate_blob(const uint8_t* b, uint64_t len, lc_column* col) {
+    if (len < 64 || memcmp(b, "LCF1", 4) != 0 || get(b + 4, 2) != 1) return LC_ERR_CORRUPT;
+    const uint64_t flags = get(b + 6, 2);
+    if (flags > 1) return LC_ERR_CORRUPT;
+    const bool lm = flags == 1;
+    const uint64_t kb = get(b + 8, 4), log2 = get(b + 12, 4), N = get(b + 16, 8), eps = get(b + 24, 8);
+    const uint64_t C = get(b + 32, 8), L = get(b + 40, 8), W = get(b + 48, 8), NL = get(b + 56, 8);
+    if (kb != 4 && kb != 8) return LC_ERR_CORRUPT;
+    const uint64_t lim = 1ull << 40;
+    if (N > lim || C > lim || L > lim || W > lim || NL > lim) return LC_ERR_CORRUPT;
+    if (lm ? (log2 != 0 || eps != 0) : (log2 < 8 || log2 > 16 || eps > (1ull << 30) || NL != 0)) return LC_ERR_CORRUPT;
+    const Layout y = make_layout((int)kb, C, L, W, NL, lm);
+    if (y.total != len) return LC_ERR_CORRUPT;
+    // padding bytes between arrays are zero
+    struct Ar { uint64_t off, bytes; };
+    std::vector<Ar> arrs;
+    if (lm) arrs.insert(arrs.end(), {{y.lkb, 8 * (NL + 1)}, {y.lcb, 8 * (NL + 1)}, {y.leps, 8 * NL}, {y.llog, NL}});
+    arrs.insert(arrs.end(), {{y.ckb, 8 * (C + 1)}, {y.csb, 8 * (C + 1)}, {y.cwb, 8 * (C + 1)}, {y.icpt, kb * L},
+                             {y.slope, 8 * L}, {y.bitoff, 4 * L}, {y.start, 2 * L}, {y.width, L}});
+    for (const Ar& a : arrs)
+        for (uint64_t i = a.off + a.bytes; i < pad16(a.off + a.bytes); ++i)
+            if (b[i]) return LC_ERR_CORRUPT;
+    auto U = [&](uint64_t off, uint64_t i) { return get(b + off + 8 * i, 8); };
+    if (U(y.ckb, 0) || U(y.csb, 0) || U(y.cwb, 0)) return LC_ERR_CORRUPT;
+    if (U(y.ckb, C) != N || U(y.csb, C) != L || U(y.cwb, C) != W) return LC_ERR_CORRUPT;
+    for (uint64_t c = 0; c < C; ++c) {
+        const uint64_t k0 = U(y.ckb, c), k1 = U(y.ckb, c + 1), s0 = U(y.csb, c), s1 = U(y.csb, c + 1);
+        const uint64_t w0 = U(y.cwb, c), w1 = U(y.cwb, c + 1);
+        if (k1 <= k0 || k1 - k0 > kMaxChunk || s1 <= s0 || s1 > L || w1 < w0 || ((w1 - w0) & 1)) return LC_ERR_CORRUPT;
+        const uint64_t nc = k1 - k0;
+        uint64_t bits = 0;
+        for (uint64_t j = s0; j < s1; ++j) {
+            const uint64_t st = get(b + y.start + 2 * j, 2);
+            const uint64_t en = j + 1 < s1 ? get(b + y.start + 2 * (j + 1), 2) : nc;
+            if ((j == s0 && st != 0) || en <= st || en > nc) return LC_ERR_CORRUPT;
+            const uint64_t w = b[y.width + j];
+            if (w > 32 || get(b + y.bitoff + 4 * j, 4) != bits) return LC_ERR_CORRUPT;
+            bits += w * (en - st - 1);
+        }
+        uint64_t words = (bits + 63) / 64;
+        words += words & 1;
+        if (w1 - w0 != words) return LC_ERR_CORRUPT;
+        for (uint64_t p = bits; p < 64 * words; ++p) {  // unused payload bits are zero
+            const uint64_t gp = 64 * w0 + p;
+            if ((b[y.payload + (gp >> 3)] >> (gp & 7)) & 1) return LC_ERR_CORRUPT;
+        }
+    }
+    if (!lm) {
+        const uint64_t cs = 1ull << log2;
+        if (C != (N + cs - 1) / cs) return LC_ERR_CORRUPT;
+        for (uint64_t c = 0; c < C; ++c)
+            if (U(y.ckb, c) != c * cs) return LC_ERR_CORRUPT;
+    } else {
+        if (U(y.lkb, 0) || U(y.lcb, 0) || U(y.lkb, NL) != N || U(y.lcb, NL) != C) return LC_ERR_CORRUPT;
+        for (uint64_t l = 0; l < NL; ++l) {
+            const uint64_t a = U(y.lkb, l), e = U(y.lkb, l + 1), ca = U(y.lcb, l), cb = U(y.lcb, l + 1);
+            const uint64_t lg = b[y.llog + l];
+            if (e < a || cb < ca || lg < 8 || lg > 16 || U(y.leps, l) > (1ull << 30)) return LC_ERR_CORRUPT;
+            const uint64_t cs = 1ull << lg;
+            if (cb - ca != (e - a + cs - 1) / cs) return LC_ERR_CORRUPT;
+            for (uint64_t c = ca; c < cb; ++c)
+                if (U(y.ckb, c) != a + (c - ca) * cs) return LC_ERR_CORRUPT;
+        }
+    }
+    col->key_bytes = (uint32_t)kb;
+    col->chunk_log2 = (uint32_t)log2;
+    col->list_mode = lm;
+    col->N = N;
+    col->eps = eps;
+    col->C = C;
+    col->L = L;
+    col->W = W;
+    col->NL = NL;
+    col->lay = y;
+    col->h_ckb = new (std::nothrow) uint64_t[C + 1];
+    if (!col->h_ckb) return LC_ERR_NOMEM;
+    for (uint64_t c = 0; c <= C; ++c) col->h_ckb[c] = U(y.ckb, c);
+    return LC_OK;
+}
+
+int lc_deserialize(const void* host, uint64_t len, void* stream, lc_column** out) {
+    if (!host || !out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    lc_column* col = new_column();
+    if (!col) return LC_ERR_NOMEM;
+    cudaGetDevice(&col->device);
+    int rc = validate_blob((const uint8_t*)host, len, col);
+    if (rc) { lc_free(col); return rc; }
+    cudaStream_t st = (cudaStream_t)stream;
+    col->blob_cap = len;
+    if (cudaMalloc((void**)&col->blob, len) != cudaSuccess) {
+        col->blob = nullptr;
+        lc_free(col);
+        return LC_ERR_NOMEM;
+    }
+    rc = cuda_status(cudaMemcpyAsync(col->blob, host, len, cudaMemcpyHostToDevice, st));
+    if (!rc) rc = build_derived(col, st);
+    if (rc) { lc_free(col); return rc; }
+    *out = col;
+    return LC_OK;
+}
+
+int lc_status(const lc_column* col, void* stream) {
+    if (!col) return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t s = 0;
+    int rc = cuda_status(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    rc = cuda_status(cudaMemcpy(&s, col->status, 4, cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    if (s) cudaMemset(col->status, 0, 4);
+    if (s & kStOutOfRange) return LC_ERR_OUT_OF_RANGE;
+    if (s & kStUnsorted) return LC_ERR_UNSORTED;
+    if (s) return LC_ERR_INTERNAL;
+    return LC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// lc_internal.h -- internal structures shared by the translation units of the
+// GB300 learned-compression library (not part of the public C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lc.h"
+
+namespace lcx {
+
+// Keys decoded by one CTA of the decode kernel.  Tiles never cross a chunk.
+constexpr int kTileLog = 11;
+constexpr uint32_t kTile = 1u << kTileLog;
+// Keys per speculation block of the fitter (one 64-bit word of anchor bits).
+constexpr uint32_t kBlock = 64;
+// A chunk holds at most 2^16 keys.
+constexpr uint32_t kMaxChunk = 1u << 16;
+
+// Device status bits (OR-ed by kernels, read by lc_status / lc_compress).
+enum : uint32_t {
+    kStUnsorted = 1u,
+    kStOutOfRange = 2u,
+    kStInternal = 4u,
+};
+
+// One chunk of the fit: keys [key_begin, key_begin + n) of the input, error
+// bound eps, and where its anchor bits live in the bitmap.
+struct ChunkDesc {
+    uint64_t key_begin;
+    uint64_t bitword_begin;  // first 32-bit word of this chunk's anchor bitmap
+    uint32_t n;
+    uint32_t eps;
+    uint32_t check_prev;  // 1: K[key_begin - 1] <= K[key_begin] must hold (same list)
+    uint32_t pad;
+};
+
+// A decode tile: keys [key_begin, key_begin + n) of chunk `chunk`; its first
+// and last keys lie in segments seg_lo and seg_hi (global segment indices).
+struct TileDesc {
+    uint64_t key_begin;
+    uint64_t seg_lo;
+    uint64_t seg_hi;
+    uint32_t chunk;
+    uint32_t n;
+};
+
+// Byte offsets of every array inside an LCF1 blob.
+struct Layout {
+    uint64_t lkb, lcb, leps, llog;          // list mode only
+    uint64_t ckb, csb, cwb;                 // chunk directory
+    uint64_t icpt, slope, bitoff, start, width, payload;
+    uint64_t total;                          // exact blob length
+};
+
+Layout make_layout(int kb, uint64_t C, uint64_t L, uint64_t W, uint64_t NL, bool list_mode);
+
+// Read-only device view of a column, passed to kernels by value.
+struct ColView {
+    const uint64_t* ckb;  // chunk_key_begin [C+1]
+    const uint64_t* csb;  // chunk_seg_begin [C+1]
+    const uint64_t* cwb;  // chunk_word_begin [C+1]
+    const void* icpt;     // [L] key_bytes each
+    const int64_t* slope;
+    const uint32_t* bitoff;
+    const uint16_t* start;
+    const uint8_t* width;
+    const uint32_t* pay32;  // payload as 32-bit little-endian words [2W]
+    const TileDesc* tiles;
+    const uint64_t* chunk_tile_begin;  // [C+1]
+    const uint64_t* chunk_first_key;   // [C]
+    uint32_t* status;
+    uint64_t N, C, L, W, ntiles;
+    uint32_t chunk_log2;  // 0 in list mode
+    uint32_t list_mode;
+};
+
+}  // namespace lcx
+
+// The opaque column of the public ABI.
+struct lc_column {
+    int device;
+    uint32_t key_bytes, chunk_log2, list_mode;
+    uint64_t N, eps, C, L, W, NL;
+    lcx::Layout lay;
+    uint8_t* blob;            // device, exact LCF1 bytes (allocation may be larger)
+    uint64_t blob_cap;
+    lcx::TileDesc* tiles;     // device, derived
+    uint64_t ntiles;
+    uint64_t* chunk_tile_begin;  // device [C+1], derived
+    uint64_t* chunk_first_key;   // device [C], derived
+    uint32_t* status;            // device status word
+    uint64_t* h_ckb;             // host copy of chunk_key_begin [C+1]
+    uint64_t* h_ctb;             // host copy of chunk_tile_begin [C+1]
+    lcx::ColView view;
+};
+
+namespace lcx {
+
+// Compression pipeline (lc_compress.cu).  chunks_h: C chunk descriptors (host).
+// Allocates col->blob and fills everything but the prefix (header, list
+// directory, chunk_key_begin) and the padding bytes; sets col->L, col->W and
+// col->lay.  Synchronizes `st`.
+int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
+                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col);
+// Upload the host-built prefix of the blob and zero its padding bytes.
+int finish_blob(lc_column* col, const uint8_t* prefix_h, uint64_t prefix_len, cudaStream_t st);
+
+// Derived directories and the kernel view (lc_query.cu).
+int build_derived(lc_column* col, cudaStream_t st);
+
+int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);
+int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count,
+                  const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
+int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st);
+int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
+
+// Exclusive scan of n uint32 counts into n+1 uint64 offsets (out[n] = total),
+// optionally applying f(count) = even_words(count bits) first.
+enum class ScanOp { Identity, BitsToEvenWords };
+int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n, ScanOp op, void* tmp,
+                   size_t tmp_bytes, cudaStream_t st);
+size_t scan_tmp_bytes(uint64_t n);
+
+int cuda_status(cudaError_t e);
+
+// Count of kernel launches issued by the library in this process.
+void note_launch(uint32_t k = 1);
+
+}  // namespace lcx

@@ -1,0 +1,465 @@
+// lc_query.cu -- decoding from K^c on the GPU: bulk and range decode, rank
+// access and value lower_bound (Def. 1 decoding, Fig. 2 decoding stage
+// K[i] = floor(f_j(i)) + Delta[i]; Table 2 / Sec. III-A segment search).
+//
+// Decode works on tiles of 2048 keys that never cross a chunk.  A CTA stages
+// the model of every segment that meets its tile (intercept, slope, bit base,
+// start, width) and the tile's payload words in shared memory, marks the
+// segment starts in a 2048-bit map, and then every key finds its segment by a
+// rank (popcount) on that map: no search per key.  Keys are written with
+// consecutive threads on consecutive keys (coalesced).
+#include <algorithm>
+#include <vector>
+
+#include "lc_internal.h"
+#include "lc_math.cuh"
+
+namespace lcx {
+namespace {
+
+constexpr int kDecThreads = 256;
+constexpr uint32_t kMaxSegsPerTile = kTile + 1;
+constexpr size_t kDecSmem = (size_t)kMaxSegsPerTile * 24 + 64 * 4 * 2 + (kTile + 4) * 4;
+
+template <typename KT>
+__device__ __forceinline__ uint64_t ld_icpt(const void* icpt, uint64_t j) {
+    return (uint64_t)__ldg((const KT*)icpt + j);
+}
+
+// Tile index of key i (chunk-relative position `local` in chunk c).
+__device__ __forceinline__ uint64_t tile_of(const ColView& v, uint64_t c, uint64_t local) {
+    return v.chunk_tile_begin[c] + (local >> kTileLog);
+}
+
+// Chunk holding key i.
+__device__ __forceinline__ uint64_t chunk_of(const ColView& v, uint64_t i) {
+    if (!v.list_mode) return i >> v.chunk_log2;
+    uint64_t lo = 0, hi = v.C - 1;  // last c with ckb[c] <= i
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(v.ckb + mid) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Decode keys [lo_key, hi_key) of tile t into out[g - lo_key].
+template <typename KT>
+__device__ void decode_tile(const ColView& v, uint64_t t, uint64_t lo_key, uint64_t hi_key, KT* __restrict__ out,
+                            uint8_t* smem) {
+    uint64_t* s_icpt = (uint64_t*)smem;
+    int64_t* s_slope = (int64_t*)(s_icpt + kMaxSegsPerTile);
+    uint64_t* s_meta = (uint64_t*)(s_slope + kMaxSegsPerTile);
+    uint32_t* s_bm = (uint32_t*)(s_meta + kMaxSegsPerTile);
+    uint32_t* s_pref = s_bm + 64;
+    uint32_t* s_pay = s_pref + 64;
+    __shared__ uint32_t s_win[2];
+
+    const uint32_t tid = threadIdx.x;
+    const TileDesc td = v.tiles[t];
+    const uint64_t c = td.chunk;
+    const uint64_t ckb = __ldg(v.ckb + c);
+    const uint32_t local0 = (uint32_t)(td.key_begin - ckb);
+    const uint32_t n = td.n;
+    const uint64_t j0 = td.seg_lo;
+    const uint32_t ns = (uint32_t)(td.seg_hi - j0 + 1);
+
+    if (tid < 64) s_bm[tid] = 0;
+    __syncthreads();
+    for (uint32_t j = tid; j < ns; j += kDecThreads) {
+        const uint64_t g = j0 + j;
+        const uint32_t st = __ldg(v.start + g);
+        const uint32_t w = __ldg(v.width + g);
+        const uint32_t bo = __ldg(v.bitoff + g);
+        s_icpt[j] = ld_icpt<KT>(v.icpt, g);
+        s_slope[j] = __ldg(v.slope + g);
+        // chunk-relative bit of the residual of key i (> st): bo + w (i - st - 1)
+        const uint32_t base = bo - w * (st + 1);
+        s_meta[j] = (uint64_t)base | ((uint64_t)st << 32) | ((uint64_t)w << 48);
+        const uint32_t p = j ? st - local0 : 0;
+        atomicOr(&s_bm[p >> 5], 1u << (p & 31u));
+    }
+    __syncthreads();
+    if (tid < 32) {
+        // exclusive popcount prefix over the 64 bitmap words, two per lane
+        const uint32_t a = __popc(s_bm[2 * tid]), b = __popc(s_bm[2 * tid + 1]);
+        uint32_t inc = a + b;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+            if (tid >= (uint32_t)off) inc += o;
+        }
+        const uint32_t ex = inc - a - b;
+        s_pref[2 * tid] = ex;
+        s_pref[2 * tid + 1] = ex + a;
+        if (tid == 0) {
+            // payload window: from the tile's first residual to the end of its last
+            const uint64_t m0 = s_meta[0], m1 = s_meta[ns - 1];
+            const uint32_t st0 = (uint32_t)(m0 >> 32) & 0xFFFFu, w0 = (uint32_t)(m0 >> 48);
+            const uint32_t st1 = (uint32_t)(m1 >> 32) & 0xFFFFu, w1 = (uint32_t)(m1 >> 48);
+            const uint32_t lo_bit = (uint32_t)m0 + w0 * max(local0, st0 + 1);
+            const uint32_t hi_bit = (uint32_t)m1 + w1 * (max(local0 + n - 1, st1) + 1);
+            s_win[0] = lo_bit >> 5;
+            s_win[1] = ((hi_bit + 31) >> 5) - (lo_bit >> 5) + 1;
+        }
+    }
+    __syncthreads();
+    const uint32_t wlo = s_win[0], cnt = s_win[1];
+    const uint64_t pbase = 2 * __ldg(v.cwb + c) + wlo;
+    const uint64_t plimit = 2 * v.W;
+    for (uint32_t q = tid; q < cnt + 1; q += kDecThreads) {
+        const uint64_t gi = pbase + q;
+        s_pay[q] = gi < plimit ? __ldg(v.pay32 + gi) : 0u;
+    }
+    __syncthreads();
+
+    const uint64_t kbeg = td.key_begin;
+    uint32_t p0 = 0, p1 = n;
+    if (lo_key > kbeg) p0 = (uint32_t)(lo_key - kbeg < (uint64_t)n ? lo_key - kbeg : (uint64_t)n);
+    if (hi_key < kbeg + n) p1 = (uint32_t)(hi_key > kbeg ? hi_key - kbeg : 0);
+    const uint32_t wbit = 32u * wlo;
+    for (uint32_t p = p0 + tid; p < p1; p += kDecThreads) {
+        const uint32_t wd = p >> 5;
+        const uint32_t j = s_pref[wd] + __popc(s_bm[wd] & (0xFFFFFFFFu >> (31u - (p & 31u)))) - 1;
+        const uint64_t meta = s_meta[j];
+        const uint32_t st = (uint32_t)(meta >> 32) & 0xFFFFu, w = (uint32_t)(meta >> 48);
+        const uint32_t i = local0 + p;
+        uint64_t key = s_icpt[j];
+        const uint32_t tt = i - st;
+        if (tt) {
+            const uint32_t lb = (uint32_t)meta + w * i - wbit;
+            const uint32_t z = extract_bits(s_pay[lb >> 5], s_pay[(lb >> 5) + 1], lb & 31u, w);
+            key += (uint64_t)(line_at(s_slope[j], tt) + (int64_t)unzigzag32(z));
+        }
+        out[kbeg + p - lo_key] = (KT)key;
+    }
+    __syncthreads();
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(kDecThreads) decode_kernel(ColView v, uint64_t t0, uint64_t begin, uint64_t end,
+                                                             KT* __restrict__ out) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    decode_tile<KT>(v, t0 + blockIdx.x, begin, end, out, smem);
+}
+
+// Work items of a multi-range decode: range r covers tiles
+// [first[r], first[r] + ntiles[r]).
+__global__ void range_tiles_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
+                                   uint64_t m, uint64_t* __restrict__ first, uint32_t* __restrict__ ntiles) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m; r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = begin[r], cnt = count[r];
+        if (cnt == 0 || b > v.N || cnt > v.N - b) {
+            if (cnt) atomicOr(v.status, kStOutOfRange);
+            first[r] = 0;
+            ntiles[r] = 0;
+            continue;
+        }
+        const uint64_t e = b + cnt - 1;
+        const uint64_t cb = chunk_of(v, b), ce = chunk_of(v, e);
+        const uint64_t tb = tile_of(v, cb, b - __ldg(v.ckb + cb));
+        const uint64_t te = tile_of(v, ce, e - __ldg(v.ckb + ce));
+        first[r] = tb;
+        ntiles[r] = (uint32_t)(te - tb + 1);
+    }
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(kDecThreads)
+decode_ranges_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
+                     const uint64_t* __restrict__ out_off, uint64_t m, const uint64_t* __restrict__ first,
+                     const uint64_t* __restrict__ work_off, KT* __restrict__ out) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint64_t total = work_off[m];
+    for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        uint64_t lo = 0, hi = m - 1;  // last r with work_off[r] <= w
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (work_off[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t r = lo;
+        const uint64_t b = begin[r];
+        decode_tile<KT>(v, first[r] + (w - work_off[r]), b, b + count[r], out + out_off[r], smem);
+    }
+}
+
+// One key from global memory: key t of segment j in chunk c.
+template <typename KT>
+__device__ __forceinline__ uint64_t key_at(const ColView& v, uint64_t c, uint64_t j, uint32_t t) {
+    uint64_t key = ld_icpt<KT>(v.icpt, j);
+    if (t == 0) return key;
+    const uint32_t w = __ldg(v.width + j);
+    const int64_t line = line_at(__ldg(v.slope + j), t);
+    if (w == 0) return key + (uint64_t)line;
+    const uint64_t pos = 64 * __ldg(v.cwb + c) + __ldg(v.bitoff + j) + (uint64_t)w * (t - 1);
+    const uint64_t wi = pos >> 5;  // < 2W: the residual's bits lie inside the payload
+    const uint32_t lo = __ldg(v.pay32 + wi);
+    const uint32_t hi = wi + 1 < 2 * v.W ? __ldg(v.pay32 + wi + 1) : 0u;
+    const uint32_t z = extract_bits(lo, hi, (uint32_t)(pos & 31u), w);
+    return key + (uint64_t)(line + (int64_t)unzigzag32(z));
+}
+
+template <typename KT>
+__global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint64_t m, KT* __restrict__ out) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = idx[q];
+        if (i >= v.N) {
+            atomicOr(v.status, kStOutOfRange);
+            out[q] = 0;
+            continue;
+        }
+        const uint64_t c = chunk_of(v, i);
+        const uint32_t local = (uint32_t)(i - __ldg(v.ckb + c));
+        const TileDesc* td = v.tiles + tile_of(v, c, local);
+        uint64_t lo = __ldg(&td->seg_lo), hi = __ldg(&td->seg_hi);  // last j with start[j] <= local
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(v.start + mid) <= local) lo = mid;
+            else hi = mid - 1;
+        }
+        out[q] = (KT)key_at<KT>(v, c, lo, local - __ldg(v.start + lo));
+    }
+}
+
+template <typename KT>
+__global__ void lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m, uint64_t* __restrict__ out) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = (uint64_t)vals[q];
+        if (v.C == 0 || __ldg(v.chunk_first_key) >= x) {
+            out[q] = 0;
+            continue;
+        }
+        // last chunk whose first key is < x
+        uint64_t lo = 0, hi = v.C - 1;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(v.chunk_first_key + mid) < x) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t c = lo;
+        // last segment of the chunk whose intercept (its first key) is < x
+        const uint64_t s_end = __ldg(v.csb + c + 1);
+        lo = __ldg(v.csb + c);
+        hi = s_end - 1;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (ld_icpt<KT>(v.icpt, mid) < x) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint64_t j = lo;
+        const uint64_t ckb = __ldg(v.ckb + c);
+        const uint32_t st = __ldg(v.start + j);
+        const uint32_t nj = (j + 1 < s_end ? (uint32_t)__ldg(v.start + j + 1) : (uint32_t)(__ldg(v.ckb + c + 1) - ckb)) - st;
+        // first key of the segment that is >= x (keys are sorted), or its end
+        uint32_t a = 1, b = nj;
+        while (a < b) {
+            const uint32_t mid = (a + b) >> 1;
+            if (key_at<KT>(v, c, j, mid) < x) a = mid + 1;
+            else b = mid;
+        }
+        out[q] = ckb + st + a;
+    }
+}
+
+__global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles) {
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (t >= v.ntiles) return;
+    uint64_t lo = 0, hi = v.C - 1;  // chunk: last c with chunk_tile_begin[c] <= t
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (v.chunk_tile_begin[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const uint64_t c = lo;
+    const uint64_t k = t - v.chunk_tile_begin[c];
+    const uint64_t ckb = v.ckb[c], nc = v.ckb[c + 1] - ckb;
+    const uint32_t local0 = (uint32_t)(k * kTile);
+    const uint32_t n = (uint32_t)(nc - local0 < (uint64_t)kTile ? nc - local0 : (uint64_t)kTile);
+    const uint32_t local1 = local0 + n - 1;
+    auto last_start_le = [&](uint32_t pos) {
+        uint64_t a = v.csb[c], b = v.csb[c + 1] - 1;
+        while (a < b) {
+            const uint64_t mid = (a + b + 1) >> 1;
+            if (v.start[mid] <= pos) a = mid;
+            else b = mid - 1;
+        }
+        return a;
+    };
+    TileDesc d;
+    d.key_begin = ckb + local0;
+    d.seg_lo = last_start_le(local0);
+    d.seg_hi = last_start_le(local1);
+    d.chunk = (uint32_t)c;
+    d.n = n;
+    tiles[t] = d;
+}
+
+template <typename KT>
+__global__ void first_key_kernel(ColView v, uint64_t* __restrict__ fk) {
+    const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (c < v.C) fk[c] = ld_icpt<KT>(v.icpt, v.csb[c]);
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <typename KT>
+int set_smem() {
+    static bool done = false;
+    if (done) return LC_OK;
+    cudaError_t e = cudaFuncSetAttribute(decode_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(decode_ranges_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem);
+    if (e != cudaSuccess) return cuda_status(e);
+    done = true;
+    return LC_OK;
+}
+
+}  // namespace
+
+int build_derived(lc_column* col, cudaStream_t st) {
+    const uint64_t C = col->C;
+    // host: tiles per chunk from the chunk directory
+    std::vector<uint64_t> ctb(C + 1, 0);
+    for (uint64_t c = 0; c < C; ++c) {
+        const uint64_t nc = col->h_ckb[c + 1] - col->h_ckb[c];
+        ctb[c + 1] = ctb[c] + (nc + kTile - 1) / kTile;
+    }
+    col->ntiles = ctb[C];
+    col->h_ctb = new (std::nothrow) uint64_t[C + 1];
+    if (!col->h_ctb) return LC_ERR_NOMEM;
+    std::copy(ctb.begin(), ctb.end(), col->h_ctb);
+    const size_t bytes = 8 * (C + 1) + 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1) + 256;
+    uint8_t* p = nullptr;
+    if (cudaMalloc((void**)&p, bytes) != cudaSuccess) return LC_ERR_NOMEM;
+    col->chunk_tile_begin = (uint64_t*)p;
+    col->chunk_first_key = (uint64_t*)(p + 8 * (C + 1));
+    col->tiles = (TileDesc*)(p + 16 * (C + 1));
+    col->status = (uint32_t*)(p + 16 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1));
+    int rc = cuda_status(cudaMemcpyAsync(col->chunk_tile_begin, ctb.data(), 8 * (C + 1), cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    rc = cuda_status(cudaMemsetAsync(col->status, 0, 4, st));
+    if (rc) return rc;
+
+    ColView& v = col->view;
+    const Layout& L = col->lay;
+    v.ckb = (const uint64_t*)(col->blob + L.ckb);
+    v.csb = (const uint64_t*)(col->blob + L.csb);
+    v.cwb = (const uint64_t*)(col->blob + L.cwb);
+    v.icpt = col->blob + L.icpt;
+    v.slope = (const int64_t*)(col->blob + L.slope);
+    v.bitoff = (const uint32_t*)(col->blob + L.bitoff);
+    v.start = (const uint16_t*)(col->blob + L.start);
+    v.width = (const uint8_t*)(col->blob + L.width);
+    v.pay32 = (const uint32_t*)(col->blob + L.payload);
+    v.tiles = col->tiles;
+    v.chunk_tile_begin = col->chunk_tile_begin;
+    v.chunk_first_key = col->chunk_first_key;
+    v.status = col->status;
+    v.N = col->N;
+    v.C = C;
+    v.L = col->L;
+    v.W = col->W;
+    v.ntiles = col->ntiles;
+    v.chunk_log2 = col->chunk_log2;
+    v.list_mode = col->list_mode;
+    if (C) {
+        tile_dir_kernel<<<(unsigned)((col->ntiles + 255) / 256), 256, 0, st>>>(v, col->tiles);
+        if (col->key_bytes == 4) first_key_kernel<uint32_t><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(v, col->chunk_first_key);
+        else first_key_kernel<uint64_t><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(v, col->chunk_first_key);
+        note_launch(2);
+        rc = cuda_status(cudaGetLastError());
+        if (rc) return rc;
+    }
+    return cuda_status(cudaStreamSynchronize(st));
+}
+
+// Host-side tile index of key i (uses the host copies of the directories).
+static uint64_t host_tile_of(const lc_column* col, uint64_t i) {
+    uint64_t c;
+    if (!col->list_mode) {
+        c = i >> col->chunk_log2;
+    } else {
+        c = (uint64_t)(std::upper_bound(col->h_ckb, col->h_ckb + col->C + 1, i) - col->h_ckb) - 1;
+    }
+    return col->h_ctb[c] + ((i - col->h_ckb[c]) >> kTileLog);
+}
+
+int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st) {
+    if (count == 0) return LC_OK;
+    const uint64_t t0 = host_tile_of(col, begin), t1 = host_tile_of(col, begin + count - 1);
+    const uint64_t nt = t1 - t0 + 1;
+    int rc;
+    if (col->key_bytes == 4) {
+        if ((rc = set_smem<uint32_t>())) return rc;
+        decode_kernel<uint32_t><<<(unsigned)nt, kDecThreads, kDecSmem, st>>>(col->view, t0, begin, begin + count,
+                                                                           (uint32_t*)out);
+    } else {
+        if ((rc = set_smem<uint64_t>())) return rc;
+        decode_kernel<uint64_t><<<(unsigned)nt, kDecThreads, kDecSmem, st>>>(col->view, t0, begin, begin + count,
+                                                                           (uint64_t*)out);
+    }
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count, const uint64_t* out_off,
+                  uint64_t m, void* out, cudaStream_t st) {
+    if (m == 0) return LC_OK;
+    const size_t tmp_b = scan_tmp_bytes(m);
+    const size_t bytes = 8 * m + 4 * m + 8 * (m + 1) + tmp_b + 64;
+    uint8_t* p = nullptr;
+    if (cudaMallocAsync((void**)&p, bytes, st) != cudaSuccess) return LC_ERR_NOMEM;
+    uint64_t* first = (uint64_t*)p;
+    uint64_t* work_off = first + m;
+    uint32_t* ntiles = (uint32_t*)(work_off + m + 1);
+    void* tmp = (void*)(((uintptr_t)(ntiles + m) + 15) & ~(uintptr_t)15);
+    range_tiles_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 4096), 256, 0, st>>>(col->view, begin, count,
+                                                                                              m, first, ntiles);
+    note_launch();
+    int rc = cuda_status(cudaGetLastError());
+    if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, tmp_b, st);
+    if (!rc) {
+        const unsigned grid = (unsigned)(sm_count() * 4);
+        if (col->key_bytes == 4) {
+            if (!(rc = set_smem<uint32_t>()))
+                decode_ranges_kernel<uint32_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off,
+                                                                                   m, first, work_off, (uint32_t*)out);
+        } else {
+            if (!(rc = set_smem<uint64_t>()))
+                decode_ranges_kernel<uint64_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off,
+                                                                                   m, first, work_off, (uint64_t*)out);
+        }
+        if (!rc) {
+            note_launch();
+            rc = cuda_status(cudaGetLastError());
+        }
+    }
+    cudaFreeAsync(p, st);
+    return rc;
+}
+
+int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st) {
+    if (m == 0) return LC_OK;
+    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
+    if (col->key_bytes == 4) access_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, idx, m, (uint32_t*)out);
+    else access_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, idx, m, (uint64_t*)out);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* out, cudaStream_t st) {
+    if (m == 0) return LC_OK;
+    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
+    if (col->key_bytes == 4) lower_bound_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, (const uint32_t*)vals, m, out);
+    else lower_bound_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, (const uint64_t*)vals, m, out);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lcx

@@ -1,0 +1,317 @@
+"""Thin Python binding of the C ABI in ``include/lc.h`` (ctypes).
+
+Every function has the name of the C entry point it calls and only marshals
+arguments: torch tensors become device pointers, the current torch CUDA stream
+becomes the ``stream`` argument.  Every step of the compressor runs in the CUDA
+kernels of ``liblc.so``; there is no CPU path.  If the library is not built the
+first call raises (build it with ``paper_2412_10770_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LC_OK = 0
+LC_ERR_INVALID_ARG = -1
+LC_ERR_UNSORTED = -2
+LC_ERR_OUT_OF_RANGE = -3
+LC_ERR_NOMEM = -4
+LC_ERR_CORRUPT = -5
+LC_ERR_CUDA = -6
+LC_ERR_TIMEOUT = -7
+LC_ERR_BUSY = -8
+LC_ERR_INTERNAL = -9
+LC_ERR_UNSUPPORTED = -10
+
+EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", "lc_decode_batch",
+           "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
+           "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
+           "lc_version", "lc_launch_count")
+
+
+class LcError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        msg = _lib_or_none().lc_strerror(code).decode() if _lib_or_none() else str(code)
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_uint64), ("chunk_log2", ctypes.c_uint32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("segments", ctypes.c_uint64),
+                ("words", ctypes.c_uint64), ("lists", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("eps", ctypes.c_uint64), ("key_bytes", ctypes.c_uint32), ("chunk_log2", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblc.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(paper_2412_10770_gb300.build.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    p, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    pu64 = ctypes.POINTER(ctypes.c_uint64)
+    sig = {
+        "lc_compress": ([p, u64, i32, ctypes.POINTER(_Params), p, pp], i32),
+        "lc_compress_batch": ([p, p, u64, i32, p, p, p, pp], i32),
+        "lc_decode": ([p, u64, u64, p, p], i32),
+        "lc_decode_ranges": ([p, p, p, p, u64, p, p], i32),
+        "lc_decode_batch": ([p, p, p], i32),
+        "lc_access": ([p, p, u64, p, p], i32),
+        "lc_lower_bound": ([p, p, u64, p, p], i32),
+        "lc_access1": ([p, u64, pu64], i32),
+        "lc_lower_bound1": ([p, u64, pu64], i32),
+        "lc_ratio": ([p], ctypes.c_double),
+        "lc_size": ([p, pu64], i32),
+        "lc_info": ([p, ctypes.POINTER(_Info)], i32),
+        "lc_serialize": ([p, p, u64, pu64], i32),
+        "lc_deserialize": ([p, u64, p, pp], i32),
+        "lc_status": ([p, p], i32),
+        "lc_free": ([p], None),
+        "lc_strerror": ([i32], ctypes.c_char_p),
+        "lc_version": ([], i32),
+        "lc_launch_count": ([], u64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != LC_OK:
+        raise LcError(rc, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _key_bytes(t: torch.Tensor) -> int:
+    if t.element_size() not in (4, 8) or t.is_floating_point():
+        raise TypeError("keys must be 32- or 64-bit integers")
+    return t.element_size()
+
+
+def _dev(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def key_dtype(key_bytes: int) -> torch.dtype:
+    return torch.uint32 if key_bytes == 4 else torch.uint64
+
+
+class Column:
+    """An lc_column handle (owns its device memory; freed with lc_free)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+        info = lc_info(self)
+        self.n = info["n"]
+        self.key_bytes = info["key_bytes"]
+        self.info = info
+
+    @property
+    def dtype(self) -> torch.dtype:
+        return key_dtype(self.key_bytes)
+
+    def free(self) -> None:
+        if self.handle and self.handle.value and _lib is not None:
+            _lib.lc_free(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # convenience methods
+    def decode(self, begin: int = 0, count: int | None = None, out=None, stream=None):
+        return lc_decode(self, begin, count, out, stream)
+
+    def access(self, idx, out=None, stream=None):
+        return lc_access(self, idx, out, stream)
+
+    def lower_bound(self, values, out=None, stream=None):
+        return lc_lower_bound(self, values, out, stream)
+
+    def serialize(self) -> bytes:
+        return lc_serialize(self)
+
+    def ratio(self) -> float:
+        return lc_ratio(self)
+
+
+def lc_compress(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, stream=None) -> Column:
+    lib = load()
+    _dev(keys, "keys")
+    kb = _key_bytes(keys)
+    h = ctypes.c_void_p()
+    prm = _Params(int(eps), int(chunk_log2))
+    _check(lib.lc_compress(keys.data_ptr(), keys.numel(), kb, ctypes.byref(prm), _stream(stream),
+                           ctypes.byref(h)), "lc_compress")
+    return Column(h.value)
+
+
+def lc_compress_batch(ids: torch.Tensor, list_begin, eps=0, chunk_log2=16, stream=None) -> Column:
+    lib = load()
+    _dev(ids, "ids")
+    kb = _key_bytes(ids)
+    lb = np.ascontiguousarray(list_begin, dtype=np.uint64)
+    nl = lb.size - 1
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.uint64), (nl,)))
+    g = np.ascontiguousarray(np.broadcast_to(np.asarray(chunk_log2, dtype=np.uint8), (nl,)))
+    h = ctypes.c_void_p()
+    _check(lib.lc_compress_batch(ids.data_ptr(), lb.ctypes.data, nl, kb, e.ctypes.data, g.ctypes.data,
+                                 _stream(stream), ctypes.byref(h)), "lc_compress_batch")
+    return Column(h.value)
+
+
+def lc_decode(col: Column, begin: int = 0, count: int | None = None, out=None, stream=None) -> torch.Tensor:
+    lib = load()
+    if count is None:
+        count = col.n - begin
+    if out is None:
+        out = torch.empty(count, dtype=col.dtype, device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_decode(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream)), "lc_decode")
+    return out
+
+
+def lc_decode_ranges(col: Column, begin: torch.Tensor, count: torch.Tensor, out_off: torch.Tensor, out: torch.Tensor,
+                     stream=None) -> torch.Tensor:
+    lib = load()
+    for t, nm in ((begin, "begin"), (count, "count"), (out_off, "out_off"), (out, "out")):
+        _dev(t, nm)
+    _check(lib.lc_decode_ranges(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(), begin.numel(),
+                                out.data_ptr(), _stream(stream)), "lc_decode_ranges")
+    return out
+
+
+def lc_decode_batch(col: Column, out=None, stream=None) -> torch.Tensor:
+    lib = load()
+    if out is None:
+        out = torch.empty(col.n, dtype=col.dtype, device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_decode_batch(col.handle, out.data_ptr(), _stream(stream)), "lc_decode_batch")
+    return out
+
+
+def lc_access(col: Column, idx: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    lib = load()
+    _dev(idx, "idx")
+    if idx.element_size() != 8:
+        raise TypeError("idx must hold 64-bit indices")
+    if out is None:
+        out = torch.empty(idx.numel(), dtype=col.dtype, device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_access(col.handle, idx.data_ptr(), idx.numel(), out.data_ptr(), _stream(stream)), "lc_access")
+    return out
+
+
+def lc_lower_bound(col: Column, values: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    lib = load()
+    _dev(values, "values")
+    if values.element_size() != col.key_bytes:
+        raise TypeError("values must have the column's key width")
+    if out is None:
+        out = torch.empty(values.numel(), dtype=torch.uint64, device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_lower_bound(col.handle, values.data_ptr(), values.numel(), out.data_ptr(), _stream(stream)),
+           "lc_lower_bound")
+    return out
+
+
+def lc_access1(col: Column, i: int) -> int:
+    v = ctypes.c_uint64()
+    _check(load().lc_access1(col.handle, int(i), ctypes.byref(v)), "lc_access1")
+    return v.value
+
+
+def lc_lower_bound1(col: Column, x: int) -> int:
+    v = ctypes.c_uint64()
+    _check(load().lc_lower_bound1(col.handle, int(x), ctypes.byref(v)), "lc_lower_bound1")
+    return v.value
+
+
+def lc_ratio(col: Column) -> float:
+    return load().lc_ratio(col.handle)
+
+
+def lc_size(col: Column) -> int:
+    v = ctypes.c_uint64()
+    _check(load().lc_size(col.handle, ctypes.byref(v)), "lc_size")
+    return v.value
+
+
+def lc_info(col: Column) -> dict:
+    inf = _Info()
+    _check(load().lc_info(col.handle, ctypes.byref(inf)), "lc_info")
+    return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+
+def lc_serialize(col: Column) -> bytes:
+    lib = load()
+    n = ctypes.c_uint64()
+    lib.lc_serialize(col.handle, None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.lc_serialize(col.handle, buf, n.value, ctypes.byref(n)), "lc_serialize")
+    return buf.raw[: n.value]
+
+
+def lc_deserialize(blob: bytes, stream=None) -> Column:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.lc_deserialize(blob, len(blob), _stream(stream), ctypes.byref(h)), "lc_deserialize")
+    return Column(h.value)
+
+
+def lc_status(col: Column, stream=None) -> int:
+    return load().lc_status(col.handle, _stream(stream))
+
+
+def lc_free(col: Column) -> None:
+    col.free()
+
+
+def lc_version() -> int:
+    return load().lc_version()
+
+
+def lc_launch_count() -> int:
+    return load().lc_launch_count()
