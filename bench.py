@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Benchmark of the learned compressor's hot path on GB300 (arXiv 2412.10770).
+
+Workload (the large single-column configuration): three sorted uint64 columns of
+N = 2e8 keys (lognormal gaps mu=2 sigma=1.5; 1000 piecewise-linear regimes with
+slopes log-uniform in [1, 1e4] and +-8 jitter; 1e5 clusters of ~2000 keys),
+eps = 63, 2^16-key chunks.  One step runs, for every column, the whole path:
+
+    compress (fit + model + pack)       -> K^c
+    full decode                          -> N keys
+    range decode of 4096-key windows     (16384 windows at random starts)
+    rank access                          1e8 uniform ranks
+    value lower_bound                    1e8 uniform values in [k_1, k_N]
+
+``value`` = keys of the columns pushed through that whole step per second
+(all ranks, max-over-ranks time).  Per-phase rates and algorithmic GB/s are in
+``phases``.  Inputs (1.6 GB per column) are larger than L2, so no flush is
+needed between steps.  ``e2e`` repeats the step through the same C ABI with the
+keys and queries in pinned host memory and the results copied back.
+
+``--impl reference`` times the CPU oracle (the plain C definition of the
+method) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "decode & compress keys/s + %HBM roofline; served p50/p99 vs plain path"
+GENS = ("lognormal", "piecewise", "clusters")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=200_000_000)
+    ap.add_argument("--eps", type=int, default=63)
+    ap.add_argument("--gens", default=",".join(GENS))
+    ap.add_argument("--queries", type=int, default=100_000_000)
+    ap.add_argument("--windows", type=int, default=16384)
+    ap.add_argument("--window-len", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gen_column(kind: str, n: int, seed: int):
+    from paper_2412_10770_gb300 import inputs
+
+    return inputs.column(kind, n, seed=seed, dtype=np.uint64)
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def oracle_sample_step(keys: np.ndarray, eps: int, nq: int, seed: int) -> float:
+    """One pass of the whole path with the CPU oracle over a sample; returns seconds."""
+    import oracle
+    from paper_2412_10770_gb300 import inputs
+
+    idx = inputs.uniform_ranks(nq, keys.size, seed=seed)
+    vals = inputs.uniform_values(nq, int(keys[0]), int(keys[-1]), seed=seed + 1)
+    t0 = time.perf_counter()
+    blob = oracle.compress(keys, eps, 16)
+    dec = oracle.decode(blob)
+    acc = oracle.access(blob, idx)
+    lb = oracle.lower_bound(blob, vals)
+    t = time.perf_counter() - t0
+    assert np.array_equal(dec, keys) and np.array_equal(acc, keys[idx.astype(np.int64)])
+    assert np.array_equal(lb, np.searchsorted(keys, vals, side="left"))
+    return t
+
+
+CPU_SAMPLE_LOG2 = 23
+
+
+def cpu_sample(args, full_cols=None):
+    """Bounded sample of the workload: the first 2^23 keys of each generator's
+    full-size column, with queries in the same proportion as the full workload."""
+    n_s = min(1 << CPU_SAMPLE_LOG2, args.n)
+    nq = max(1, int(n_s * args.queries / args.n))
+    gens = args.gens.split(",")
+    from paper_2412_10770_gb300 import inputs
+
+    if full_cols is None:
+        full_cols = [gen_column(g, args.n, inputs.seed_for(2, 1 + GENS.index(g))) for g in gens]
+    return [np.ascontiguousarray(c[:n_s]) for c in full_cols], nq, n_s
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cols, nq, n_s = cpu_sample(args)
+    for _ in range(args.warmup):
+        for c in cols:
+            oracle_sample_step(c, args.eps, nq, 7)
+    total = 0.0
+    for s in range(args.steps):
+        for c in cols:
+            total += oracle_sample_step(c, args.eps, nq, 11 + s)
+    keys = n_s * len(cols) * args.steps
+    value = keys / total
+    sample = (f"first 2^{CPU_SAMPLE_LOG2} keys of each of {len(cols)} full-size generator columns (eps={args.eps}), "
+              f"{nq} access + {nq} lower_bound queries each, compress+decode+access+lower_bound per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"large single column: {len(args.gens.split(','))} x N={args.n} sorted uint64 keys "
+                        f"({args.gens}), eps={args.eps}, 2^16-key chunks; per step compress, full decode, "
+                        f"{args.windows} range decodes of {args.window_len} keys, {args.queries} access and "
+                        f"{args.queries} lower_bound queries per column",
+            "n_keys_per_column": args.n, "key_bytes": 8, "eps": args.eps, "chunk_log2": 16,
+            "generators": args.gens.split(","), "queries": args.queries, "range_windows": args.windows,
+            "range_window_len": args.window_len, "l2": "inputs larger than L2 (1.6 GB per column vs 126 MB)"}
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2412_10770_gb300 import build as lcbuild
+
+    if rank == 0:
+        lcbuild.build()
+    if pg:
+        pg.barrier()
+    from paper_2412_10770_gb300 import inputs, lc
+
+    lc.load()
+    gens = args.gens.split(",")
+    N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
+    cols = []
+    for g in gens:
+        seed = inputs.seed_for(2, 1 + GENS.index(g)) + 1000 * rank  # weak scaling: own data per rank
+        k = gen_column(g, N, seed)
+        idx = inputs.uniform_ranks(m, N, seed=seed + 1)
+        vals = inputs.uniform_values(m, int(k[0]), int(k[-1]), seed=seed + 2)
+        rng = np.random.default_rng(seed + 3)
+        wb = rng.integers(0, N - wl + 1, size=nw, dtype=np.uint64)
+        wc = np.full(nw, wl, dtype=np.uint64)
+        wo = (np.arange(nw, dtype=np.uint64) * np.uint64(wl)).astype(np.uint64)
+        host = {"keys": k, "idx": idx, "vals": vals, "wb": wb, "wc": wc, "wo": wo}
+        dev = {nm: torch.from_numpy(a).cuda() for nm, a in host.items()}
+        cols.append((g, host, dev))
+    out_dec = torch.empty(N, dtype=torch.uint64, device="cuda")
+    out_rng = torch.empty(nw * wl, dtype=torch.uint64, device="cuda")
+    out_acc = torch.empty(m, dtype=torch.uint64, device="cuda")
+    out_lb = torch.empty(m, dtype=torch.uint64, device="cuda")
+    stream = torch.cuda.current_stream()
+    phases = ("compress", "decode", "range_decode", "access", "lower_bound")
+    sizes = {}
+
+    def one_step(ev=None):
+        for ci, (g, host, dev) in enumerate(cols):
+            marks = []
+            if ev is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                marks.append(e)
+            col = lc.lc_compress(dev["keys"], eps=args.eps, chunk_log2=16, stream=stream)
+            sizes[g] = (lc.lc_size(col), col.info["segments"], col.info["words"])
+
+            def mark():
+                if ev is not None:
+                    e = torch.cuda.Event(enable_timing=True)
+                    e.record(stream)
+                    marks.append(e)
+
+            mark()
+            lc.lc_decode(col, 0, N, out_dec, stream=stream)
+            mark()
+            lc.lc_decode_ranges(col, dev["wb"], dev["wc"], dev["wo"], out_rng, stream=stream)
+            mark()
+            lc.lc_access(col, dev["idx"], out_acc, stream=stream)
+            mark()
+            lc.lc_lower_bound(col, dev["vals"], out_lb, stream=stream)
+            mark()
+            col.free()
+            if ev is not None:
+                ev.append((g, marks))
+
+    # warm-up, with a correctness check of the first step's outputs
+    for w in range(args.warmup):
+        one_step()
+        if w == 0:
+            g, host, dev = cols[-1]
+            assert torch.equal(out_dec, dev["keys"]), "decode differs from the keys"
+            want = np.searchsorted(host["keys"], host["vals"][:100000], side="left")
+            assert np.array_equal(out_lb[:100000].cpu().numpy(), want), "lower_bound differs"
+    torch.cuda.synchronize()
+
+    gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
+    sampler = ClockSampler(gpu_id if gpu_id.isdigit() else str(local))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = lc.lc_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    evs = []
+    t_start.record(stream)
+    for _ in range(args.steps):
+        one_step(evs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = lc.lc_launch_count() - launches0
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    if pg:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        if pg:
+            pg.barrier()
+
+    # per-phase times (ms, summed over steps and columns)
+    ph_ms = {p: 0.0 for p in phases}
+    ph_ms_col = {g: {p: 0.0 for p in phases} for g in gens}
+    for g, marks in evs:
+        for i, p in enumerate(phases):
+            d = marks[i].elapsed_time(marks[i + 1])
+            ph_ms[p] += d
+            ph_ms_col[g][p] += d
+    K = args.steps
+    kb = 8
+    peak, peak_kind = measured_peaks()
+    blob_bytes = {g: sizes[g][0] for g in gens}
+    tot_blob = sum(blob_bytes.values())
+    ncols = len(gens)
+    # algorithmic bytes per phase per step (all columns)
+    alg = {
+        "compress": ncols * N * kb + tot_blob,
+        "decode": tot_blob + ncols * N * kb,
+        "range_decode": ncols * nw * wl * kb + ncols * nw * wl * kb * tot_blob / (ncols * N * kb),
+        "access": ncols * m * (8 + kb + 64),
+        "lower_bound": ncols * m * (kb + 8 + 64),
+    }
+    units = {"compress": ncols * N, "decode": ncols * N, "range_decode": ncols * nw * wl,
+             "access": ncols * m, "lower_bound": ncols * m}
+    phase_out = {}
+    for p in phases:
+        sec = ph_ms[p] / 1e3 / K
+        phase_out[p] = {"ms_per_step": ph_ms[p] / K, "units_per_s": units[p] / sec,
+                        "unit": "keys/s" if p in ("compress", "decode", "range_decode") else "queries/s",
+                        "alg_gbs": alg[p] / sec / 1e9, "hbm_frac": alg[p] / sec / 1e9 / peak,
+                        "per_column_ms": {g: ph_ms_col[g][p] / K for g in gens}}
+    dom = max(phases, key=lambda p: ph_ms[p])
+    dom_launch_ms = ph_ms[dom] / K / ncols
+    achieved = alg[dom] / ncols / (dom_launch_ms / 1e3) / 1e9
+    value = world * ncols * N / (ms / 1e3)
+
+    line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": workload_config(args),
+            "phases": phase_out,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
+                         "traffic": None},
+            "ratio": {g: blob_bytes[g] / (N * kb) for g in gens},
+            "segments": {g: sizes[g][1] for g in gens},
+            "clocks": clocks, "gpu_launches": launches}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        e2e = run_e2e(args, cols, lc, torch, stream)
+        if pg:
+            t = torch.tensor([e2e["ms"]], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e["ms"] = float(t.item())
+        line["e2e"] = {"value": world * ncols * N / (e2e["ms"] / 1e3), "unit": "keys/s",
+                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        samp, nq, n_s = cpu_sample(args, [host["keys"] for _, host, _ in cols])
+        t = sum(oracle_sample_step(c, args.eps, nq, 5) for c in samp)
+        line["cpu_baseline"] = {"value": n_s * len(samp) / t, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first 2^{CPU_SAMPLE_LOG2} keys of each generator column, {nq} access + {nq} "
+                                          f"lower_bound queries each; compress+decode+access+lower_bound",
+                                "seconds": t}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def run_e2e(args, cols, lc, torch, stream):
+    """The same step through the C ABI with inputs and results in pinned host
+    memory: every step copies keys and queries in and decoded keys and query
+    results out."""
+    N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
+    pinned = []
+    for g, host, dev in cols:
+        ph = {nm: torch.from_numpy(a).pin_memory() for nm, a in host.items()}
+        pinned.append(ph)
+    outs_h = {"dec": torch.empty(N, dtype=torch.uint64).pin_memory(),
+              "rng": torch.empty(nw * wl, dtype=torch.uint64).pin_memory(),
+              "acc": torch.empty(m, dtype=torch.uint64).pin_memory(),
+              "lb": torch.empty(m, dtype=torch.uint64).pin_memory()}
+    d_in = {nm: torch.empty_like(t, device="cuda") for nm, t in pinned[0].items()}
+    d_out = {"dec": torch.empty(N, dtype=torch.uint64, device="cuda"),
+             "rng": torch.empty(nw * wl, dtype=torch.uint64, device="cuda"),
+             "acc": torch.empty(m, dtype=torch.uint64, device="cuda"),
+             "lb": torch.empty(m, dtype=torch.uint64, device="cuda")}
+    h2d = sum(t.numel() * t.element_size() for ph in pinned for t in ph.values())
+    d2h = len(cols) * sum(t.numel() * t.element_size() for t in outs_h.values())
+
+    def step():
+        for ph in pinned:
+            for nm, t in ph.items():
+                d_in[nm].copy_(t, non_blocking=True)
+            col = lc.lc_compress(d_in["keys"], eps=args.eps, chunk_log2=16, stream=stream)
+            lc.lc_decode(col, 0, N, d_out["dec"], stream=stream)
+            lc.lc_decode_ranges(col, d_in["wb"], d_in["wc"], d_in["wo"], d_out["rng"], stream=stream)
+            lc.lc_access(col, d_in["idx"], d_out["acc"], stream=stream)
+            lc.lc_lower_bound(col, d_in["vals"], d_out["lb"], stream=stream)
+            for nm in outs_h:
+                outs_h[nm].copy_(d_out[nm], non_blocking=True)
+            torch.cuda.synchronize()
+            col.free()
+
+    step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return {"ms": a.elapsed_time(b) / args.steps, "h2d": h2d, "d2h": d2h}
+
+
+if __name__ == "__main__":
+    main()
