@@ -123,6 +123,26 @@ int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_de
 int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
                      const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream);
 
+/* lc_decode_ranges for callers that cannot allocate device memory.  It does
+ * the same work and writes the same output, but calls no cudaMalloc, cudaFree
+ * or allocating library routine.  This helps callers whose request path must
+ * not allocate: a serving loop that has to keep the allocator, and the device
+ * synchronisation a cudaFree can cause, out of its latency; or an application
+ * that owns all device memory and hands libraries only its own buffers.  The
+ * paper has no counterpart: this is an interface choice of the library.
+ *   - m <= LC_NOALLOC_MAX_RANGES, else LC_ERR_INVALID_ARG (nothing launched).
+ *   - The work lists live in one file-scope device array of about 0.7 MB that
+ *     every GPU loading the library keeps until the process exits.
+ *   - The first call on a device looks up that array's device address (with
+ *     the device current) and caches it; make this first call before any
+ *     stream capture.
+ *   - All calls share the array and leave their work lists in it.  Calls on
+ *     one stream are ordered and safe; calls whose kernels overlap on the GPU
+ *     (other streams, other host threads) race on it. */
+#define LC_NOALLOC_MAX_RANGES 32768
+int lc_decode_ranges_noalloc(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
+                             const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream);
+
 /* Every key of every list (list mode) or of the column.  Same as
  * lc_decode(col, 0, N, ...). */
 int lc_decode_batch(const lc_column* col, void* out_dev, void* stream);

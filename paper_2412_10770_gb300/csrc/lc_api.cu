@@ -292,6 +292,14 @@ int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint
     return decode_ranges(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
 }
 
+int lc_decode_ranges_noalloc(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
+                             const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream) {
+    if (!col || (m && (!begin_dev || !count_dev || !out_off_dev || !out_dev))) return LC_ERR_INVALID_ARG;
+    if (m > LC_NOALLOC_MAX_RANGES) return LC_ERR_INVALID_ARG;
+    if (col->N == 0) return LC_OK;
+    return decode_ranges_noalloc(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
+}
+
 int lc_decode_batch(const lc_column* col, void* out_dev, void* stream) {
     if (!col) return LC_ERR_INVALID_ARG;
     return lc_decode(col, 0, col->N, out_dev, stream);

@@ -113,6 +113,8 @@ int build_derived(lc_column* col, cudaStream_t st);
 int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);
 int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count,
                   const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
+int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uint64_t* count,
+                          const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st);
 int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
 

@@ -9,6 +9,7 @@
 // rank (popcount) on that map: no search per key.  Keys are written with
 // consecutive threads on consecutive keys (coalesced).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "lc_internal.h"
@@ -458,6 +459,87 @@ int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* ou
     const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
     if (col->key_bytes == 4) lower_bound_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, (const uint32_t*)vals, m, out);
     else lower_bound_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, (const uint64_t*)vals, m, out);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ multi-range decode without allocation
+//
+// lc_decode_ranges_noalloc serves callers that cannot call cudaMalloc or
+// cudaMallocAsync: for example a serving loop that must keep the allocator (and
+// the device synchronisation a cudaFree can imply) off its request path, or a
+// host application that owns all device memory and gives libraries only
+// buffers it allocated itself.  Its work lists live in one file-scope device
+// array instead of a per-call allocation.  Every GPU that loads this library
+// holds the array until the process exits.
+
+namespace {
+
+constexpr uint64_t kNoAllocMaxRanges = LC_NOALLOC_MAX_RANGES;
+constexpr size_t kNoAllocFirstOff = 0;                                                // uint64 first[m]
+constexpr size_t kNoAllocWorkOff = kNoAllocFirstOff + 8 * kNoAllocMaxRanges;          // uint64 work_off[m+1]
+constexpr size_t kNoAllocTilesOff = (kNoAllocWorkOff + 8 * (kNoAllocMaxRanges + 1) + 255) & ~(size_t)255;
+constexpr size_t kNoAllocScanOff = (kNoAllocTilesOff + 4 * kNoAllocMaxRanges + 255) & ~(size_t)255;
+constexpr size_t kNoAllocScanBytes = 8 * ((kNoAllocMaxRanges + 4095) / 4096 + 1);    // scan partials
+constexpr size_t kNoAllocScratchBytes = kNoAllocScanOff + kNoAllocScanBytes;
+
+__device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+uint8_t* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch(uint8_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kMaxDevices) return LC_ERR_INTERNAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        g_noalloc_ptr[dev] = (uint8_t*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LC_OK;
+}
+
+}  // namespace
+
+int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uint64_t* count, const uint64_t* out_off,
+                          uint64_t m, void* out, cudaStream_t st) {
+    if (m > kNoAllocMaxRanges) return LC_ERR_INVALID_ARG;
+    if (m == 0) return LC_OK;
+    uint8_t* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // Every word read below is written earlier in this call (first and ntiles
+    // by range_tiles_kernel, the scan partials and work_off by the scan), so
+    // nothing has to be cleared between calls.
+    uint64_t* first = (uint64_t*)(scratch + kNoAllocFirstOff);
+    uint64_t* work_off = (uint64_t*)(scratch + kNoAllocWorkOff);
+    uint32_t* ntiles = (uint32_t*)(scratch + kNoAllocTilesOff);
+    void* tmp = scratch + kNoAllocScanOff;
+    range_tiles_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 4096), 256, 0, st>>>(col->view, begin, count,
+                                                                                              m, first, ntiles);
+    note_launch();
+    rc = cuda_status(cudaGetLastError());
+    if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, kNoAllocScanBytes, st);
+    if (rc) return rc;
+    const unsigned grid = (unsigned)(sm_count() * 4);
+    if (col->key_bytes == 4) {
+        if ((rc = set_smem<uint32_t>())) return rc;
+        decode_ranges_kernel<uint32_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off, m, first,
+                                                                           work_off, (uint32_t*)out);
+    } else {
+        if ((rc = set_smem<uint64_t>())) return rc;
+        decode_ranges_kernel<uint64_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off, m, first,
+                                                                           work_off, (uint64_t*)out);
+    }
     note_launch();
     return cuda_status(cudaGetLastError());
 }

@@ -28,7 +28,8 @@ LC_ERR_BUSY = -8
 LC_ERR_INTERNAL = -9
 LC_ERR_UNSUPPORTED = -10
 
-EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", "lc_decode_batch",
+EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", "lc_decode_ranges_noalloc",
+           "lc_decode_batch",
            "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
            "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
            "lc_version", "lc_launch_count")
@@ -80,6 +81,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_compress_batch": ([p, p, u64, i32, p, p, p, pp], i32),
         "lc_decode": ([p, u64, u64, p, p], i32),
         "lc_decode_ranges": ([p, p, p, p, u64, p, p], i32),
+        "lc_decode_ranges_noalloc": ([p, p, p, p, u64, p, p], i32),
         "lc_decode_batch": ([p, p, p], i32),
         "lc_access": ([p, p, u64, p, p], i32),
         "lc_lower_bound": ([p, p, u64, p, p], i32),
@@ -220,6 +222,21 @@ def lc_decode_ranges(col: Column, begin: torch.Tensor, count: torch.Tensor, out_
         _dev(t, nm)
     _check(lib.lc_decode_ranges(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(), begin.numel(),
                                 out.data_ptr(), _stream(stream)), "lc_decode_ranges")
+    return out
+
+
+LC_NOALLOC_MAX_RANGES = 32768
+
+
+def lc_decode_ranges_noalloc(col: Column, begin: torch.Tensor, count: torch.Tensor, out_off: torch.Tensor,
+                             out: torch.Tensor, stream=None) -> torch.Tensor:
+    """lc_decode_ranges without any device allocation (at most
+    LC_NOALLOC_MAX_RANGES ranges; see include/lc.h)."""
+    lib = load()
+    for t, nm in ((begin, "begin"), (count, "count"), (out_off, "out_off"), (out, "out")):
+        _dev(t, nm)
+    _check(lib.lc_decode_ranges_noalloc(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(),
+                                        begin.numel(), out.data_ptr(), _stream(stream)), "lc_decode_ranges_noalloc")
     return out
 
 
