@@ -162,6 +162,7 @@ void lc_free(lc_column* col) {
     cudaDeviceSynchronize();
     if (col->blob) cudaFree(col->blob);
     if (col->chunk_tile_begin) cudaFree(col->chunk_tile_begin);
+    if (col->derived2) cudaFree(col->derived2);
     if (cur != col->device) cudaSetDevice(cur);
     delete[] col->h_ckb;
     delete[] col->h_ctb;

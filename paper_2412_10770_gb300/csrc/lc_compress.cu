@@ -46,6 +46,7 @@ constexpr int kModelThreads = 256;
 constexpr int kPackThreads = 256;
 constexpr uint32_t kWin = 2048;             // keys per pack window
 constexpr uint32_t kMaxBlocks = kMaxChunk / kBlock;
+constexpr uint32_t kWalkAhead = 8 * 32;     // keys the warp walk prefetches ahead of its step
 
 template <typename KT>
 __device__ __forceinline__ uint64_t ldk(const KT* __restrict__ K, uint32_t i) {
@@ -81,6 +82,8 @@ __device__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, 
         const uint32_t i = p + lane;
         const bool valid = i < n;
         const uint32_t d = i - x;
+        // keep the keys of the steps ahead on their way into L2
+        if (i + kWalkAhead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
         uint64_t D = valid ? ldk(K, i) - kx : 0;
         bool fits = false, tlo = false, thi = false;
         int64_t dlo = 0, dhi = 0;

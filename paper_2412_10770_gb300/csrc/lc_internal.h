@@ -46,6 +46,32 @@ struct TileDesc {
     uint32_t n;
 };
 
+// Derived (not serialized) directories of a column, built on the device when a
+// column is created.  They put everything one random query needs into few
+// sectors.
+//
+// SegRec: one segment's model in 32 bytes (one sector): intercept K[s_j],
+// Q32 slope, the global index of its anchor with the width in the top byte,
+// and the global payload bit of its residual t = 1.
+struct SegRec {
+    uint64_t icpt;
+    int64_t slope;
+    uint64_t kstart_w;  // anchor key index (low 56 bits) | width << 56
+    uint64_t bit1;
+};
+// RankWord: anchor bits of keys [64q, 64q + 64) and the number of anchors
+// before key 64q, so that the segment of key i is
+// before + popcount(bits & mask(i)) - 1.
+struct RankWord {
+    uint64_t bits;
+    uint64_t before;
+};
+// The sampled intercept levels used by lower_bound: level d >= 1 holds
+// icpt[16^d k]; level 0 is seg_icpt itself.  The top level has at most
+// kTopMax entries and is staged in shared memory.
+constexpr int kMaxLevels = 12;
+constexpr uint32_t kTopMax = 4096;
+
 // Byte offsets of every array inside an LCF1 blob.
 struct Layout {
     uint64_t lkb, lcb, leps, llog;          // list mode only
@@ -69,7 +95,13 @@ struct ColView {
     const uint32_t* pay32;  // payload as 32-bit little-endian words [2W]
     const TileDesc* tiles;
     const uint64_t* chunk_tile_begin;  // [C+1]
-    const uint64_t* chunk_first_key;   // [C]
+    const SegRec* recs;                // [L]
+    const RankWord* rank;              // [ceil(N / 64)]
+    const uint64_t* level[kMaxLevels]; // sampled intercepts, level[0] unused (seg_icpt)
+    uint64_t level_n[kMaxLevels];
+    uint32_t top;                      // index of the top level (staged in shared memory)
+    uint32_t max_tile_segs;            // most segments meeting one decode tile
+    uint32_t key_bytes;
     uint32_t* status;
     uint64_t N, C, L, W, ntiles;
     uint32_t chunk_log2;  // 0 in list mode
@@ -89,7 +121,7 @@ struct lc_column {
     lcx::TileDesc* tiles;     // device, derived
     uint64_t ntiles;
     uint64_t* chunk_tile_begin;  // device [C+1], derived
-    uint64_t* chunk_first_key;   // device [C], derived
+    uint8_t* derived2;           // device: SegRec, RankWord and intercept levels
     uint32_t* status;            // device status word
     uint64_t* h_ckb;             // host copy of chunk_key_begin [C+1]
     uint64_t* h_ctb;             // host copy of chunk_tile_begin [C+1]

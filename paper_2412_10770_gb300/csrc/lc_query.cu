@@ -22,6 +22,9 @@ constexpr int kDecThreads = 256;
 constexpr uint32_t kMaxSegsPerTile = kTile + 1;
 constexpr size_t kDecSmem = (size_t)kMaxSegsPerTile * 24 + 64 * 4 * 2 + (kTile + 4) * 4;
 
+// Shared memory of one decode CTA when no tile meets more than ms segments.
+__host__ __device__ constexpr size_t dec_smem(uint32_t ms) { return (size_t)ms * 24 + 64 * 4 * 2 + (kTile + 4) * 4; }
+
 template <typename KT>
 __device__ __forceinline__ uint64_t ld_icpt(const void* icpt, uint64_t j) {
     return (uint64_t)__ldg((const KT*)icpt + j);
@@ -48,10 +51,11 @@ __device__ __forceinline__ uint64_t chunk_of(const ColView& v, uint64_t i) {
 template <typename KT>
 __device__ void decode_tile(const ColView& v, uint64_t t, uint64_t lo_key, uint64_t hi_key, KT* __restrict__ out,
                             uint8_t* smem) {
+    const uint32_t ms = v.max_tile_segs;
     uint64_t* s_icpt = (uint64_t*)smem;
-    int64_t* s_slope = (int64_t*)(s_icpt + kMaxSegsPerTile);
-    uint64_t* s_meta = (uint64_t*)(s_slope + kMaxSegsPerTile);
-    uint32_t* s_bm = (uint32_t*)(s_meta + kMaxSegsPerTile);
+    int64_t* s_slope = (int64_t*)(s_icpt + ms);
+    uint64_t* s_meta = (uint64_t*)(s_slope + ms);
+    uint32_t* s_bm = (uint32_t*)(s_meta + ms);
     uint32_t* s_pref = s_bm + 64;
     uint32_t* s_pay = s_pref + 64;
     __shared__ uint32_t s_win[2];
@@ -185,22 +189,35 @@ decode_ranges_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64
     }
 }
 
-// One key from global memory: key t of segment j in chunk c.
-template <typename KT>
-__device__ __forceinline__ uint64_t key_at(const ColView& v, uint64_t c, uint64_t j, uint32_t t) {
-    uint64_t key = ld_icpt<KT>(v.icpt, j);
-    if (t == 0) return key;
-    const uint32_t w = __ldg(v.width + j);
-    const int64_t line = line_at(__ldg(v.slope + j), t);
-    if (w == 0) return key + (uint64_t)line;
-    const uint64_t pos = 64 * __ldg(v.cwb + c) + __ldg(v.bitoff + j) + (uint64_t)w * (t - 1);
+// Key t of the segment whose record is r (Fig. 2: floor(f_j(i)) + Delta[i]).
+__device__ __forceinline__ uint64_t rec_key(const ColView& v, const SegRec& r, uint32_t t) {
+    if (t == 0) return r.icpt;
+    const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+    const int64_t line = line_at(r.slope, t);
+    if (w == 0) return r.icpt + (uint64_t)line;
+    const uint64_t pos = r.bit1 + (uint64_t)w * (t - 1);
     const uint64_t wi = pos >> 5;  // < 2W: the residual's bits lie inside the payload
     const uint32_t lo = __ldg(v.pay32 + wi);
     const uint32_t hi = wi + 1 < 2 * v.W ? __ldg(v.pay32 + wi + 1) : 0u;
-    const uint32_t z = extract_bits(lo, hi, (uint32_t)(pos & 31u), w);
-    return key + (uint64_t)(line + (int64_t)unzigzag32(z));
+    return r.icpt + (uint64_t)(line + (int64_t)unzigzag32(extract_bits(lo, hi, (uint32_t)(pos & 31u), w)));
 }
 
+__device__ __forceinline__ SegRec load_rec(const SegRec* p) {
+    const ulonglong2* q = (const ulonglong2*)p;
+    const ulonglong2 a = __ldg(q), b = __ldg(q + 1);
+    SegRec r;
+    r.icpt = a.x;
+    r.slope = (int64_t)a.y;
+    r.kstart_w = b.x;
+    r.bit1 = b.y;
+    return r;
+}
+
+constexpr uint64_t kKeyMask = (1ull << 56) - 1;
+
+// Rank access: the segment of key i comes from one rank word (anchor bits +
+// anchors before), its model from one 32-byte record, its residual from the
+// payload: three dependent loads.
 template <typename KT>
 __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint64_t m, KT* __restrict__ out) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
@@ -210,60 +227,112 @@ __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint6
             out[q] = 0;
             continue;
         }
-        const uint64_t c = chunk_of(v, i);
-        const uint32_t local = (uint32_t)(i - __ldg(v.ckb + c));
-        const TileDesc* td = v.tiles + tile_of(v, c, local);
-        uint64_t lo = __ldg(&td->seg_lo), hi = __ldg(&td->seg_hi);  // last j with start[j] <= local
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(v.start + mid) <= local) lo = mid;
-            else hi = mid - 1;
-        }
-        out[q] = (KT)key_at<KT>(v, c, lo, local - __ldg(v.start + lo));
+        const ulonglong2 rw = __ldg((const ulonglong2*)(v.rank + (i >> 6)));
+        const uint64_t j = rw.y + __popcll(rw.x & (~0ull >> (63u - (uint32_t)(i & 63u)))) - 1;
+        const SegRec r = load_rec(v.recs + j);
+        out[q] = (KT)rec_key(v, r, (uint32_t)(i - (r.kstart_w & kKeyMask)));
     }
 }
 
+// Value lower_bound: the last segment whose intercept (its first key) is < x is
+// found through the 16-ary sampled intercept levels (top level in shared
+// memory, the next ones L2-resident, the last a 128-byte run of seg_icpt); then
+// the segment's own line brackets the answer: every key lies within
+// R = 2^(w-1) of floor(f), so keys before t < (dx - R)/s are < x and the key at
+// t >= (dx + R + 1)/s is >= x (s = slope / 2^32, dx = x - intercept).  A
+// binary search inside the bracket finishes.
 template <typename KT>
-__global__ void lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m, uint64_t* __restrict__ out) {
+__global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m,
+                                                          uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t s_top[];
+    const uint32_t top = v.top;
+    const uint64_t ntop = top ? v.level_n[top] : v.L;
+    for (uint64_t k = threadIdx.x; k < ntop; k += blockDim.x)
+        s_top[k] = top ? __ldg(v.level[top] + k) : ld_icpt<KT>(v.icpt, k);
+    __syncthreads();
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x = (uint64_t)vals[q];
-        if (v.C == 0 || __ldg(v.chunk_first_key) >= x) {
+        if (v.L == 0 || s_top[0] >= x) {
             out[q] = 0;
             continue;
         }
-        // last chunk whose first key is < x
-        uint64_t lo = 0, hi = v.C - 1;
+        uint64_t lo = 0, hi = ntop - 1;  // last entry < x
         while (lo < hi) {
             const uint64_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(v.chunk_first_key + mid) < x) lo = mid;
+            if (s_top[mid] < x) lo = mid;
             else hi = mid - 1;
         }
-        const uint64_t c = lo;
-        // last segment of the chunk whose intercept (its first key) is < x
-        const uint64_t s_end = __ldg(v.csb + c + 1);
-        lo = __ldg(v.csb + c);
-        hi = s_end - 1;
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (ld_icpt<KT>(v.icpt, mid) < x) lo = mid;
-            else hi = mid - 1;
+        for (int d = (int)top - 1; d >= 0; --d) {
+            const uint64_t nd = d ? v.level_n[d] : v.L;
+            const uint64_t base = 16 * lo;
+            uint64_t a = base, b = min(base + 16, nd) - 1;
+            while (a < b) {
+                const uint64_t mid = (a + b + 1) >> 1;
+                const uint64_t key = d ? __ldg(v.level[d] + mid) : ld_icpt<KT>(v.icpt, mid);
+                if (key < x) a = mid;
+                else b = mid - 1;
+            }
+            lo = a;
         }
         const uint64_t j = lo;
-        const uint64_t ckb = __ldg(v.ckb + c);
-        const uint32_t st = __ldg(v.start + j);
-        const uint32_t nj = (j + 1 < s_end ? (uint32_t)__ldg(v.start + j + 1) : (uint32_t)(__ldg(v.ckb + c + 1) - ckb)) - st;
-        // first key of the segment that is >= x (keys are sorted), or its end
-        uint32_t a = 1, b = nj;
+        const SegRec r = load_rec(v.recs + j);
+        const uint64_t ks = r.kstart_w & kKeyMask;
+        const uint64_t ke = j + 1 < v.L ? (__ldg(&v.recs[j + 1].kstart_w) & kKeyMask) : v.N;
+        const uint32_t n = (uint32_t)(ke - ks);
+        uint32_t a = 1, b = n;  // first t in [1, n) with key(t) >= x, or n
+        if (n >= 32 && r.slope > 0) {
+            const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+            const float s = (float)r.slope * 2.3283064365386963e-10f;  // keys per index
+            const float th = (float)(x - r.icpt) / s;
+            const float dl = ((float)((1u << w) >> 1) + 1.0f) / s + 2.0f;
+            const float fa = th - dl, fb = th + dl + 1.0f;
+            a = fa <= 1.0f ? 1u : (fa >= (float)n ? n : (uint32_t)fa);
+            b = fb <= 1.0f ? 1u : (fb >= (float)n ? n : (uint32_t)fb);
+            if (a > b) a = b;
+        }
         while (a < b) {
             const uint32_t mid = (a + b) >> 1;
-            if (key_at<KT>(v, c, j, mid) < x) a = mid + 1;
+            if (rec_key(v, r, mid) < x) a = mid + 1;
             else b = mid;
         }
-        out[q] = ckb + st + a;
+        out[q] = ks + a;
     }
 }
 
-__global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles) {
+// Derived directories: segment records and rank bits (one CTA per chunk).
+template <typename KT>
+__global__ void rec_kernel(ColView v, SegRec* __restrict__ recs, RankWord* __restrict__ rank) {
+    const uint64_t c = blockIdx.x;
+    const uint64_t ckb = v.ckb[c], bit0 = 64 * v.cwb[c];
+    for (uint64_t j = v.csb[c] + threadIdx.x; j < v.csb[c + 1]; j += blockDim.x) {
+        const uint64_t k = ckb + v.start[j];
+        SegRec r;
+        r.icpt = ld_icpt<KT>(v.icpt, j);
+        r.slope = v.slope[j];
+        r.kstart_w = k | ((uint64_t)v.width[j] << 56);
+        r.bit1 = bit0 + v.bitoff[j];
+        recs[j] = r;
+        atomicOr((unsigned long long*)&rank[k >> 6].bits, 1ull << (k & 63u));
+    }
+}
+
+__global__ void rank_pop_kernel(const RankWord* __restrict__ rank, uint64_t nw, uint32_t* __restrict__ pop) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nw; q += (uint64_t)gridDim.x * blockDim.x)
+        pop[q] = __popcll(rank[q].bits);
+}
+
+__global__ void rank_before_kernel(RankWord* __restrict__ rank, uint64_t nw, const uint64_t* __restrict__ before) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nw; q += (uint64_t)gridDim.x * blockDim.x)
+        rank[q].before = before[q];
+}
+
+template <typename KT>
+__global__ void level_kernel(ColView v, uint64_t* __restrict__ lvl, uint64_t n, uint64_t stride) {
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
+        lvl[k] = ld_icpt<KT>(v.icpt, k * stride);
+}
+
+__global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles, uint32_t* __restrict__ max_segs) {
     const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (t >= v.ntiles) return;
     uint64_t lo = 0, hi = v.C - 1;  // chunk: last c with chunk_tile_begin[c] <= t
@@ -294,12 +363,7 @@ __global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles) {
     d.chunk = (uint32_t)c;
     d.n = n;
     tiles[t] = d;
-}
-
-template <typename KT>
-__global__ void first_key_kernel(ColView v, uint64_t* __restrict__ fk) {
-    const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (c < v.C) fk[c] = ld_icpt<KT>(v.icpt, v.csb[c]);
+    atomicMax(max_segs, (uint32_t)(d.seg_hi - d.seg_lo + 1));
 }
 
 int sm_count() {
@@ -324,7 +388,7 @@ int set_smem() {
 }  // namespace
 
 int build_derived(lc_column* col, cudaStream_t st) {
-    const uint64_t C = col->C;
+    const uint64_t C = col->C, L = col->L, N = col->N;
     // host: tiles per chunk from the chunk directory
     std::vector<uint64_t> ctb(C + 1, 0);
     for (uint64_t c = 0; c < C; ++c) {
@@ -335,48 +399,115 @@ int build_derived(lc_column* col, cudaStream_t st) {
     col->h_ctb = new (std::nothrow) uint64_t[C + 1];
     if (!col->h_ctb) return LC_ERR_NOMEM;
     std::copy(ctb.begin(), ctb.end(), col->h_ctb);
-    const size_t bytes = 8 * (C + 1) + 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1) + 256;
+    const size_t bytes = 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1) + 256;
     uint8_t* p = nullptr;
     if (cudaMalloc((void**)&p, bytes) != cudaSuccess) return LC_ERR_NOMEM;
     col->chunk_tile_begin = (uint64_t*)p;
-    col->chunk_first_key = (uint64_t*)(p + 8 * (C + 1));
-    col->tiles = (TileDesc*)(p + 16 * (C + 1));
-    col->status = (uint32_t*)(p + 16 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1));
+    col->tiles = (TileDesc*)(p + 8 * (C + 1));
+    col->status = (uint32_t*)(p + 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1));
     int rc = cuda_status(cudaMemcpyAsync(col->chunk_tile_begin, ctb.data(), 8 * (C + 1), cudaMemcpyHostToDevice, st));
     if (rc) return rc;
     rc = cuda_status(cudaMemsetAsync(col->status, 0, 4, st));
     if (rc) return rc;
 
+    // segment records, rank words, sampled intercept levels
+    const uint64_t nw = (N + 63) / 64;
+    uint32_t top = 0;
+    uint64_t level_n[kMaxLevels] = {L};
+    uint64_t level_off[kMaxLevels] = {0};
+    uint64_t lv_total = 0;
+    while (level_n[top] > kTopMax && top + 1 < (uint32_t)kMaxLevels) {
+        ++top;
+        level_n[top] = (level_n[top - 1] + 15) / 16;
+        level_off[top] = lv_total;
+        lv_total += level_n[top];
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t off_rank = al(sizeof(SegRec) * L);
+    const size_t off_lv = al(off_rank + sizeof(RankWord) * nw);
+    const size_t bytes2 = al(off_lv + 8 * lv_total) + 256;
+    if (cudaMalloc((void**)&col->derived2, bytes2) != cudaSuccess) return LC_ERR_NOMEM;
+    SegRec* recs = (SegRec*)col->derived2;
+    RankWord* rank = (RankWord*)(col->derived2 + off_rank);
+    uint64_t* lv = (uint64_t*)(col->derived2 + off_lv);
+    if (nw) {
+        rc = cuda_status(cudaMemsetAsync(rank, 0, sizeof(RankWord) * nw, st));
+        if (rc) return rc;
+    }
+
     ColView& v = col->view;
-    const Layout& L = col->lay;
-    v.ckb = (const uint64_t*)(col->blob + L.ckb);
-    v.csb = (const uint64_t*)(col->blob + L.csb);
-    v.cwb = (const uint64_t*)(col->blob + L.cwb);
-    v.icpt = col->blob + L.icpt;
-    v.slope = (const int64_t*)(col->blob + L.slope);
-    v.bitoff = (const uint32_t*)(col->blob + L.bitoff);
-    v.start = (const uint16_t*)(col->blob + L.start);
-    v.width = (const uint8_t*)(col->blob + L.width);
-    v.pay32 = (const uint32_t*)(col->blob + L.payload);
+    const Layout& Ly = col->lay;
+    v.ckb = (const uint64_t*)(col->blob + Ly.ckb);
+    v.csb = (const uint64_t*)(col->blob + Ly.csb);
+    v.cwb = (const uint64_t*)(col->blob + Ly.cwb);
+    v.icpt = col->blob + Ly.icpt;
+    v.slope = (const int64_t*)(col->blob + Ly.slope);
+    v.bitoff = (const uint32_t*)(col->blob + Ly.bitoff);
+    v.start = (const uint16_t*)(col->blob + Ly.start);
+    v.width = (const uint8_t*)(col->blob + Ly.width);
+    v.pay32 = (const uint32_t*)(col->blob + Ly.payload);
     v.tiles = col->tiles;
     v.chunk_tile_begin = col->chunk_tile_begin;
-    v.chunk_first_key = col->chunk_first_key;
+    v.recs = recs;
+    v.rank = rank;
+    for (int d = 0; d < kMaxLevels; ++d) {
+        v.level[d] = (d && d <= (int)top) ? lv + level_off[d] : nullptr;
+        v.level_n[d] = d <= (int)top ? level_n[d] : 0;
+    }
+    v.top = top;
+    v.key_bytes = col->key_bytes;
     v.status = col->status;
-    v.N = col->N;
+    v.N = N;
     v.C = C;
-    v.L = col->L;
+    v.L = L;
     v.W = col->W;
     v.ntiles = col->ntiles;
     v.chunk_log2 = col->chunk_log2;
     v.list_mode = col->list_mode;
     if (C) {
-        tile_dir_kernel<<<(unsigned)((col->ntiles + 255) / 256), 256, 0, st>>>(v, col->tiles);
-        if (col->key_bytes == 4) first_key_kernel<uint32_t><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(v, col->chunk_first_key);
-        else first_key_kernel<uint64_t><<<(unsigned)((C + 255) / 256), 256, 0, st>>>(v, col->chunk_first_key);
+        rc = cuda_status(cudaMemsetAsync(col->status + 1, 0, 4, st));
+        if (rc) return rc;
+        tile_dir_kernel<<<(unsigned)((col->ntiles + 255) / 256), 256, 0, st>>>(v, col->tiles, col->status + 1);
+        if (col->key_bytes == 4) rec_kernel<uint32_t><<<(unsigned)C, 128, 0, st>>>(v, recs, rank);
+        else rec_kernel<uint64_t><<<(unsigned)C, 128, 0, st>>>(v, recs, rank);
         note_launch(2);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
+        // rank prefix: popcounts, exclusive scan, scatter
+        const size_t tmpb = scan_tmp_bytes(nw);
+        uint8_t* t = nullptr;
+        if (cudaMallocAsync((void**)&t, al(4 * nw) + al(8 * (nw + 1)) + tmpb, st) != cudaSuccess) return LC_ERR_NOMEM;
+        uint32_t* pop = (uint32_t*)t;
+        uint64_t* before = (uint64_t*)(t + al(4 * nw));
+        const unsigned g = (unsigned)std::min<uint64_t>((nw + 255) / 256, 65535);
+        rank_pop_kernel<<<g, 256, 0, st>>>(rank, nw, pop);
+        note_launch();
+        rc = scan_exclusive(pop, before, nw, ScanOp::Identity, t + al(4 * nw) + al(8 * (nw + 1)), tmpb, st);
+        if (!rc) {
+            rank_before_kernel<<<g, 256, 0, st>>>(rank, nw, before);
+            note_launch();
+            rc = cuda_status(cudaGetLastError());
+        }
+        for (uint32_t d = 1; !rc && d <= top; ++d) {
+            uint64_t stride = 1;
+            for (uint32_t e = 0; e < d; ++e) stride *= 16;
+            const unsigned gl = (unsigned)std::min<uint64_t>((level_n[d] + 255) / 256, 65535);
+            if (col->key_bytes == 4) level_kernel<uint32_t><<<gl, 256, 0, st>>>(v, lv + level_off[d], level_n[d], stride);
+            else level_kernel<uint64_t><<<gl, 256, 0, st>>>(v, lv + level_off[d], level_n[d], stride);
+            note_launch();
+            rc = cuda_status(cudaGetLastError());
+        }
+        cudaFreeAsync(t, st);
+        if (rc) return rc;
+        uint32_t ms = 0;
+        rc = cuda_status(cudaMemcpyAsync(&ms, col->status + 1, 4, cudaMemcpyDeviceToHost, st));
+        if (rc) return rc;
+        rc = cuda_status(cudaStreamSynchronize(st));
+        if (rc) return rc;
+        v.max_tile_segs = std::max<uint32_t>(ms, 1);
+        return LC_OK;
     }
+    v.max_tile_segs = 1;
     return cuda_status(cudaStreamSynchronize(st));
 }
 
@@ -398,11 +529,11 @@ int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out
     int rc;
     if (col->key_bytes == 4) {
         if ((rc = set_smem<uint32_t>())) return rc;
-        decode_kernel<uint32_t><<<(unsigned)nt, kDecThreads, kDecSmem, st>>>(col->view, t0, begin, begin + count,
+        decode_kernel<uint32_t><<<(unsigned)nt, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, t0, begin, begin + count,
                                                                            (uint32_t*)out);
     } else {
         if ((rc = set_smem<uint64_t>())) return rc;
-        decode_kernel<uint64_t><<<(unsigned)nt, kDecThreads, kDecSmem, st>>>(col->view, t0, begin, begin + count,
+        decode_kernel<uint64_t><<<(unsigned)nt, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, t0, begin, begin + count,
                                                                            (uint64_t*)out);
     }
     note_launch();
@@ -429,11 +560,11 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
         const unsigned grid = (unsigned)(sm_count() * 4);
         if (col->key_bytes == 4) {
             if (!(rc = set_smem<uint32_t>()))
-                decode_ranges_kernel<uint32_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off,
+                decode_ranges_kernel<uint32_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off,
                                                                                    m, first, work_off, (uint32_t*)out);
         } else {
             if (!(rc = set_smem<uint64_t>()))
-                decode_ranges_kernel<uint64_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off,
+                decode_ranges_kernel<uint64_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off,
                                                                                    m, first, work_off, (uint64_t*)out);
         }
         if (!rc) {
@@ -456,9 +587,14 @@ int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cud
 
 int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* out, cudaStream_t st) {
     if (m == 0) return LC_OK;
-    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
-    if (col->key_bytes == 4) lower_bound_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, (const uint32_t*)vals, m, out);
-    else lower_bound_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, (const uint64_t*)vals, m, out);
+    const ColView& v = col->view;
+    const uint64_t ntop = v.top ? v.level_n[v.top] : v.L;
+    const size_t smem = 8 * std::max<uint64_t>(ntop, 1);
+    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 6);
+    if (col->key_bytes == 4)
+        lower_bound_kernel<uint32_t><<<grid, 256, smem, st>>>(v, (const uint32_t*)vals, m, out);
+    else
+        lower_bound_kernel<uint64_t><<<grid, 256, smem, st>>>(v, (const uint64_t*)vals, m, out);
     note_launch();
     return cuda_status(cudaGetLastError());
 }
@@ -533,11 +669,11 @@ int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uin
     const unsigned grid = (unsigned)(sm_count() * 4);
     if (col->key_bytes == 4) {
         if ((rc = set_smem<uint32_t>())) return rc;
-        decode_ranges_kernel<uint32_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off, m, first,
+        decode_ranges_kernel<uint32_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off, m, first,
                                                                            work_off, (uint32_t*)out);
     } else {
         if ((rc = set_smem<uint64_t>())) return rc;
-        decode_ranges_kernel<uint64_t><<<grid, kDecThreads, kDecSmem, st>>>(col->view, begin, count, out_off, m, first,
+        decode_ranges_kernel<uint64_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off, m, first,
                                                                            work_off, (uint64_t*)out);
     }
     note_launch();
