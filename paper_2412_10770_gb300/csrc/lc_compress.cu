@@ -3,22 +3,16 @@
 // arithmetic so that the bytes equal those of the CPU definition.
 //
 // Pipeline for C chunks (each chunk is independent: segments never cross one):
-//   fit_kernel    one CTA per chunk.  The chunk is split into 64-key blocks.
-//                 (S) every thread runs the greedy cone from its block's first
-//                 key ("speculative" anchors), following the block's last
-//                 segment past the block end; (F) assuming the true segment that
-//                 enters block k ends where block k-1's speculation says, every
-//                 thread re-walks its block until it meets a speculative anchor
-//                 (from there on the speculation is exact: the greedy from a
-//                 given anchor is deterministic); (R) one warp chains the blocks
-//                 in order, using (S)/(F) whenever their assumption holds and
-//                 walking the cone itself (32 keys per step) otherwise.  Output:
-//                 one anchor bit per key and the segment count per chunk.
+//   spec_kernel   one CTA per 8192-key window; speculative greedy per 32-key
+//                 block (S) and a re-walk from the predicted entry (F), on keys
+//                 staged in shared memory.
+//   chain_kernel  one warp per chunk chains the blocks in order (R): the true
+//                 anchors as one bit per key, and the segment count per chunk.
 //   scan          chunk_seg_begin.
 //   model_kernel  one CTA per chunk.  Every segment's cone is the intersection
 //                 of its keys' slope intervals, so with the anchors known it is a
 //                 segmented max/min over keys (exact rational comparisons, one
-//                 division per segment edge).  Then the slope (floor midpoint),
+//                 division per cone edge).  Then the slope (floor midpoint),
 //                 the width (bit length of the largest zigzag residual) and the
 //                 bit offsets.  Writes the segment arrays of the blob.
 //   scan          chunk_word_begin.
@@ -40,223 +34,294 @@ namespace {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;     // segment end not found within the walk limit
 constexpr uint32_t kInvalid = 0xFFFFFFFEu;  // (F) had no entry point
-constexpr uint32_t kCap = 64;               // (S)/(F) follow a segment at most this far past the block
-constexpr int kFitThreads = 256;
 constexpr int kModelThreads = 256;
 constexpr int kPackThreads = 256;
 constexpr uint32_t kWin = 2048;             // keys per pack window
-constexpr uint32_t kMaxBlocks = kMaxChunk / kBlock;
-constexpr uint32_t kWalkAhead = 8 * 32;     // keys the warp walk prefetches ahead of its step
+constexpr uint32_t kWalkAhead = 32 * 32;    // keys the warp walk prefetches into L2 ahead of its step
 
 template <typename KT>
 __device__ __forceinline__ uint64_t ldk(const KT* __restrict__ K, uint32_t i) {
     return (uint64_t)__ldg(K + i);
 }
 
-// Next anchor after anchor x: the first key that empties the cone, or `limit`
-// if the segment reaches it (n when limit == n, kNone for an earlier limit).
+// The greedy cone (Def. 2, shrinking-cone reading) with a whole warp: each
+// step takes 32 keys (one per lane), an inclusive max/min scan over the lanes of
+// their slope fractions (frac_step's reading, no division) gives the cone after
+// every key, and the first lane whose cone is empty is the next anchor.  The
+// next step's keys are loaded while this step computes; keys further ahead are
+// prefetched into L2.  Called with all 32 lanes active and warp-uniform
+// arguments.
 template <typename KT>
-__device__ uint32_t greedy_end(const KT* __restrict__ K, uint32_t x, uint32_t limit, uint32_t n,
-                               int64_t eps, const uint64_t* __restrict__ magic) {
-    uint64_t kx = ldk(K, x);
-    int64_t LO = INT64_MIN, HI = INT64_MAX;
-    for (uint32_t i = x + 1; i < limit; ++i) {
-        uint64_t D = ldk(K, i) - kx;
-        if (!cone_step(D, i - x, eps, LO, HI, magic)) return i;
-    }
-    return limit >= n ? n : kNone;
-}
-
-// The same greedy with a whole warp: each step tests 32 keys against the cone
-// carried in from the previous step (two line evaluations per key); only keys
-// that move an edge pay for a division, and an inclusive max/min scan over the
-// lanes gives the cone after every key, hence the first key that empties it.
-// Called with all 32 lanes active and warp-uniform arguments.
-template <typename KT>
-__device__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, int64_t eps,
-                              uint32_t lane, const uint64_t* __restrict__ magic) {
+__device__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, int64_t eps, uint32_t lane) {
     const uint64_t kx = ldk(K, x);
-    int64_t LO = INT64_MIN, HI = INT64_MAX;
+    Frac cone = frac_open();
     uint32_t p = x + 1;
+    // the keys of the next four steps are in flight in a register ring
+    uint64_t k1 = p + lane < n ? ldk(K, p + lane) : 0;
+    uint64_t k2 = p + 32 + lane < n ? ldk(K, p + 32 + lane) : 0;
+    uint64_t k3 = p + 64 + lane < n ? ldk(K, p + 64 + lane) : 0;
+    uint64_t k4 = p + 96 + lane < n ? ldk(K, p + 96 + lane) : 0;
     while (p < n) {
         const uint32_t i = p + lane;
-        const bool valid = i < n;
-        const uint32_t d = i - x;
-        // keep the keys of the steps ahead on their way into L2
+        const uint64_t Ki = k1;
+        k1 = k2;
+        k2 = k3;
+        k3 = k4;
+        k4 = i + 128 < n ? ldk(K, i + 128) : 0;
         if (i + kWalkAhead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
-        uint64_t D = valid ? ldk(K, i) - kx : 0;
-        bool fits = false, tlo = false, thi = false;
-        int64_t dlo = 0, dhi = 0;
-        if (valid && D < (1ull << 48)) {
-            dlo = (int64_t)D - eps;
-            dhi = (int64_t)D + eps;
-            const int64_t pl = line_at(LO, d), ph = line_at(HI, d);
-            fits = pl <= dhi && ph >= dlo;
-            tlo = fits && pl < dlo;
-            thi = fits && ph > dhi;
+        const uint32_t d = i - x;
+        const uint64_t D = Ki - kx;
+        // fast path: every key's slope interval contains the carried cone, so the
+        // cone does not move and every key joins
+        {
+            const bool inside = i >= n || (D < ((uint64_t)d << 31) + (uint64_t)eps &&
+                                           !frac_gt((int64_t)D - eps, d, cone.X, cone.E) &&
+                                           (D + (uint64_t)eps + 1) * (uint64_t)cone.F >= cone.Y * (uint64_t)d);
+            if (__all_sync(0xFFFFFFFFu, inside)) {
+                if (p + 32 >= n) return n;
+                p += 32;
+                continue;
+            }
         }
-        const uint32_t failm = __ballot_sync(0xFFFFFFFFu, !fits);
-        const uint32_t ff = failm ? (uint32_t)(__ffs(failm) - 1) : 32u;
-        const uint32_t below = ff >= 32 ? 0xFFFFFFFFu : ((1u << ff) - 1u);
-        const uint32_t need = __ballot_sync(0xFFFFFFFFu, tlo || thi) & below;
-        if (need == 0) {
-            if (ff < 32) return min(p + ff, n);
-            p += 32;
-            continue;
-        }
-        int64_t mylo = INT64_MIN, myhi = INT64_MAX;
-        if (lane < ff) {
-            if (tlo) mylo = ceil_q32(dlo, d, magic);
-            if (thi) myhi = ceil_q32(dhi + 1, d, magic) - 1;
+        // this lane's key as fractions; a key that cannot join pins the lower bound above any upper one
+        Frac v;
+        if (i < n && D < ((uint64_t)d << 31) + (uint64_t)eps) {
+            v.X = (int64_t)D - eps;
+            v.E = d;
+            v.Y = D + (uint64_t)eps + 1;
+            v.F = d;
+        } else {
+            v.X = (1ll << 47) - 1;
+            v.E = 1;
+            v.Y = 1ull << 31;
+            v.F = 1;
         }
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const int64_t a = __shfl_up_sync(0xFFFFFFFFu, mylo, off);
-            const int64_t b = __shfl_up_sync(0xFFFFFFFFu, myhi, off);
+            const int64_t ox = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
+            const uint32_t oe = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
+            const uint64_t oy = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
+            const uint32_t of = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
             if (lane >= (uint32_t)off) {
-                mylo = max(mylo, a);
-                myhi = min(myhi, b);
+                if (frac_gt(ox, oe, v.X, v.E)) { v.X = ox; v.E = oe; }
+                if (oy * (uint64_t)v.F < v.Y * (uint64_t)of) { v.Y = oy; v.F = of; }
             }
         }
-        const int64_t clo = max(LO, mylo), chi = min(HI, myhi);
-        const uint32_t badm = __ballot_sync(0xFFFFFFFFu, lane >= ff || clo > chi);
-        const uint32_t bk = badm ? (uint32_t)(__ffs(badm) - 1) : 32u;
-        if (bk > 0) {
-            LO = __shfl_sync(0xFFFFFFFFu, clo, bk - 1);
-            HI = __shfl_sync(0xFFFFFFFFu, chi, bk - 1);
-        }
-        if (bk < 32) return min(p + bk, n);
+        if (frac_gt(cone.X, cone.E, v.X, v.E)) { v.X = cone.X; v.E = cone.E; }
+        if (cone.Y * (uint64_t)v.F < v.Y * (uint64_t)cone.F) { v.Y = cone.Y; v.F = cone.F; }
+        const uint32_t badm = __ballot_sync(0xFFFFFFFFu, !frac_ok(v));
+        if (badm) return min(p + (uint32_t)(__ffs(badm) - 1), n);
+        cone.X = __shfl_sync(0xFFFFFFFFu, v.X, 31);
+        cone.E = __shfl_sync(0xFFFFFFFFu, v.E, 31);
+        cone.Y = __shfl_sync(0xFFFFFFFFu, v.Y, 31);
+        cone.F = __shfl_sync(0xFFFFFFFFu, v.F, 31);
         p += 32;
     }
     return n;
 }
 
-// ------------------------------------------------------------------ fit
+// ------------------------------------------------------------------ fit: speculation (S) and re-walk (F)
 
+constexpr uint32_t kFB = 32;                    // keys per fit block: one 32-bit word of anchor bits
+constexpr uint32_t kWinKeys = 8192;             // keys per speculation window, one CTA, one block per thread
+constexpr uint32_t kFCap = 32;                  // (S)/(F) follow a segment at most this far past its block
+constexpr int kSpecThreads = kWinKeys / kFB;    // 256
+constexpr uint32_t kStageKeys = kWinKeys + kFB + kFCap;
+constexpr uint32_t kStageSlots = kStageKeys + kStageKeys / 32 + 1;
+constexpr int kChainThreads = 128;              // four chunks per CTA, one warp each
+
+// A window's keys staged in shared memory: local key q sits in slot q + q/32,
+// so that lanes walking 32 consecutive 32-key blocks read distinct banks.
 template <typename KT>
-__global__ void __launch_bounds__(kFitThreads)
-fit_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, uint32_t* __restrict__ tbits,
-           uint32_t* __restrict__ counts, uint32_t* __restrict__ status) {
-    __shared__ uint64_t s_spec[kMaxBlocks];
-    __shared__ uint64_t s_fix[kMaxBlocks];  // (F) anchors; overwritten in place by (R) with the true ones
-    __shared__ uint32_t s_exitS[kMaxBlocks];
-    __shared__ uint32_t s_exitF[kMaxBlocks];
-    __shared__ uint8_t s_sync[kMaxBlocks];
+struct Staged {
+    const KT* s;
+    uint32_t base;
+    __device__ __forceinline__ uint64_t operator()(uint32_t i) const {
+        const uint32_t q = i - base;
+        return (uint64_t)s[q + (q >> 5)];
+    }
+};
 
-    const ChunkDesc cd = chunks[blockIdx.x];
+// One CTA per window of 8192 keys of one chunk (plus one block of left halo
+// and kFCap keys of right halo, all staged in shared memory).
+//   (S) every thread runs the greedy from its block's first key: the
+//       speculative anchors of the block, and the anchor that follows the
+//       block's last segment (exitS, kNone if it runs past kFCap).
+//   (F) every thread assumes the true segment entering its block k ends at
+//       exitS[k-1] and re-walks the greedy from there until it meets a
+//       speculative anchor (the greedy from one anchor is deterministic, so
+//       from there on the speculation is exact); exitF is where the true path
+//       leaves the block under that assumption.
+// Per block: spec, fix (F's anchors before the meeting point), sync (offset of
+// the meeting point, 0xFF if none), exitS, exitF.  Also checks sortedness.
+template <typename KT>
+__global__ void __launch_bounds__(kSpecThreads)
+spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
+            uint32_t* __restrict__ spec_g, uint32_t* __restrict__ fix_g, uint32_t* __restrict__ exitS_g,
+            uint32_t* __restrict__ exitF_g, uint8_t* __restrict__ sync_g, uint32_t* __restrict__ status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ uint32_t s_spec[kSpecThreads + 1], s_exitS[kSpecThreads + 1];
+    const WinDesc wd = wins[blockIdx.x];
+    const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
-    const uint32_t n = cd.n;
+    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
     const int64_t eps = cd.eps;
-    const uint32_t nblk = (n + kBlock - 1) / kBlock;
-    const uint64_t* __restrict__ magic = g_magic;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-
-    // (S) speculative greedy from every block start; also the sortedness check.
+    const uint32_t tid = threadIdx.x;
+    const uint32_t base = w0 >= kFB ? w0 - kFB : 0;
+    const uint32_t top = min(n, w1 + kFCap);
+    KT* s = (KT*)smem;
+    for (uint32_t q = tid; q < top - base; q += kSpecThreads) s[q + (q >> 5)] = __ldg(K + base + q);
+    __syncthreads();
+    const Staged<KT> st{s, base};
     bool unsorted = false;
-    for (uint32_t k = tid; k < nblk; k += kFitThreads) {
-        const uint32_t b = k * kBlock, e = min(b + kBlock, n);
-        if (b == 0 && cd.check_prev) unsorted |= __ldg(K - 1) > __ldg(K);
-        for (uint32_t i = max(b, 1u); i < e; ++i) unsorted |= ldk(K, i - 1) > ldk(K, i);
-        uint64_t mask = 0;
-        uint32_t x = b, ex;
-        for (;;) {
-            mask |= 1ull << (x - b);
-            const uint32_t y = greedy_end(K, x, min(n, e + kCap), n, eps, magic);
-            if (y == kNone || y >= e) {
-                ex = y;
-                break;
-            }
-            x = y;
-        }
-        s_spec[k] = mask;
-        s_exitS[k] = ex;
-    }
+    for (uint32_t i = max(w0, 1u) + tid; i < w1; i += kSpecThreads) unsorted |= st(i - 1) > st(i);
+    if (w0 == 0 && cd.check_prev && tid == 0) unsorted |= __ldg(K - 1) > __ldg(K);
     if (unsorted) atomicOr(status, kStUnsorted);
-    __syncthreads();
 
-    // (F) re-walk block k from the entry that block k-1's speculation predicts,
-    // until a speculative anchor is met.
-    for (uint32_t k = tid; k < nblk; k += kFitThreads) {
-        if (k == 0) {
-            s_fix[0] = 0;
-            s_exitF[0] = kInvalid;
-            s_sync[0] = 0xFF;
-            continue;
-        }
-        uint32_t x = s_exitS[k - 1];
-        if (x == kNone) {
-            s_fix[k] = 0;
-            s_exitF[k] = kInvalid;
-            s_sync[k] = 0xFF;
-            continue;
-        }
-        const uint32_t b = k * kBlock, e = min(b + kBlock, n);
-        const uint64_t sm = s_spec[k];
-        uint64_t fm = 0;
-        uint32_t sync = 0xFF;
-        while (x < e) {
-            if ((sm >> (x - b)) & 1ull) {
-                sync = x - b;
+    const uint32_t kfirst = w0 / kFB - (w0 > 0 ? 1u : 0u);
+    const uint32_t nb = (w1 + kFB - 1) / kFB - kfirst;
+    // (S): one flat loop per block; a key that empties the cone starts the next
+    // segment inside the block, or ends the walk past the block's end
+    for (uint32_t lb = tid; lb < nb; lb += kSpecThreads) {
+        const uint32_t b = (kfirst + lb) * kFB, e = min(b + kFB, n), lim = min(n, e + kFCap);
+        uint32_t mask = 1u, x = b, ex = lim >= n ? n : kNone;
+        uint64_t kx = st(b);
+        Frac cone = frac_open();
+        for (uint32_t i = b + 1; i < lim; ++i) {
+            const uint64_t Ki = st(i);
+            if (frac_step(Ki - kx, i - x, eps, cone)) continue;
+            if (i >= e) {
+                ex = i;
                 break;
             }
-            fm |= 1ull << (x - b);
-            x = greedy_end(K, x, min(n, e + kCap), n, eps, magic);
-            if (x == kNone) break;
+            mask |= 1u << (i - b);
+            x = i;
+            kx = Ki;
+            cone = frac_open();
         }
-        s_fix[k] = fm;
-        s_sync[k] = (uint8_t)sync;
-        s_exitF[k] = sync != 0xFF ? s_exitS[k] : x;
+        s_spec[lb] = mask;
+        s_exitS[lb] = ex;
     }
     __syncthreads();
-
-    // (R) chain the blocks in order: the true anchors.
-    if (warp == 0) {
-        uint32_t x = 0, total = 0;
-        for (uint32_t k = 0; k < nblk; ++k) {
-            const uint32_t b = k * kBlock, e = min(b + kBlock, n);
-            uint64_t mask = 0;
-            if (x < e) {
-                uint32_t xn;
-                if (k == 0) {
-                    mask = s_spec[0];
-                    xn = s_exitS[0];
-                } else if (x == s_exitS[k - 1] && s_exitF[k] != kInvalid) {
-                    mask = s_fix[k];
-                    const uint32_t so = s_sync[k];
-                    if (so != 0xFF) mask |= s_spec[k] & (~0ull << so);
-                    xn = s_exitF[k];
-                } else {
-                    const uint64_t sm = s_spec[k];
-                    xn = x;
-                    while (xn < e) {
-                        if ((sm >> (xn - b)) & 1ull) {
-                            mask |= sm & (~0ull << (xn - b));
-                            xn = s_exitS[k];
-                            break;
-                        }
-                        mask |= 1ull << (xn - b);
-                        xn = warp_walk(K, xn, n, eps, lane, magic);
+    // (F): from the entry block k-1 predicts, until a speculative anchor
+    for (uint32_t lb = (w0 > 0 ? 1u : 0u) + tid; lb < nb; lb += kSpecThreads) {
+        const uint32_t k = kfirst + lb;
+        const uint32_t b = k * kFB, e = min(b + kFB, n), lim = min(n, e + kFCap);
+        const uint32_t x0 = k == 0 ? 0u : s_exitS[lb - 1];
+        uint32_t fm = 0, sync = 0xFF, exf;
+        if (x0 == kNone) {
+            exf = kInvalid;
+        } else if (x0 >= e) {
+            exf = x0;  // the entering segment covers the whole block
+        } else {
+            const uint32_t sm = s_spec[lb];
+            exf = lim >= n ? n : kNone;
+            if ((sm >> (x0 - b)) & 1u) {
+                sync = x0 - b;
+            } else {
+                fm = 1u << (x0 - b);
+                uint32_t x = x0;
+                uint64_t kx = st(x0);
+                Frac cone = frac_open();
+                for (uint32_t i = x0 + 1; i < lim; ++i) {
+                    const uint64_t Ki = st(i);
+                    if (frac_step(Ki - kx, i - x, eps, cone)) continue;
+                    if (i >= e) {
+                        exf = i;
+                        break;
                     }
+                    if ((sm >> (i - b)) & 1u) {
+                        sync = i - b;
+                        break;
+                    }
+                    fm |= 1u << (i - b);
+                    x = i;
+                    kx = Ki;
+                    cone = frac_open();
                 }
-                if (xn == kNone) {
-                    const uint32_t la = b + 63u - (uint32_t)__clzll((long long)mask);
-                    xn = warp_walk(K, la, n, eps, lane, magic);
-                }
-                x = xn;
             }
-            __syncwarp();
-            if (lane == 0) s_fix[k] = mask;
-            total += __popcll(mask);
+            if (sync != 0xFF) exf = s_exitS[lb];
         }
-        if (lane == 0) counts[blockIdx.x] = total;
+        const uint64_t g = cd.bitword_begin + k;
+        spec_g[g] = s_spec[lb];
+        exitS_g[g] = s_exitS[lb];
+        fix_g[g] = fm;
+        sync_g[g] = (uint8_t)sync;
+        exitF_g[g] = exf;
     }
-    __syncthreads();
+}
 
-    // anchor bitmap of the chunk, 32 bits per word
-    uint32_t* __restrict__ T = tbits + cd.bitword_begin;
-    const uint32_t nwords = (n + 31) / 32;
-    for (uint32_t wd = tid; wd < nwords; wd += kFitThreads)
-        T[wd] = (uint32_t)(s_fix[wd >> 1] >> (32 * (wd & 1u)));
+// ------------------------------------------------------------------ fit: the true chain (R)
+
+// One warp per chunk follows the true anchors block by block.  Where the true
+// path enters block k exactly at exitS[k-1], (F) already holds the answer for
+// block k, and block k+1's assumption holds too iff exitF[k] == exitS[k]; so a
+// ballot over 32 blocks takes the whole run of consistent blocks at once.
+// Elsewhere the warp walks the cone itself (32 keys per step) until it meets a
+// speculative anchor.  Output: the chunk's anchor bitmap and segment count.
+template <typename KT>
+__global__ void __launch_bounds__(kChainThreads)
+chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, uint64_t C,
+             const uint32_t* __restrict__ spec_g, const uint32_t* __restrict__ fix_g,
+             const uint32_t* __restrict__ exitS_g, const uint32_t* __restrict__ exitF_g,
+             const uint8_t* __restrict__ sync_g, uint32_t* __restrict__ tbits, uint32_t* __restrict__ counts) {
+    const uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= C) return;  // whole warps leave together
+    const uint32_t lane = threadIdx.x & 31u;
+    const ChunkDesc cd = chunks[c];
+    const KT* __restrict__ K = keys + cd.key_begin;
+    const uint32_t n = cd.n, nblk = (n + kFB - 1) / kFB;
+    const int64_t eps = cd.eps;
+    const uint64_t gb = cd.bitword_begin;
+    uint32_t* __restrict__ T = tbits + gb;
+    uint32_t x = 0, knext = 0, total = 0;
+    while (x < n) {
+        const uint32_t k = x / kFB;
+        for (uint32_t q = knext + lane; q < k; q += 32) T[q] = 0;
+        const bool entry_ok = k == 0 ? x == 0 : x == __ldg(exitS_g + gb + k - 1);
+        if (entry_ok) {
+            const uint32_t kb = k + lane;
+            const bool valid = kb < nblk;
+            uint32_t eS = kNone, eF = kInvalid, m = 0;
+            if (valid) {
+                eS = __ldg(exitS_g + gb + kb);
+                eF = __ldg(exitF_g + gb + kb);
+                const uint32_t so = __ldg(sync_g + gb + kb);
+                m = __ldg(fix_g + gb + kb) | (so != 0xFF ? __ldg(spec_g + gb + kb) & (0xFFFFFFFFu << so) : 0u);
+            }
+            const uint32_t okm = __ballot_sync(0xFFFFFFFFu, valid && eF == eS && eF != kNone);
+            const uint32_t nvalid = __popc(__ballot_sync(0xFFFFFFFFu, valid));
+            uint32_t r = ~okm ? (uint32_t)__ffs(~okm) : 32u;  // lanes 0..r-1 follow one another
+            r = min(r, nvalid);
+            if (lane < r) T[kb] = m;
+            total += __reduce_add_sync(0xFFFFFFFFu, lane < r ? (uint32_t)__popc(m) : 0u);
+            uint32_t xl = __shfl_sync(0xFFFFFFFFu, eF, r - 1);
+            const uint32_t ml = __shfl_sync(0xFFFFFFFFu, m, r - 1);
+            if (xl == kNone) xl = warp_walk(K, (k + r - 1) * kFB + 31u - (uint32_t)__clz(ml), n, eps, lane);
+            knext = k + r;
+            x = xl;
+        } else {
+            const uint32_t b = k * kFB, e = min(b + kFB, n);
+            const uint32_t sm = __ldg(spec_g + gb + k);
+            uint32_t m = 0, xn = x;
+            while (xn < e) {
+                if ((sm >> (xn - b)) & 1u) {
+                    m |= sm & (0xFFFFFFFFu << (xn - b));
+                    xn = __ldg(exitS_g + gb + k);
+                    if (xn == kNone) xn = warp_walk(K, b + 31u - (uint32_t)__clz(m), n, eps, lane);
+                    break;
+                }
+                m |= 1u << (xn - b);
+                xn = warp_walk(K, xn, n, eps, lane);
+            }
+            if (lane == 0) T[k] = m;
+            total += __popc(m);
+            knext = k + 1;
+            x = xn;
+        }
+    }
+    for (uint32_t q = knext + lane; q < nblk; q += 32) T[q] = 0;
+    if (lane == 0) counts[c] = total;
 }
 
 // ------------------------------------------------------------------ block scans
@@ -314,15 +379,6 @@ struct Cone {
     uint32_t has;
 };
 
-__device__ __forceinline__ void cone_add(Cone& c, int64_t xl, uint64_t yh, uint32_t d) {
-    if (!c.has) {
-        c.X = xl; c.E = d; c.Y = yh; c.F = d; c.has = 1;
-        return;
-    }
-    if (xl * (int64_t)c.E > c.X * (int64_t)d) { c.X = xl; c.E = d; }
-    if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { c.Y = yh; c.F = d; }
-}
-
 __device__ __forceinline__ void cone_merge(Cone& c, const Cone& o) {
     if (!o.has) return;
     if (!c.has) { c = o; return; }
@@ -344,212 +400,335 @@ __device__ __forceinline__ int64_t cone_slope(const Cone& c, const uint64_t* __r
 
 __device__ __forceinline__ bool tbit(const uint32_t* s_T, uint32_t i) { return (s_T[i >> 5] >> (i & 31u)) & 1u; }
 
-// First anchor strictly after position a (n if none), scanning words.
-__device__ __forceinline__ uint32_t next_anchor(const uint32_t* s_T, uint32_t a, uint32_t n) {
-    uint32_t i = a + 1;
-    if (i >= n) return n;
-    uint32_t wd = i >> 5;
-    uint32_t bits = s_T[wd] & (0xFFFFFFFFu << (i & 31u));
-    const uint32_t nw = (n + 31) >> 5;
-    while (!bits) {
-        if (++wd >= nw) return n;
-        bits = s_T[wd];
-    }
-    return min(n, wd * 32u + (uint32_t)(__ffs(bits) - 1));
+__device__ __forceinline__ Cone shfl_up_cone(const Cone& v, int off) {
+    Cone u;
+    u.X = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
+    u.Y = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
+    u.E = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
+    u.F = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
+    u.has = __shfl_up_sync(0xFFFFFFFFu, v.has, off);
+    return u;
 }
 
+// Merge of one Cone per lane into every lane (butterfly).
+__device__ __forceinline__ Cone warp_reduce_cone(Cone v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        Cone u;
+        u.X = __shfl_xor_sync(0xFFFFFFFFu, v.X, m);
+        u.Y = __shfl_xor_sync(0xFFFFFFFFu, v.Y, m);
+        u.E = __shfl_xor_sync(0xFFFFFFFFu, v.E, m);
+        u.F = __shfl_xor_sync(0xFFFFFFFFu, v.F, m);
+        u.has = __shfl_xor_sync(0xFFFFFFFFu, v.has, m);
+        cone_merge(v, u);
+    }
+    return v;
+}
+
+__device__ __forceinline__ Cone shfl_cone(const Cone& v, int src) {
+    Cone u;
+    u.X = __shfl_sync(0xFFFFFFFFu, v.X, src);
+    u.Y = __shfl_sync(0xFFFFFFFFu, v.Y, src);
+    u.E = __shfl_sync(0xFFFFFFFFu, v.E, src);
+    u.F = __shfl_sync(0xFFFFFFFFu, v.F, src);
+    u.has = __shfl_sync(0xFFFFFFFFu, v.has, src);
+    return u;
+}
+
+// One CTA per chunk, eight warps, warp w on keys [w R, (w+1) R).  A warp steps
+// through its keys 32 at a time (lane = key, coalesced loads) carrying the open
+// segment across steps.  Pass 1: a segmented scan over the lanes (boundaries at
+// the anchors) of the exact rational extremes max (D-eps)/d and
+// min (D+eps+1)/d gives each segment's cone at its last key, hence its slope.
+// Pass 2: the same scan over the zigzag residuals gives each width.  A segment
+// still open at the end of a warp's keys (its "head") is finished from the
+// first pieces of the following warps.  Pass 3: the bit offsets, a scan over
+// the chunk's segments.
 template <typename KT>
 __global__ void __launch_bounds__(kModelThreads)
 model_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks,
              const uint32_t* __restrict__ tbits, const uint64_t* __restrict__ csb, KT* __restrict__ icpt,
              int64_t* __restrict__ slope, uint32_t* __restrict__ bitoff, uint16_t* __restrict__ start,
              uint8_t* __restrict__ width, uint32_t* __restrict__ chunk_bits) {
-    __shared__ uint32_t s_T[kMaxChunk / 32];
-    __shared__ Cone s_part[kModelThreads];
-    __shared__ Cone s_head[kModelThreads];
-    __shared__ uint32_t s_head_anchor[kModelThreads], s_head_end[kModelThreads], s_cnt[kModelThreads];
-    __shared__ uint64_t s_head_rank[kModelThreads];
-    __shared__ int64_t s_head_M[kModelThreads];
-    __shared__ uint32_t s_part_z[kModelThreads], s_head_z[kModelThreads];
-    __shared__ uint32_t s_warp_u32[32];
-    __shared__ int32_t s_warp_i32[32];
+    constexpr uint32_t NW = kModelThreads / 32;
+    __shared__ uint32_t s_T[kMaxChunk / 32 + 1];
+    __shared__ Cone s_part[NW], s_head[NW];
+    __shared__ uint32_t s_cnt[NW], s_head_anchor[NW], s_part_z[NW], s_head_z[NW];
+    __shared__ int32_t s_last[NW];
+    __shared__ uint64_t s_head_rank[NW], s_head_ka[NW];
+    __shared__ int64_t s_head_M[NW];
+    __shared__ uint32_t s_scan[32];
 
     const ChunkDesc cd = chunks[blockIdx.x];
     const KT* __restrict__ K = keys + cd.key_begin;
     const uint32_t n = cd.n;
     const int64_t eps = cd.eps;
     const uint64_t* __restrict__ magic = g_magic;
-    const uint32_t tid = threadIdx.x;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
     const uint32_t nwords = (n + 31) / 32;
-    for (uint32_t wd = tid; wd < nwords; wd += kModelThreads) s_T[wd] = tbits[cd.bitword_begin + wd];
+    for (uint32_t q = tid; q < nwords; q += kModelThreads) s_T[q] = tbits[cd.bitword_begin + q];
+    if (tid == 0) s_T[nwords] = 0;
+    const uint32_t R = ((n + NW * 32 - 1) / (NW * 32)) * 32;
+    const uint32_t r0 = min(n, w * R), r1 = min(n, r0 + R);
     __syncthreads();
+    {
+        uint32_t cnt = 0;
+        int32_t last = -1;
+        for (uint32_t q = (r0 >> 5) + lane; q < ((r1 + 31) >> 5); q += 32) {
+            const uint32_t bits = s_T[q];
+            cnt += __popc(bits);
+            if (bits) last = max(last, (int32_t)(q * 32 + 31 - __clz(bits)));
+        }
+        cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        last = __reduce_max_sync(0xFFFFFFFFu, last);
+        if (lane == 0) {
+            s_cnt[w] = cnt;
+            s_last[w] = last;
+            s_part[w].has = 0;
+            s_head_anchor[w] = kNone;
+            s_part_z[w] = 0;
+            s_head_z[w] = 0;
+        }
+    }
+    __syncthreads();
+    uint32_t before = 0;
+    int32_t prev = -1;
+    for (uint32_t u = 0; u < w; ++u) {
+        before += s_cnt[u];
+        prev = max(prev, s_last[u]);
+    }
     const uint64_t seg0 = csb[blockIdx.x];
+    const bool empty = r0 >= r1;
+    const bool foreign0 = !empty && !tbit(s_T, r0);
+    const uint32_t a_first = foreign0 ? (uint32_t)prev : r0;
+    const uint64_t ka_first = foreign0 ? ldk(K, a_first) : 0;
 
-    // runs of R keys (a multiple of 32) per thread
-    const uint32_t per = (n + kModelThreads - 1) / kModelThreads;
-    const uint32_t R = ((per + 31) / 32) * 32;
-    const uint32_t r0 = min(n, tid * R), r1 = min(n, r0 + R);
-    uint32_t cnt = 0;
-    int32_t last = -1;
-    for (uint32_t wd = r0 >> 5; wd < (r1 + 31) >> 5; ++wd) {
-        const uint32_t bits = s_T[wd];
-        cnt += __popc(bits);
-        if (bits) last = (int32_t)(wd * 32 + 31 - __clz(bits));
-    }
-    s_cnt[tid] = cnt;
-    uint32_t rank_total;
-    const uint32_t rank_base = block_excl_scan<uint32_t>(cnt, AddOp(), 0u, s_warp_u32, &rank_total);
-    const int32_t prev_anchor = block_excl_scan<int32_t>(last, MaxOp(), -1, s_warp_i32, nullptr);
-
-    const bool run_empty = r0 >= r1;
-    const bool starts_with_anchor = !run_empty && tbit(s_T, r0);
-    const uint32_t a0 = starts_with_anchor ? r0 : (uint32_t)max(prev_anchor, 0);
-    const uint64_t j0 = seg0 + (starts_with_anchor ? rank_base : rank_base - 1);
-
-    // pass 1: cones
-    Cone c{0, 0, 0, 0, 0};
-    uint32_t cur_a = a0;
-    uint64_t cur_j = j0;
-    uint64_t ka = run_empty ? 0 : ldk(K, a0);
-    bool first_piece = !starts_with_anchor;
-    s_part[tid].has = 0;
-    s_head[tid].has = 0;
-    s_head_anchor[tid] = kNone;
-    for (uint32_t i = r0; i < r1; ++i) {
-        if (tbit(s_T, i)) {
-            if (i != r0) {  // close the piece that ends here: complete unless it began before the run
-                if (first_piece) {
-                    s_part[tid] = c;
-                } else {
-                    slope[cur_j] = cone_slope(c, magic);
-                    start[cur_j] = (uint16_t)cur_a;
-                    icpt[cur_j] = (KT)ka;
+    // pass 1: cones and slopes
+    {
+        uint32_t a_c = a_first;
+        uint64_t ka_c = ka_first;
+        bool foreign = foreign0, open = false;
+        Cone cc{0, 0, 0, 0, 0};
+        uint64_t rank_p = seg0 + before;
+        Cone acc{0, 0, 0, 0, 0};  // per-lane part of the open segment from steps without anchors
+        bool acc_used = false;
+        uint64_t Kn = r0 + lane < r1 ? ldk(K, r0 + lane) : 0;
+        for (uint32_t p = r0; p < r1; p += 32) {
+            const uint32_t i = p + lane;
+            const bool in = i < r1;
+            const uint64_t Ki = Kn;  // loaded during the previous step
+            if (i + 32 < r1) Kn = ldk(K, i + 32);
+            if (i + kWalkAhead < r1) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
+            uint32_t word = s_T[p >> 5];
+            if (r1 - p < 32) word &= (1u << (r1 - p)) - 1u;
+            const bool ends = in && (i + 1 >= n || tbit(s_T, i + 1));
+            if (word == 0 && !__any_sync(0xFFFFFFFFu, ends)) {
+                // no segment starts or ends here: each lane folds its own key
+                if (in) {
+                    const uint64_t D = Ki - ka_c;
+                    Cone u;
+                    u.X = (int64_t)D - eps;
+                    u.Y = D + (uint64_t)eps + 1;
+                    u.E = u.F = i - a_c;
+                    u.has = 1;
+                    cone_merge(acc, u);
                 }
-                ++cur_j;
+                acc_used = true;
+                continue;
             }
-            cur_a = i;
-            ka = ldk(K, i);
-            c.has = 0;
-            first_piece = false;
-            continue;
+            if (acc_used) {
+                cone_merge(cc, warp_reduce_cone(acc));
+                acc.has = 0;
+                acc_used = false;
+            }
+            const bool isa = (word >> lane) & 1u;
+            const uint32_t le = word & (0xFFFFFFFFu >> (31u - lane));
+            const int hl = le ? 31 - __clz(le) : -1;
+            const uint64_t kh = __shfl_sync(0xFFFFFFFFu, Ki, hl >= 0 ? hl : (int)lane);
+            const uint64_t ka = hl >= 0 ? kh : ka_c;
+            const uint32_t a = hl >= 0 ? p + (uint32_t)hl : a_c;
+            Cone v{0, 0, 0, 0, 0};
+            if (in && !isa) {
+                const uint64_t D = Ki - ka;
+                v.X = (int64_t)D - eps;
+                v.Y = D + (uint64_t)eps + 1;
+                v.E = v.F = i - a;
+                v.has = 1;
+            }
+            const uint32_t seg_lo = hl >= 0 ? (uint32_t)hl : 0u;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const Cone u = shfl_up_cone(v, off);
+                if (lane >= (uint32_t)off && lane - off >= seg_lo) cone_merge(v, u);
+            }
+            if (hl < 0) cone_merge(v, cc);
+            if (ends) {
+                if (hl < 0 && foreign) {
+                    s_part[w] = v;
+                } else {
+                    const uint64_t j = hl >= 0 ? rank_p + __popc(le) - 1 : rank_p - 1;
+                    slope[j] = cone_slope(v, magic);
+                    start[j] = (uint16_t)a;
+                    icpt[j] = (KT)ka;
+                }
+            }
+            const int ll = (int)min(31u, r1 - p - 1);
+            const bool end_ll = __shfl_sync(0xFFFFFFFFu, ends, ll);
+            const int hll = __shfl_sync(0xFFFFFFFFu, hl, ll);
+            const Cone vl = shfl_cone(v, ll);
+            const uint64_t kal = __shfl_sync(0xFFFFFFFFu, ka, ll);
+            if (hll >= 0) {
+                foreign = false;
+                a_c = p + (uint32_t)hll;
+                ka_c = kal;
+            } else if (end_ll) {
+                foreign = false;
+            }
+            if (end_ll) cc.has = 0;
+            else cc = vl;
+            rank_p += __popc(word);
+            open = !end_ll;
         }
-        const uint64_t D = ldk(K, i) - ka;
-        cone_add(c, (int64_t)D - eps, D + (uint64_t)eps + 1, i - cur_a);
-    }
-    if (!run_empty) {
-        if (first_piece) {
-            s_part[tid] = c;
-        } else if (r1 == n || tbit(s_T, r1)) {
-            slope[cur_j] = cone_slope(c, magic);
-            start[cur_j] = (uint16_t)cur_a;
-            icpt[cur_j] = (KT)ka;
-        } else {
-            s_head[tid] = c;
-            s_head_anchor[tid] = cur_a;
-            s_head_rank[tid] = cur_j;
+        if (acc_used) {
+            cone_merge(cc, warp_reduce_cone(acc));
+            open = true;
+        }
+        if (lane == 0 && open) {
+            if (foreign) {
+                s_part[w] = cc;
+            } else {
+                s_head[w] = cc;
+                s_head_anchor[w] = a_c;
+                s_head_rank[w] = rank_p - 1;
+                s_head_ka[w] = ka_c;
+            }
         }
     }
     __syncthreads();
-
-    // heads: fold the pieces of the following runs that the segment spans
     const uint32_t nruns = (n + R - 1) / R;
-    if (s_head_anchor[tid] != kNone) {
+    if (tid < NW && s_head_anchor[tid] != kNone) {
         Cone h = s_head[tid];
         uint32_t u = tid + 1;
         for (; u < nruns; ++u) {
             cone_merge(h, s_part[u]);
             if (s_cnt[u] > 0) break;
         }
-        const uint32_t a = s_head_anchor[tid];
-        const uint32_t end = u < nruns ? next_anchor(s_T, u * R - 1, n) : n;
-        s_head_end[tid] = end;
         const int64_t M = cone_slope(h, magic);
-        s_head_M[tid] = M;
         const uint64_t j = s_head_rank[tid];
         slope[j] = M;
-        start[j] = (uint16_t)a;
-        icpt[j] = (KT)ldk(K, a);
+        start[j] = (uint16_t)s_head_anchor[tid];
+        icpt[j] = (KT)s_head_ka[tid];
+        s_head_M[tid] = M;
     }
     __syncthreads();
 
-    // pass 2: residual widths
-    uint32_t owned_bits = 0;
+    // pass 2: widths
     {
-        cur_a = a0;
-        cur_j = j0;
-        ka = run_empty ? 0 : ldk(K, a0);
-        int64_t M = 0;
-        if (!run_empty) M = starts_with_anchor ? slope[j0] : s_head_M[a0 / R];
-        first_piece = !starts_with_anchor;
-        uint32_t zmax = 0;
-        s_part_z[tid] = 0;
-        s_head_z[tid] = 0;
-        for (uint32_t i = r0; i < r1; ++i) {
-            if (tbit(s_T, i)) {
-                if (i != r0) {
-                    if (first_piece) {
-                        s_part_z[tid] = zmax;
-                    } else {
-                        const uint32_t w = 32u - __clz(zmax);
-                        width[cur_j] = (uint8_t)w;
-                        owned_bits += w * (i - cur_a - 1);
-                    }
-                    ++cur_j;
-                }
-                cur_a = i;
-                ka = ldk(K, i);
-                first_piece = false;
-                zmax = 0;
-                // the slope of the segment starting here: its own (complete) or this run's head
-                M = (s_head_anchor[tid] == i) ? s_head_M[tid] : slope[cur_j];
+        uint32_t a_c = a_first;
+        uint64_t ka_c = ka_first;
+        int64_t M_c = foreign0 ? s_head_M[a_first / R] : 0;
+        bool foreign = foreign0, open = false;
+        uint32_t z_c = 0;
+        const uint32_t my_head = s_head_anchor[w];
+        uint64_t rank_p = seg0 + before;
+        uint32_t zacc = 0;
+        bool acc_used = false;
+        uint64_t Kn = r0 + lane < r1 ? ldk(K, r0 + lane) : 0;
+        for (uint32_t p = r0; p < r1; p += 32) {
+            const uint32_t i = p + lane;
+            const bool in = i < r1;
+            const uint64_t Ki = Kn;  // loaded during the previous step
+            if (i + 32 < r1) Kn = ldk(K, i + 32);
+            if (i + kWalkAhead < r1) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
+            uint32_t word = s_T[p >> 5];
+            if (r1 - p < 32) word &= (1u << (r1 - p)) - 1u;
+            const bool ends = in && (i + 1 >= n || tbit(s_T, i + 1));
+            if (word == 0 && !__any_sync(0xFFFFFFFFu, ends)) {
+                if (in) zacc = max(zacc, zigzag32((int64_t)(Ki - ka_c) - line_at(M_c, i - a_c)));
+                acc_used = true;
                 continue;
             }
-            const uint64_t D = ldk(K, i) - ka;
-            const int64_t r = (int64_t)D - line_at(M, i - cur_a);
-            zmax = max(zmax, zigzag32(r));
-        }
-        if (!run_empty && first_piece) s_part_z[tid] = zmax;
-        if (!run_empty && !first_piece) {
-            if (r1 == n || tbit(s_T, r1)) {
-                const uint32_t w = 32u - __clz(zmax);
-                width[cur_j] = (uint8_t)w;
-                owned_bits += w * (r1 - cur_a - 1);
-            } else {
-                s_head_z[tid] = zmax;
+            if (acc_used) {
+                z_c = max(z_c, __reduce_max_sync(0xFFFFFFFFu, zacc));
+                zacc = 0;
+                acc_used = false;
             }
+            const bool isa = (word >> lane) & 1u;
+            const uint32_t le = word & (0xFFFFFFFFu >> (31u - lane));
+            const int hl = le ? 31 - __clz(le) : -1;
+            const uint64_t kh = __shfl_sync(0xFFFFFFFFu, Ki, hl >= 0 ? hl : (int)lane);
+            const uint64_t ka = hl >= 0 ? kh : ka_c;
+            const uint32_t a = hl >= 0 ? p + (uint32_t)hl : a_c;
+            const uint64_t j = hl >= 0 ? rank_p + __popc(le) - 1 : rank_p - 1;
+            int64_t M = M_c;
+            if (hl >= 0) M = a == my_head ? s_head_M[w] : slope[j];
+            uint32_t z = (in && !isa) ? zigzag32((int64_t)(Ki - ka) - line_at(M, i - a)) : 0u;
+            const uint32_t seg_lo = hl >= 0 ? (uint32_t)hl : 0u;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, z, off);
+                if (lane >= (uint32_t)off && lane - off >= seg_lo) z = max(z, u);
+            }
+            if (hl < 0) z = max(z, z_c);
+            if (ends) {
+                if (hl < 0 && foreign) s_part_z[w] = z;
+                else width[j] = (uint8_t)(32u - __clz(z));
+            }
+            const int ll = (int)min(31u, r1 - p - 1);
+            const bool end_ll = __shfl_sync(0xFFFFFFFFu, ends, ll);
+            const int hll = __shfl_sync(0xFFFFFFFFu, hl, ll);
+            const uint32_t zl = __shfl_sync(0xFFFFFFFFu, z, ll);
+            const int64_t Ml = __shfl_sync(0xFFFFFFFFu, M, ll);
+            const uint64_t kal = __shfl_sync(0xFFFFFFFFu, ka, ll);
+            if (hll >= 0) {
+                foreign = false;
+                a_c = p + (uint32_t)hll;
+                ka_c = kal;
+                M_c = Ml;
+            } else if (end_ll) {
+                foreign = false;
+            }
+            z_c = end_ll ? 0u : zl;
+            rank_p += __popc(word);
+            open = !end_ll;
+        }
+        if (acc_used) {
+            z_c = max(z_c, __reduce_max_sync(0xFFFFFFFFu, zacc));
+            open = true;
+        }
+        if (lane == 0 && open) {
+            if (foreign) s_part_z[w] = z_c;
+            else s_head_z[w] = z_c;
         }
     }
     __syncthreads();
-    if (s_head_anchor[tid] != kNone) {
-        uint32_t zmax = s_head_z[tid];
+    if (tid < NW && s_head_anchor[tid] != kNone) {
+        uint32_t z = s_head_z[tid];
         for (uint32_t u = tid + 1; u < nruns; ++u) {
-            zmax = max(zmax, s_part_z[u]);
+            z = max(z, s_part_z[u]);
             if (s_cnt[u] > 0) break;
         }
-        const uint32_t w = 32u - __clz(zmax);
-        width[s_head_rank[tid]] = (uint8_t)w;
-        owned_bits += w * (s_head_end[tid] - s_head_anchor[tid] - 1);
+        width[s_head_rank[tid]] = (uint8_t)(32u - __clz(z));
     }
+    __syncthreads();
 
-    // bit offsets: exclusive scan of the bits of the segments each run owns
-    uint32_t total_bits;
-    uint32_t bit = block_excl_scan<uint32_t>(owned_bits, AddOp(), 0u, s_warp_u32, &total_bits);
-    if (!run_empty) {
-        uint64_t j = starts_with_anchor ? j0 : j0 + 1;
-        for (uint32_t wd = r0 >> 5; wd < (r1 + 31) >> 5; ++wd) {
-            uint32_t bits = s_T[wd];
-            while (bits) {
-                const uint32_t a = wd * 32 + (uint32_t)(__ffs(bits) - 1);
-                bits &= bits - 1;
-                if (a < r0 || a >= r1) continue;
-                const uint32_t end = (s_head_anchor[tid] == a) ? s_head_end[tid] : next_anchor(s_T, a, n);
-                bitoff[j] = bit;
-                bit += (uint32_t)width[j] * (end - a - 1);
-                ++j;
-            }
+    // pass 3: bit offsets of the chunk's segments, in order
+    const uint64_t s1 = csb[blockIdx.x + 1];
+    uint32_t carry = 0;
+    for (uint64_t b0 = seg0; b0 < s1; b0 += kModelThreads) {
+        const uint64_t j = b0 + tid;
+        uint32_t bits = 0;
+        if (j < s1) {
+            const uint32_t st = start[j];
+            const uint32_t en = j + 1 < s1 ? (uint32_t)start[j + 1] : n;
+            bits = (uint32_t)width[j] * (en - st - 1);
         }
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan<uint32_t>(bits, AddOp(), 0u, s_scan, &tot);
+        if (j < s1) bitoff[j] = carry + ex;
+        carry += tot;
     }
-    if (tid == 0) chunk_bits[blockIdx.x] = total_bits;
+    if (tid == 0) chunk_bits[blockIdx.x] = carry;
 }
 
 // ------------------------------------------------------------------ pack
@@ -741,15 +920,33 @@ static int ensure_magic(int dev) {
     return LC_OK;
 }
 
+struct FitScratch {
+    const WinDesc* wins;
+    uint64_t nwins;
+    uint32_t *spec, *fix, *exitS, *exitF;
+    uint8_t* sync;
+};
+
 template <typename KT>
-static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, uint32_t* tbits, uint32_t* counts,
-                        uint64_t* csb, uint32_t* status, void* tmp, size_t tmp_bytes, lc_column* col,
-                        cudaStream_t st, int stage) {
+static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, const FitScratch& fs, uint32_t* tbits,
+                        uint32_t* counts, uint64_t* csb, uint32_t* status, void* tmp, size_t tmp_bytes,
+                        lc_column* col, cudaStream_t st, int stage) {
     uint8_t* blob = col->blob;
     const Layout& lay = col->lay;
     if (stage == 0) {
-        fit_kernel<KT><<<(unsigned)C, kFitThreads, 0, st>>>(keys, chunks_d, tbits, counts, status);
-        note_launch();
+        static bool attr[2] = {false, false};
+        const size_t smem = sizeof(KT) * kStageSlots;
+        if (!attr[sizeof(KT) == 8]) {
+            int rc = cuda_status(
+                cudaFuncSetAttribute(spec_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (rc) return rc;
+            attr[sizeof(KT) == 8] = true;
+        }
+        spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.fix,
+                                                                        fs.exitS, fs.exitF, fs.sync, status);
+        chain_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0, st>>>(
+            keys, chunks_d, C, fs.spec, fs.fix, fs.exitS, fs.exitF, fs.sync, tbits, counts);
+        note_launch(2);
         int rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         return scan_exclusive(counts, csb, C, ScanOp::Identity, tmp, tmp_bytes, st);
@@ -774,11 +971,20 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
                   uint64_t payload_bound_words, cudaStream_t st, lc_column* col) {
     int rc = ensure_magic(col->device);
     if (rc) return rc;
-    // scratch: chunk table, anchor bitmap, per-chunk counts, scan partials, status, csb
+    // windows of the speculation kernel
+    std::vector<WinDesc> wins;
+    for (uint64_t c = 0; c < C; ++c)
+        for (uint32_t off = 0; off < chunks_h[c].n; off += kWinKeys) wins.push_back(WinDesc{(uint32_t)c, off});
+    const uint64_t nwins = wins.size();
+    // scratch: chunk table, windows, per-block fit state, anchor bitmap,
+    // per-chunk counts, scan partials, status, chunk_seg_begin
     const size_t tmp_bytes = scan_tmp_bytes(C);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t off_chunks = 0;
-    const size_t off_bits = al(off_chunks + C * sizeof(ChunkDesc));
+    const size_t off_wins = al(off_chunks + C * sizeof(ChunkDesc));
+    const size_t off_blk = al(off_wins + nwins * sizeof(WinDesc));
+    const size_t off_sync = al(off_blk + 4 * 4 * bitwords);
+    const size_t off_bits = al(off_sync + bitwords);
     const size_t off_counts = al(off_bits + bitwords * 4);
     const size_t off_tmp = al(off_counts + (C + 1) * 4);
     const size_t off_status = al(off_tmp + tmp_bytes);
@@ -787,6 +993,14 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     uint8_t* scratch = nullptr;
     if (cudaMallocAsync((void**)&scratch, scratch_bytes, st) != cudaSuccess) return LC_ERR_NOMEM;
     ChunkDesc* chunks_d = (ChunkDesc*)(scratch + off_chunks);
+    FitScratch fs;
+    fs.wins = (const WinDesc*)(scratch + off_wins);
+    fs.nwins = nwins;
+    fs.spec = (uint32_t*)(scratch + off_blk);
+    fs.fix = fs.spec + bitwords;
+    fs.exitS = fs.fix + bitwords;
+    fs.exitF = fs.exitS + bitwords;
+    fs.sync = scratch + off_sync;
     uint32_t* tbits = (uint32_t*)(scratch + off_bits);
     uint32_t* counts = (uint32_t*)(scratch + off_counts);
     void* tmp = scratch + off_tmp;
@@ -800,6 +1014,8 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
         return code;
     };
 
+    rc = cuda_status(cudaMemcpyAsync(scratch + off_wins, wins.data(), nwins * sizeof(WinDesc), cudaMemcpyHostToDevice, st));
+    if (rc) return fail(rc);
     rc = cuda_status(cudaMemcpyAsync(chunks_d, chunks_h, C * sizeof(ChunkDesc), cudaMemcpyHostToDevice, st));
     if (rc) return fail(rc);
     rc = cuda_status(cudaMemsetAsync(status, 0, 4, st));
@@ -807,10 +1023,10 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
 
     // stage 0: anchors and segment counts
     if (kb == 4)
-        rc = run_pipeline<uint32_t>((const uint32_t*)keys_dev, chunks_d, C, tbits, counts, csb_tmp, status, tmp,
+        rc = run_pipeline<uint32_t>((const uint32_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 0);
     else
-        rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, tbits, counts, csb_tmp, status, tmp,
+        rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 0);
     if (rc) return fail(rc);
     rc = cuda_status(cudaMemcpyAsync(&total, csb_tmp + C, 8, cudaMemcpyDeviceToHost, st));
@@ -837,10 +1053,10 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
 
     // stage 1: model, widths, payload
     if (kb == 4)
-        rc = run_pipeline<uint32_t>((const uint32_t*)keys_dev, chunks_d, C, tbits, counts, csb_tmp, status, tmp,
+        rc = run_pipeline<uint32_t>((const uint32_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 1);
     else
-        rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, tbits, counts, csb_tmp, status, tmp,
+        rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 1);
     if (rc) return fail(rc);
     rc = cuda_status(cudaMemcpyAsync(&total, col->blob + lay.cwb + 8 * C, 8, cudaMemcpyDeviceToHost, st));

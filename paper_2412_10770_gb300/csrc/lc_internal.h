@@ -13,8 +13,6 @@ namespace lcx {
 // Keys decoded by one CTA of the decode kernel.  Tiles never cross a chunk.
 constexpr int kTileLog = 11;
 constexpr uint32_t kTile = 1u << kTileLog;
-// Keys per speculation block of the fitter (one 64-bit word of anchor bits).
-constexpr uint32_t kBlock = 64;
 // A chunk holds at most 2^16 keys.
 constexpr uint32_t kMaxChunk = 1u << 16;
 
@@ -34,6 +32,12 @@ struct ChunkDesc {
     uint32_t eps;
     uint32_t check_prev;  // 1: K[key_begin - 1] <= K[key_begin] must hold (same list)
     uint32_t pad;
+};
+
+// A speculation window of the fit: keys [off, off + 8192) of chunk `chunk`.
+struct WinDesc {
+    uint32_t chunk;
+    uint32_t off;
 };
 
 // A decode tile: keys [key_begin, key_begin + n) of chunk `chunk`; its first

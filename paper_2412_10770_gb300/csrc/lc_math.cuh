@@ -61,6 +61,44 @@ __device__ __forceinline__ bool cone_step(uint64_t D, uint32_t d, int64_t eps, i
     return true;
 }
 
+// The same cone without division.  Key t admits the real Q32 slopes in
+// [2^32 (D_t - eps)/d_t, 2^32 (D_t + eps + 1)/d_t); the integer cone of a run
+// of keys is non-empty iff ceil(max lower) < ceil(min upper).  Both extremes
+// are fractions x/e and y/f with e, f < 2^16, so their gap, when positive, is
+// 2^32 (y e - x f)/(e f) >= 2^32/(e f) > 1: the integer cone is non-empty iff
+// x/e < y/f as fractions.  The int64 cap on the slope is the upper fraction
+// 2^31/1 a fresh cone starts from.  State: max lower x/e (X, E) and min upper
+// y/f (Y, F).  Returns false (state unchanged) when key (D, d) empties it.
+struct Frac {
+    int64_t X;   // max (D - eps) over keys, as X / E
+    uint32_t E;
+    uint64_t Y;  // min (D + eps + 1), as Y / F
+    uint32_t F;
+};
+
+__device__ __forceinline__ Frac frac_open() { return Frac{-(1ll << 31), 1u, 1ull << 31, 1u}; }
+
+// x1/e1 > x2/e2 for |x| < 2^47 and 0 < e < 2^16 (no overflow).
+__device__ __forceinline__ bool frac_gt(int64_t x1, uint32_t e1, int64_t x2, uint32_t e2) {
+    return x1 * (int64_t)e2 > x2 * (int64_t)e1;
+}
+
+__device__ __forceinline__ bool frac_ok(const Frac& c) {
+    return c.X < 0 || (uint64_t)c.X * c.F < c.Y * c.E;
+}
+
+__device__ __forceinline__ bool frac_step(uint64_t D, uint32_t d, int64_t eps, Frac& c) {
+    if (D >= ((uint64_t)d << 31) + (uint64_t)eps) return false;  // lower bound at or above the int64 cap
+    const int64_t xl = (int64_t)D - eps;
+    const uint64_t yh = D + (uint64_t)eps + 1;
+    Frac n = c;
+    if (frac_gt(xl, d, c.X, c.E)) { n.X = xl; n.E = d; }
+    if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { n.Y = yh; n.F = d; }
+    if (!frac_ok(n)) return false;
+    c = n;
+    return true;
+}
+
 __device__ __forceinline__ uint32_t zigzag32(int64_t r) {
     return (uint32_t)(((uint64_t)r << 1) ^ (uint64_t)(r >> 63));
 }

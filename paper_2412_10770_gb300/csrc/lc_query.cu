@@ -401,7 +401,7 @@ int build_derived(lc_column* col, cudaStream_t st) {
     std::copy(ctb.begin(), ctb.end(), col->h_ctb);
     const size_t bytes = 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1) + 256;
     uint8_t* p = nullptr;
-    if (cudaMalloc((void**)&p, bytes) != cudaSuccess) return LC_ERR_NOMEM;
+    if (cudaMallocAsync((void**)&p, bytes, st) != cudaSuccess) return LC_ERR_NOMEM;
     col->chunk_tile_begin = (uint64_t*)p;
     col->tiles = (TileDesc*)(p + 8 * (C + 1));
     col->status = (uint32_t*)(p + 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1));
@@ -426,7 +426,10 @@ int build_derived(lc_column* col, cudaStream_t st) {
     const size_t off_rank = al(sizeof(SegRec) * L);
     const size_t off_lv = al(off_rank + sizeof(RankWord) * nw);
     const size_t bytes2 = al(off_lv + 8 * lv_total) + 256;
-    if (cudaMalloc((void**)&col->derived2, bytes2) != cudaSuccess) return LC_ERR_NOMEM;
+    if (cudaMallocAsync((void**)&col->derived2, bytes2, st) != cudaSuccess) {
+        col->derived2 = nullptr;
+        return LC_ERR_NOMEM;
+    }
     SegRec* recs = (SegRec*)col->derived2;
     RankWord* rank = (RankWord*)(col->derived2 + off_rank);
     uint64_t* lv = (uint64_t*)(col->derived2 + off_lv);
