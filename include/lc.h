@@ -147,6 +147,17 @@ int lc_decode_ranges_noalloc(const lc_column* col, const uint64_t* begin_dev, co
  * lc_decode(col, 0, N, ...). */
 int lc_decode_batch(const lc_column* col, void* out_dev, void* stream);
 
+/* A decode recorded once into a CUDA graph and replayed (the batching path:
+ * every list of a batch column decoded by one persistent launch).  The graph
+ * holds lc_decode(col, begin, count, out_dev); col and out_dev must outlive it.
+ * Recording uses `stream` (a non-default stream; NULL records on a private
+ * stream).  lc_graph_launch replays it asynchronously on `stream`. */
+typedef struct lc_graph lc_graph;
+int lc_graph_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream,
+                    lc_graph** out);
+int lc_graph_launch(lc_graph* graph, void* stream);
+void lc_graph_free(lc_graph* graph);
+
 /* Rank access (Sec. III-C, the quantile query f(i) + Delta[i]): out[q] =
  * K[idx[q]] for q < m.  idx_dev: m uint64 indices (device).  out_dev: m keys
  * of key_bytes bytes (device).  An index >= N yields 0 and sets

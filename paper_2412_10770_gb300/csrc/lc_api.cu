@@ -306,6 +306,59 @@ int lc_decode_batch(const lc_column* col, void* out_dev, void* stream) {
     return lc_decode(col, 0, col->N, out_dev, stream);
 }
 
+struct lc_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+int lc_graph_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream, lc_graph** out) {
+    if (!col || !out || (count && !out_dev)) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (begin > col->N || count > col->N - begin) return LC_ERR_OUT_OF_RANGE;
+    cudaStream_t st = (cudaStream_t)stream, own = nullptr;
+    if (!st) {
+        if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return LC_ERR_CUDA;
+        st = own;
+    }
+    // one eager run sets the kernel attributes outside the capture
+    int rc = decode_range(col, begin, count, out_dev, st);
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    lc_graph* g = nullptr;
+    if (!rc) {
+        g = new (std::nothrow) lc_graph{nullptr, nullptr};
+        if (!g) rc = LC_ERR_NOMEM;
+    }
+    if (!rc) rc = cuda_status(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (!rc) {
+        const int rk = decode_range(col, begin, count, out_dev, st);
+        const int re = cuda_status(cudaStreamEndCapture(st, &g->graph));
+        rc = rk ? rk : re;
+    }
+    if (!rc) rc = cuda_status(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    if (own) cudaStreamDestroy(own);
+    if (rc) {
+        if (g) {
+            if (g->graph) cudaGraphDestroy(g->graph);
+            delete g;
+        }
+        return rc;
+    }
+    *out = g;
+    return LC_OK;
+}
+
+int lc_graph_launch(lc_graph* g, void* stream) {
+    if (!g) return LC_ERR_INVALID_ARG;
+    return cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+}
+
+void lc_graph_free(lc_graph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
 int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* out_dev, void* stream) {
     if (!col || (m && (!idx_dev || !out_dev))) return LC_ERR_INVALID_ARG;
     if (col->N == 0) {

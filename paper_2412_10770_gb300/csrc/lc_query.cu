@@ -141,11 +141,12 @@ __device__ void decode_tile(const ColView& v, uint64_t t, uint64_t lo_key, uint6
     __syncthreads();
 }
 
+// Persistent: each CTA decodes tiles t0 + blockIdx.x, t0 + blockIdx.x + gridDim.x, ...
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads) decode_kernel(ColView v, uint64_t t0, uint64_t begin, uint64_t end,
-                                                             KT* __restrict__ out) {
+__global__ void __launch_bounds__(kDecThreads) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
+                                                             uint64_t end, KT* __restrict__ out) {
     extern __shared__ __align__(16) uint8_t smem[];
-    decode_tile<KT>(v, t0 + blockIdx.x, begin, end, out, smem);
+    for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) decode_tile<KT>(v, t0 + t, begin, end, out, smem);
 }
 
 // Work items of a multi-range decode: range r covers tiles
@@ -525,22 +526,27 @@ static uint64_t host_tile_of(const lc_column* col, uint64_t i) {
     return col->h_ctb[c] + ((i - col->h_ckb[c]) >> kTileLog);
 }
 
+template <typename KT>
+static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_t begin, uint64_t count, void* out,
+                         cudaStream_t st) {
+    int rc = set_smem<KT>();
+    if (rc) return rc;
+    const size_t smem = dec_smem(col->view.max_tile_segs);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel<KT>, kDecThreads, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    const uint64_t grid = std::min<uint64_t>(nt, (uint64_t)sm_count() * occ);
+    decode_kernel<KT><<<(unsigned)grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count, (KT*)out);
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
 int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st) {
     if (count == 0) return LC_OK;
     const uint64_t t0 = host_tile_of(col, begin), t1 = host_tile_of(col, begin + count - 1);
-    const uint64_t nt = t1 - t0 + 1;
-    int rc;
-    if (col->key_bytes == 4) {
-        if ((rc = set_smem<uint32_t>())) return rc;
-        decode_kernel<uint32_t><<<(unsigned)nt, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, t0, begin, begin + count,
-                                                                           (uint32_t*)out);
-    } else {
-        if ((rc = set_smem<uint64_t>())) return rc;
-        decode_kernel<uint64_t><<<(unsigned)nt, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, t0, begin, begin + count,
-                                                                           (uint64_t*)out);
-    }
-    note_launch();
-    return cuda_status(cudaGetLastError());
+    if (col->key_bytes == 4) return launch_decode<uint32_t>(col, t0, t1 - t0 + 1, begin, count, out, st);
+    return launch_decode<uint64_t>(col, t0, t1 - t0 + 1, begin, count, out, st);
 }
 
 int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count, const uint64_t* out_off,

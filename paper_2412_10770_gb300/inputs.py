@@ -164,3 +164,49 @@ def posting_lists(n_lists: int, total: int, universe: int, seed: int, alpha: flo
             pick = rng.permutation(pick)[:k]
         ids[a:a + k] = np.sort(pick).astype(np.uint32)
     return ids, begin
+
+
+def posting_lists_device(n_lists: int, total: int, universe: int, seed: int, alpha: float = 1.1, lo: int = 16,
+                         hi: int = 10**7, device: str = "cuda", max_sort: int = 1 << 29):
+    """The same posting-list recipe as ``posting_lists``, drawn on the GPU for
+    workloads too large for the host: every list draws its ids uniformly with
+    replacement, duplicates are dropped and the shortfall is redrawn until each
+    list holds its length of distinct ids (the result is a uniform sample
+    without replacement: the procedure treats every id alike).  Lists are
+    processed in groups of at most ``max_sort`` ids.  Returns (ids uint32
+    tensor on ``device``, list_begin uint64 numpy array)."""
+    import torch
+
+    rng = _rng(seed)
+    lens = zipf_lengths(n_lists, total, alpha, lo, min(hi, universe))
+    rng.shuffle(lens)
+    begin = np.zeros(n_lists + 1, dtype=np.uint64)
+    np.cumsum(lens, out=begin[1:])
+    out = torch.empty(int(begin[-1]), dtype=torch.int32, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    l0 = 0
+    while l0 < n_lists:
+        l1 = l0 + 1
+        while l1 < n_lists and int(begin[l1 + 1] - begin[l0]) <= max_sort:
+            l1 += 1
+        lens_g = torch.from_numpy(lens[l0:l1]).to(device)
+        lid = torch.repeat_interleave(torch.arange(l1 - l0, device=device, dtype=torch.int64), lens_g)
+        key = (lid << 32) | torch.randint(0, universe, (lid.numel(),), generator=gen, device=device)
+        del lid
+        while True:
+            key = torch.sort(key).values
+            keep = torch.ones_like(key, dtype=torch.bool)
+            keep[1:] = key[1:] != key[:-1]
+            key = key[keep]
+            deficit = lens_g - torch.bincount(key >> 32, minlength=l1 - l0)
+            short = int(deficit.sum())
+            if short == 0:
+                break
+            extra = torch.repeat_interleave(torch.arange(l1 - l0, device=device, dtype=torch.int64), deficit)
+            key = torch.cat([key, (extra << 32) | torch.randint(0, universe, (short,), generator=gen, device=device)])
+        a, b = int(begin[l0]), int(begin[l1])
+        out[a:b] = (key & 0xFFFFFFFF).to(torch.int32)
+        del key
+        l0 = l1
+    return out.view(torch.uint32), begin

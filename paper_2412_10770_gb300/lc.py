@@ -32,7 +32,7 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_decode_batch",
            "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
            "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
-           "lc_version", "lc_launch_count")
+           "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free")
 
 
 class LcError(RuntimeError):
@@ -97,6 +97,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_strerror": ([i32], ctypes.c_char_p),
         "lc_version": ([], i32),
         "lc_launch_count": ([], u64),
+        "lc_graph_decode": ([p, u64, u64, p, p, pp], i32),
+        "lc_graph_launch": ([p, p], i32),
+        "lc_graph_free": ([p], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -328,6 +331,50 @@ def lc_free(col: Column) -> None:
 
 def lc_version() -> int:
     return load().lc_version()
+
+
+class Graph:
+    """A decode recorded into a CUDA graph (lc_graph_decode); replay with launch()."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep  # column and output must outlive the graph
+
+    def launch(self, stream=None) -> None:
+        _check(load().lc_graph_launch(self.handle, _stream(stream)), "lc_graph_launch")
+
+    def free(self) -> None:
+        if self.handle and self.handle.value and _lib is not None:
+            _lib.lc_graph_free(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def lc_graph_decode(col: Column, begin: int = 0, count: int | None = None, out=None, stream=None) -> tuple:
+    """Record lc_decode(col, begin, count, out) into a CUDA graph; returns (Graph, out)."""
+    lib = load()
+    if count is None:
+        count = col.n - begin
+    if out is None:
+        out = torch.empty(count, dtype=col.dtype, device="cuda")
+    _dev(out, "out")
+    h = ctypes.c_void_p()
+    _check(lib.lc_graph_decode(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream), ctypes.byref(h)),
+           "lc_graph_decode")
+    return Graph(h.value, (col, out)), out
+
+
+def lc_graph_launch(graph: Graph, stream=None) -> None:
+    graph.launch(stream)
+
+
+def lc_graph_free(graph: Graph) -> None:
+    graph.free()
 
 
 def lc_launch_count() -> int:

@@ -1,0 +1,107 @@
+"""Autotuner of the fit parameters for batches of posting lists.
+
+The paper's only hyper-parameter is eps (Sec. II-A, Sec. IV-A): a larger eps
+means fewer segments but wider residuals.  BitTuner's closed form (quoted in
+Sec. II-A / IV-A) puts the optimum near eps* = sqrt(2 ln2 sigma^2 C (K + 2F)),
+with sigma^2 the variance of the key gaps and C a data-dependent constant the
+paper leaves open; Sec. IV-A notes that a single global eps is not optimal
+when lists differ.  This tuner therefore picks (eps, chunk_log2) per bucket of
+list lengths (powers of two) by measurement: it compresses a sample of each
+bucket's lists under every candidate, on the GPU, in batched calls, and keeps
+the smallest K^c.  The BitTuner value is computed per bucket beside the choice,
+with C fitted across the buckets, as a reference.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import lc
+
+EPS_CANDIDATES = tuple([0] + [(1 << k) - 1 for k in range(1, 25)])
+LOG2_CANDIDATES = (10, 12, 14, 16)
+
+
+def _bucket(length: int) -> int:
+    return max(0, int(length).bit_length() - 1)
+
+
+def _sample_batch(ids: torch.Tensor, begin: np.ndarray, lists: np.ndarray, max_keys: int):
+    """Concatenate (prefixes of) the chosen lists, at most max_keys ids in all."""
+    parts, lens = [], []
+    budget = max_keys
+    for l in lists:
+        a, b = int(begin[l]), int(begin[l + 1])
+        take = min(b - a, max(16, budget // max(1, len(lists))))
+        parts.append(ids[a:a + take])
+        lens.append(take)
+    sb = np.zeros(len(lens) + 1, dtype=np.uint64)
+    np.cumsum(lens, out=sb[1:])
+    return torch.cat(parts).contiguous(), sb
+
+
+def _size(ids: torch.Tensor, sb: np.ndarray, eps: int, log2: int) -> int:
+    col = lc.lc_compress_batch(ids, sb, eps, log2)
+    try:
+        return lc.lc_size(col)
+    finally:
+        col.free()
+
+
+def tune(ids: torch.Tensor, begin: np.ndarray, sample_lists: int = 24, sample_keys: int = 1 << 20,
+         seed: int = 0, eps_candidates=EPS_CANDIDATES, log2_candidates=LOG2_CANDIDATES):
+    """Per-list (eps, chunk_log2) for the lists ids[begin[l]:begin[l+1]].
+
+    Returns (eps uint64[nl], chunk_log2 uint8[nl], table) where table lists,
+    per length bucket, the chosen parameters, the sample's bits per key, the
+    gap variance and the BitTuner reference value."""
+    begin = np.asarray(begin, dtype=np.uint64)
+    lens = np.diff(begin).astype(np.int64)
+    nl = lens.size
+    rng = np.random.Generator(np.random.PCG64(seed))
+    buckets = {}
+    for l in range(nl):
+        if lens[l] > 0:
+            buckets.setdefault(_bucket(lens[l]), []).append(l)
+    eps_of = np.zeros(nl, dtype=np.uint64)
+    log2_of = np.full(nl, 16, dtype=np.uint8)
+    kb = ids.element_size()
+    table = []
+    for bkt in sorted(buckets):
+        members = np.array(buckets[bkt])
+        pick = rng.choice(members, size=min(sample_lists, members.size), replace=False)
+        sids, sb = _sample_batch(ids, begin, np.sort(pick), sample_keys)
+        nkeys = int(sb[-1])
+        # eps first (at the widest chunk), then the chunk length for lists that span chunks
+        sizes = {e: _size(sids, sb, e, 16) for e in eps_candidates}
+        best_eps = min(sizes, key=lambda e: (sizes[e], e))
+        best_log2, best = 16, sizes[best_eps]
+        if (1 << bkt) > (1 << min(log2_candidates)):
+            for g in log2_candidates:
+                if g == 16:
+                    continue
+                s = _size(sids, sb, best_eps, g)
+                if s < best:
+                    best, best_log2 = s, g
+        h = sids.to(torch.int64)
+        gaps = []
+        for i in range(len(sb) - 1):
+            seg = h[int(sb[i]):int(sb[i + 1])]
+            if seg.numel() > 1:
+                gaps.append(seg[1:] - seg[:-1])
+        var = float(torch.cat(gaps).double().var()) if gaps else 0.0
+        eps_of[members] = best_eps
+        log2_of[members] = best_log2
+        table.append({"bucket_min_len": 1 << bkt, "lists": int(members.size), "sample_keys": nkeys, "eps": best_eps,
+                      "chunk_log2": best_log2, "bits_per_key": 8.0 * best / nkeys, "gap_var": var,
+                      "raw_bits_per_key": 8 * kb})
+    # BitTuner reference: eps* = sqrt(2 ln2 sigma^2 C (K + 2F)); C fitted (median) over the buckets
+    K, F = 8 * kb, 64
+    ratios = [t["eps"] ** 2 / (2 * math.log(2) * t["gap_var"] * (K + 2 * F)) for t in table
+              if t["eps"] > 0 and t["gap_var"] > 0]
+    C = float(np.median(ratios)) if ratios else 0.0
+    for t in table:
+        t["bittuner_eps"] = math.sqrt(2 * math.log(2) * t["gap_var"] * C * (K + 2 * F)) if t["gap_var"] > 0 else 0.0
+    return eps_of, log2_of, {"buckets": table, "bittuner_C": C, "K": K, "F": F}
