@@ -177,6 +177,69 @@ int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key);
 int lc_lower_bound1(const lc_column* col, uint64_t v, uint64_t* pos);
 
+/* ------------------------------------------------------------ serving */
+
+/* Continuous batching over device-resident columns.  A server keeps `slots`
+ * CUDA streams; a scheduler thread takes requests as they are submitted and,
+ * whenever a slot is free, packs the waiting requests that fit in the free
+ * HBM budget (device memory for their inputs and outputs) into one batch:
+ * one fused launch for all access and lower_bound requests (over any of the
+ * columns), one persistent launch for all range decodes, with the copies in
+ * and out on the same stream.  Batches on different slots overlap on the
+ * device; a request that arrives while others run is admitted as soon as a
+ * slot and its memory are free.  Results equal those of the single-request
+ * calls (lc_access, lc_lower_bound, lc_decode).  The paper has no serving
+ * layer; this is the library's runtime around its queries (Sec. III). */
+enum { LC_OP_ACCESS = 1, LC_OP_LOWER_BOUND = 2, LC_OP_DECODE = 3 };
+
+typedef struct {
+    uint32_t op;       /* LC_OP_* */
+    uint32_t column;   /* index into the server's columns */
+    uint64_t count;    /* ranks, values, or keys to decode */
+    uint64_t begin;    /* LC_OP_DECODE: first key */
+    const void* input; /* host: count uint64 ranks (access) or count values of key_bytes (lower_bound) */
+    void* output;      /* host: count keys (access, decode) or count uint64 positions (lower_bound);
+                          page-locked memory lets the copy overlap */
+    uint64_t user;     /* returned in the completion */
+} lc_request;
+
+typedef struct {
+    uint64_t ticket;
+    uint64_t user;
+    int32_t status;      /* LC_OK, or LC_ERR_OUT_OF_RANGE / LC_ERR_NOMEM (larger than the whole budget) / ... */
+    uint32_t batch_size; /* requests in the batch it ran in */
+    double latency_us;   /* from lc_server_submit to completion */
+} lc_completion;
+
+typedef struct {
+    uint64_t submitted, completed, batches;
+    uint64_t peak_hbm_bytes;    /* most device memory held by batches at once (<= budget) */
+    uint32_t peak_inflight;     /* most batches on the device at once */
+    uint32_t slots;
+} lc_server_stats_t;
+
+typedef struct lc_server lc_server;
+
+/* cols: ncols single-mode or list-mode columns of one key width, all on the
+ * current device; they must outlive the server.  hbm_budget: bytes of device
+ * memory the server may hold for request inputs and outputs.  slots: streams
+ * (batches in flight), 1..64. */
+int lc_server_create(lc_column* const* cols, int ncols, uint64_t hbm_budget, int slots, lc_server** out);
+/* Queue one request (thread-safe, non-blocking).  The input and output
+ * buffers must stay valid until its completion has been returned. */
+int lc_server_submit(lc_server* server, const lc_request* req, uint64_t* ticket);
+/* Up to `max` finished requests, without waiting. */
+int lc_server_poll(lc_server* server, lc_completion* out, int max, int* got);
+/* Up to `max` finished requests, waiting at most timeout_us for the first. */
+int lc_server_wait(lc_server* server, lc_completion* out, int max, int* got, uint64_t timeout_us);
+int lc_server_stats(lc_server* server, lc_server_stats_t* stats);
+/* Finish the queued and running work, then release the server. */
+int lc_server_destroy(lc_server* server);
+
+/* The plain path: one request alone, synchronously (copy in, one kernel, copy
+ * out, wait) on `stream`. */
+int lc_serve_sync(lc_column* const* cols, int ncols, const lc_request* req, void* stream, lc_completion* out);
+
 /* ------------------------------------------------------------ size, bytes, status */
 
 /* r = size(K^c) / size(K) with size(K) = N * key_bytes (Def. 1).  Returns a

@@ -40,6 +40,17 @@ struct WinDesc {
     uint32_t off;
 };
 
+// One request of a serving batch, as the device sees it.
+struct SrvReq {
+    uint64_t begin;       // LC_OP_DECODE: first key
+    uint64_t count;       // queries (access, lower_bound) or keys (decode)
+    uint64_t qoff;        // access / lower_bound: first query of the request in the batch
+    uint64_t first_tile;  // decode: first tile
+    uint64_t out;         // decode: device address of the request's keys
+    uint32_t col;
+    uint32_t op;
+};
+
 // A decode tile: keys [key_begin, key_begin + n) of chunk `chunk`; its first
 // and last keys lie in segments seg_lo and seg_hi (global segment indices).
 struct TileDesc {
@@ -153,6 +164,13 @@ int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uin
                           const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st);
 int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
+
+// Serving: one batch of requests over several columns (lc_query.cu).
+int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, uint32_t nqreq, uint64_t nq,
+                 const uint64_t* qin_d, uint64_t* qout_d, const SrvReq* dreqs_d, uint32_t ndreq,
+                 const uint64_t* work_off_d, uint64_t nwork, uint32_t max_tile_segs, uint32_t* status_d,
+                 cudaStream_t st);
+uint64_t tile_of_key(const lc_column* col, uint64_t i);
 
 // Exclusive scan of n uint32 counts into n+1 uint64 offsets (out[n] = total),
 // optionally applying f(count) = even_words(count bits) first.

@@ -50,8 +50,8 @@ __device__ __forceinline__ uint64_t chunk_of(const ColView& v, uint64_t i) {
 // Decode keys [lo_key, hi_key) of tile t into out[g - lo_key].
 template <typename KT>
 __device__ void decode_tile(const ColView& v, uint64_t t, uint64_t lo_key, uint64_t hi_key, KT* __restrict__ out,
-                            uint8_t* smem) {
-    const uint32_t ms = v.max_tile_segs;
+                            uint8_t* smem, uint32_t smem_segs = 0) {
+    const uint32_t ms = smem_segs ? smem_segs : v.max_tile_segs;
     uint64_t* s_icpt = (uint64_t*)smem;
     int64_t* s_slope = (int64_t*)(s_icpt + ms);
     uint64_t* s_meta = (uint64_t*)(s_slope + ms);
@@ -218,7 +218,14 @@ constexpr uint64_t kKeyMask = (1ull << 56) - 1;
 
 // Rank access: the segment of key i comes from one rank word (anchor bits +
 // anchors before), its model from one 32-byte record, its residual from the
-// payload: three dependent loads.
+// payload: three dependent loads.  i < v.N.
+__device__ __forceinline__ uint64_t access_one(const ColView& v, uint64_t i) {
+    const ulonglong2 rw = __ldg((const ulonglong2*)(v.rank + (i >> 6)));
+    const uint64_t j = rw.y + __popcll(rw.x & (~0ull >> (63u - (uint32_t)(i & 63u)))) - 1;
+    const SegRec r = load_rec(v.recs + j);
+    return rec_key(v, r, (uint32_t)(i - (r.kstart_w & kKeyMask)));
+}
+
 template <typename KT>
 __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint64_t m, KT* __restrict__ out) {
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
@@ -228,11 +235,16 @@ __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint6
             out[q] = 0;
             continue;
         }
-        const ulonglong2 rw = __ldg((const ulonglong2*)(v.rank + (i >> 6)));
-        const uint64_t j = rw.y + __popcll(rw.x & (~0ull >> (63u - (uint32_t)(i & 63u)))) - 1;
-        const SegRec r = load_rec(v.recs + j);
-        out[q] = (KT)rec_key(v, r, (uint32_t)(i - (r.kstart_w & kKeyMask)));
+        out[q] = (KT)access_one(v, i);
     }
+}
+
+// Entry k of the top intercept level: from `top_keys` when staged, else from
+// the level itself.
+template <typename KT>
+__device__ __forceinline__ uint64_t top_at(const ColView& v, const uint64_t* top_keys, uint64_t k) {
+    if (top_keys) return top_keys[k];
+    return v.top ? __ldg(v.level[v.top] + k) : ld_icpt<KT>(v.icpt, k);
 }
 
 // Value lower_bound: the last segment whose intercept (its first key) is < x is
@@ -243,60 +255,112 @@ __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint6
 // t >= (dx + R + 1)/s is >= x (s = slope / 2^32, dx = x - intercept).  A
 // binary search inside the bracket finishes.
 template <typename KT>
+__device__ uint64_t lower_bound_one(const ColView& v, uint64_t x, const uint64_t* top_keys) {
+    const uint32_t top = v.top;
+    const uint64_t ntop = top ? v.level_n[top] : v.L;
+    if (v.L == 0 || top_at<KT>(v, top_keys, 0) >= x) return 0;
+    uint64_t lo = 0, hi = ntop - 1;  // last entry < x
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi + 1) >> 1;
+        if (top_at<KT>(v, top_keys, mid) < x) lo = mid;
+        else hi = mid - 1;
+    }
+    for (int d = (int)top - 1; d >= 0; --d) {
+        const uint64_t nd = d ? v.level_n[d] : v.L;
+        const uint64_t base = 16 * lo;
+        uint64_t a = base, b = min(base + 16, nd) - 1;
+        while (a < b) {
+            const uint64_t mid = (a + b + 1) >> 1;
+            const uint64_t key = d ? __ldg(v.level[d] + mid) : ld_icpt<KT>(v.icpt, mid);
+            if (key < x) a = mid;
+            else b = mid - 1;
+        }
+        lo = a;
+    }
+    const uint64_t j = lo;
+    const SegRec r = load_rec(v.recs + j);
+    const uint64_t ks = r.kstart_w & kKeyMask;
+    const uint64_t ke = j + 1 < v.L ? (__ldg(&v.recs[j + 1].kstart_w) & kKeyMask) : v.N;
+    const uint32_t n = (uint32_t)(ke - ks);
+    uint32_t a = 1, b = n;  // first t in [1, n) with key(t) >= x, or n
+    if (n >= 32 && r.slope > 0) {
+        const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+        const float s = (float)r.slope * 2.3283064365386963e-10f;  // keys per index
+        const float th = (float)(x - r.icpt) / s;
+        const float dl = ((float)((1u << w) >> 1) + 1.0f) / s + 2.0f;
+        const float fa = th - dl, fb = th + dl + 1.0f;
+        a = fa <= 1.0f ? 1u : (fa >= (float)n ? n : (uint32_t)fa);
+        b = fb <= 1.0f ? 1u : (fb >= (float)n ? n : (uint32_t)fb);
+        if (a > b) a = b;
+    }
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (rec_key(v, r, mid) < x) a = mid + 1;
+        else b = mid;
+    }
+    return ks + a;
+}
+
+template <typename KT>
 __global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m,
                                                           uint64_t* __restrict__ out) {
     extern __shared__ uint64_t s_top[];
-    const uint32_t top = v.top;
-    const uint64_t ntop = top ? v.level_n[top] : v.L;
-    for (uint64_t k = threadIdx.x; k < ntop; k += blockDim.x)
-        s_top[k] = top ? __ldg(v.level[top] + k) : ld_icpt<KT>(v.icpt, k);
+    const uint64_t ntop = v.top ? v.level_n[v.top] : v.L;
+    for (uint64_t k = threadIdx.x; k < ntop; k += blockDim.x) s_top[k] = top_at<KT>(v, nullptr, k);
     __syncthreads();
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = (uint64_t)vals[q];
-        if (v.L == 0 || s_top[0] >= x) {
-            out[q] = 0;
-            continue;
-        }
-        uint64_t lo = 0, hi = ntop - 1;  // last entry < x
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
+        out[q] = lower_bound_one<KT>(v, (uint64_t)vals[q], s_top);
+}
+
+// ------------------------------------------------------------------ serving: multi-column batches
+
+// Access and lower_bound requests of one batch, over any of the server's
+// columns: query q belongs to the last request whose qoff <= q.
+template <typename KT>
+__global__ void serve_query_kernel(const ColView* __restrict__ views, const SrvReq* __restrict__ reqs, uint32_t nreq,
+                                   uint64_t nq, const uint64_t* __restrict__ qin, uint64_t* __restrict__ qout,
+                                   uint32_t* __restrict__ status) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nq; q += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nreq - 1;
         while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (s_top[mid] < x) lo = mid;
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (reqs[mid].qoff <= q) lo = mid;
             else hi = mid - 1;
         }
-        for (int d = (int)top - 1; d >= 0; --d) {
-            const uint64_t nd = d ? v.level_n[d] : v.L;
-            const uint64_t base = 16 * lo;
-            uint64_t a = base, b = min(base + 16, nd) - 1;
-            while (a < b) {
-                const uint64_t mid = (a + b + 1) >> 1;
-                const uint64_t key = d ? __ldg(v.level[d] + mid) : ld_icpt<KT>(v.icpt, mid);
-                if (key < x) a = mid;
-                else b = mid - 1;
+        const SrvReq& rq = reqs[lo];
+        const ColView& v = views[rq.col];
+        const uint64_t x = qin[q];
+        if (rq.op == LC_OP_ACCESS) {
+            if (x >= v.N) {
+                atomicOr(status, kStOutOfRange);
+                qout[q] = 0;
+            } else {
+                qout[q] = access_one(v, x);
             }
-            lo = a;
+        } else {
+            qout[q] = lower_bound_one<KT>(v, x, nullptr);
         }
-        const uint64_t j = lo;
-        const SegRec r = load_rec(v.recs + j);
-        const uint64_t ks = r.kstart_w & kKeyMask;
-        const uint64_t ke = j + 1 < v.L ? (__ldg(&v.recs[j + 1].kstart_w) & kKeyMask) : v.N;
-        const uint32_t n = (uint32_t)(ke - ks);
-        uint32_t a = 1, b = n;  // first t in [1, n) with key(t) >= x, or n
-        if (n >= 32 && r.slope > 0) {
-            const uint32_t w = (uint32_t)(r.kstart_w >> 56);
-            const float s = (float)r.slope * 2.3283064365386963e-10f;  // keys per index
-            const float th = (float)(x - r.icpt) / s;
-            const float dl = ((float)((1u << w) >> 1) + 1.0f) / s + 2.0f;
-            const float fa = th - dl, fb = th + dl + 1.0f;
-            a = fa <= 1.0f ? 1u : (fa >= (float)n ? n : (uint32_t)fa);
-            b = fb <= 1.0f ? 1u : (fb >= (float)n ? n : (uint32_t)fb);
-            if (a > b) a = b;
+    }
+}
+
+// Range decodes of one batch: work item w is tile first_tile + (w - work_off[r])
+// of request r, written to that request's own device buffer.
+template <typename KT>
+__global__ void __launch_bounds__(kDecThreads)
+serve_decode_kernel(const ColView* __restrict__ views, const SrvReq* __restrict__ reqs, uint32_t nreq,
+                    const uint64_t* __restrict__ work_off, uint32_t smem_segs) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint64_t total = work_off[nreq];
+    for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        uint32_t lo = 0, hi = nreq - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (work_off[mid] <= w) lo = mid;
+            else hi = mid - 1;
         }
-        while (a < b) {
-            const uint32_t mid = (a + b) >> 1;
-            if (rec_key(v, r, mid) < x) a = mid + 1;
-            else b = mid;
-        }
-        out[q] = ks + a;
+        const SrvReq& rq = reqs[lo];
+        decode_tile<KT>(views[rq.col], rq.first_tile + (w - work_off[lo]), rq.begin, rq.begin + rq.count,
+                        (KT*)rq.out, smem, smem_segs);
     }
 }
 
@@ -688,5 +752,52 @@ int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uin
     note_launch();
     return cuda_status(cudaGetLastError());
 }
+
+
+int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, uint32_t nqreq, uint64_t nq,
+                 const uint64_t* qin_d, uint64_t* qout_d, const SrvReq* dreqs_d, uint32_t ndreq,
+                 const uint64_t* work_off_d, uint64_t nwork, uint32_t max_tile_segs, uint32_t* status_d,
+                 cudaStream_t st) {
+    int rc;
+    if (nq) {
+        const unsigned grid = (unsigned)std::min<uint64_t>((nq + 255) / 256, (uint64_t)sm_count() * 8);
+        if (key_bytes == 4)
+            serve_query_kernel<uint32_t><<<grid, 256, 0, st>>>(views_d, qreqs_d, nqreq, nq, qin_d, qout_d, status_d);
+        else
+            serve_query_kernel<uint64_t><<<grid, 256, 0, st>>>(views_d, qreqs_d, nqreq, nq, qin_d, qout_d, status_d);
+        note_launch();
+        if ((rc = cuda_status(cudaGetLastError()))) return rc;
+    }
+    if (nwork) {
+        const size_t smem = dec_smem(max_tile_segs);
+        const unsigned grid = (unsigned)std::min<uint64_t>(nwork, (uint64_t)sm_count() * 4);
+        if (key_bytes == 4) {
+            static bool done = false;
+            if (!done) {
+                if ((rc = cuda_status(cudaFuncSetAttribute(serve_decode_kernel<uint32_t>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem))))
+                    return rc;
+                done = true;
+            }
+            serve_decode_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(views_d, dreqs_d, ndreq, work_off_d,
+                                                                          max_tile_segs);
+        } else {
+            static bool done = false;
+            if (!done) {
+                if ((rc = cuda_status(cudaFuncSetAttribute(serve_decode_kernel<uint64_t>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem))))
+                    return rc;
+                done = true;
+            }
+            serve_decode_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(views_d, dreqs_d, ndreq, work_off_d,
+                                                                          max_tile_segs);
+        }
+        note_launch();
+        if ((rc = cuda_status(cudaGetLastError()))) return rc;
+    }
+    return LC_OK;
+}
+
+uint64_t tile_of_key(const lc_column* col, uint64_t i) { return host_tile_of(col, i); }
 
 }  // namespace lcx

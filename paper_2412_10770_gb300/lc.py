@@ -32,7 +32,10 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_decode_batch",
            "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
            "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
-           "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free")
+           "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free", "lc_server_create", "lc_server_submit",
+           "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync")
+
+LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
 
 class LcError(RuntimeError):
@@ -50,6 +53,22 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("segments", ctypes.c_uint64),
                 ("words", ctypes.c_uint64), ("lists", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
                 ("eps", ctypes.c_uint64), ("key_bytes", ctypes.c_uint32), ("chunk_log2", ctypes.c_uint32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint32), ("column", ctypes.c_uint32), ("count", ctypes.c_uint64),
+                ("begin", ctypes.c_uint64), ("input", ctypes.c_void_p), ("output", ctypes.c_void_p),
+                ("user", ctypes.c_uint64)]
+
+
+class _Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("user", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("batch_size", ctypes.c_uint32), ("latency_us", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("peak_hbm_bytes", ctypes.c_uint64), ("peak_inflight", ctypes.c_uint32), ("slots", ctypes.c_uint32)]
 
 
 _lib = None
@@ -100,6 +119,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_graph_decode": ([p, u64, u64, p, p, pp], i32),
         "lc_graph_launch": ([p, p], i32),
         "lc_graph_free": ([p], None),
+        "lc_server_create": ([p, ctypes.c_int, u64, ctypes.c_int, pp], i32),
+        "lc_server_submit": ([p, ctypes.POINTER(_Request), pu64], i32),
+        "lc_server_poll": ([p, ctypes.POINTER(_Completion), ctypes.c_int, ctypes.POINTER(ctypes.c_int)], i32),
+        "lc_server_wait": ([p, ctypes.POINTER(_Completion), ctypes.c_int, ctypes.POINTER(ctypes.c_int), u64], i32),
+        "lc_server_stats": ([p, ctypes.POINTER(_ServerStats)], i32),
+        "lc_server_destroy": ([p], i32),
+        "lc_serve_sync": ([p, ctypes.c_int, ctypes.POINTER(_Request), p, ctypes.POINTER(_Completion)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -379,3 +405,102 @@ def lc_graph_free(graph: Graph) -> None:
 
 def lc_launch_count() -> int:
     return load().lc_launch_count()
+
+
+# ---------------------------------------------------------------- serving
+
+
+def _as_request(op: int, column: int, count: int, begin: int, inp: int, out: int, user: int) -> _Request:
+    return _Request(int(op), int(column), int(count), int(begin), ctypes.c_void_p(inp or None),
+                    ctypes.c_void_p(out or None), int(user))
+
+
+def _completion_dict(c: _Completion) -> dict:
+    return {"ticket": c.ticket, "user": c.user, "status": c.status, "batch_size": c.batch_size,
+            "latency_us": c.latency_us}
+
+
+class Server:
+    """lc_server: continuous batching over device-resident columns.  Request
+    inputs and outputs are host addresses (page-locked memory overlaps best)."""
+
+    def __init__(self, cols, hbm_budget: int, slots: int = 4):
+        lib = load()
+        self._cols = list(cols)
+        arr = (ctypes.c_void_p * len(self._cols))(*[c.handle.value for c in self._cols])
+        h = ctypes.c_void_p()
+        _check(lib.lc_server_create(arr, len(self._cols), int(hbm_budget), int(slots), ctypes.byref(h)),
+               "lc_server_create")
+        self.handle = h
+        self._buf = (_Completion * 1024)()
+
+    def submit(self, op: int, column: int, count: int, begin: int = 0, inp: int = 0, out: int = 0,
+               user: int = 0) -> int:
+        r = _as_request(op, column, count, begin, inp, out, user)
+        t = ctypes.c_uint64()
+        _check(load().lc_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "lc_server_submit")
+        return t.value
+
+    def poll(self, max_n: int = 1024) -> list:
+        got = ctypes.c_int()
+        _check(load().lc_server_poll(self.handle, self._buf, min(max_n, 1024), ctypes.byref(got)), "lc_server_poll")
+        return [_completion_dict(self._buf[i]) for i in range(got.value)]
+
+    def wait(self, max_n: int = 1024, timeout_us: int = 100000) -> list:
+        got = ctypes.c_int()
+        rc = load().lc_server_wait(self.handle, self._buf, min(max_n, 1024), ctypes.byref(got), int(timeout_us))
+        if rc not in (LC_OK, LC_ERR_TIMEOUT):
+            raise LcError(rc, "lc_server_wait")
+        return [_completion_dict(self._buf[i]) for i in range(got.value)]
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load().lc_server_stats(self.handle, ctypes.byref(st)), "lc_server_stats")
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self) -> None:
+        if self.handle and self.handle.value and _lib is not None:
+            _lib.lc_server_destroy(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lc_server_create(cols, hbm_budget: int, slots: int = 4) -> Server:
+    return Server(cols, hbm_budget, slots)
+
+
+def lc_server_submit(server: Server, op: int, column: int, count: int, begin: int = 0, inp: int = 0, out: int = 0,
+                     user: int = 0) -> int:
+    return server.submit(op, column, count, begin, inp, out, user)
+
+
+def lc_server_poll(server: Server, max_n: int = 1024) -> list:
+    return server.poll(max_n)
+
+
+def lc_server_wait(server: Server, max_n: int = 1024, timeout_us: int = 100000) -> list:
+    return server.wait(max_n, timeout_us)
+
+
+def lc_server_stats(server: Server) -> dict:
+    return server.stats()
+
+
+def lc_server_destroy(server: Server) -> None:
+    server.close()
+
+
+def lc_serve_sync(cols, op: int, column: int, count: int, begin: int = 0, inp: int = 0, out: int = 0, user: int = 0,
+                  stream=None) -> dict:
+    """The plain path: one request alone, synchronously."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(cols))(*[c.handle.value for c in cols])
+    r = _as_request(op, column, count, begin, inp, out, user)
+    c = _Completion()
+    _check(lib.lc_serve_sync(arr, len(cols), ctypes.byref(r), _stream(stream), ctypes.byref(c)), "lc_serve_sync")
+    return _completion_dict(c)
