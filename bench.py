@@ -60,6 +60,11 @@ def parse_args():
     ap.add_argument("--lists", type=int, default=1_000_000)
     ap.add_argument("--total", type=int, default=2_000_000_000)
     ap.add_argument("--per-list-sample", type=int, default=2000)
+    ap.add_argument("--columns", type=int, default=64)
+    ap.add_argument("--column-keys", type=int, default=50_000_000)
+    ap.add_argument("--requests", type=int, default=3000)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=16.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -220,6 +225,9 @@ def main():
         return
     if args.config == 3:
         run_batch(args)
+        return
+    if args.config == 4:
+        run_serve(args)
         return
     world, rank, local = dist_env()
     import torch
@@ -491,6 +499,162 @@ def run_batch(args):
             "batched_over_per_list": value / (skeys / tp),
             "ratio": size / (4 * N), "bits_per_id": 8 * size / N, "segments": segs,
             "tuning": table, "gen_s": t_gen, "tune_s": t_tune, "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
+def _serve_requests(keys_n, key_max, R, seed, dec_max=16_000_000):
+    """The request mix of the serving workload: 40% access batches of 1..4096
+    ranks, 40% lower_bound batches of 1..4096 values, 20% range decodes of
+    log-uniform length in [1, 1.6e7]; column uniform."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    reqs, dec_total = [], 0
+    for u in range(R):
+        c = int(rng.integers(0, len(keys_n)))
+        r = rng.random()
+        if r < 0.4:
+            cnt = int(rng.integers(1, 4097))
+            reqs.append([1, c, cnt, 0, rng.integers(0, keys_n[c], size=cnt, dtype=np.uint64)])
+        elif r < 0.8:
+            cnt = int(rng.integers(1, 4097))
+            reqs.append([2, c, cnt, 0, rng.integers(0, key_max[c] + 1, size=cnt, dtype=np.uint64)])
+        else:
+            cnt = min(int(np.exp(rng.uniform(0, np.log(dec_max)))), keys_n[c])
+            b = int(rng.integers(0, keys_n[c] - cnt + 1))
+            reqs.append([3, c, cnt, b, None])
+            dec_total += cnt
+    arena = torch.empty(sum(q[2] for q in reqs), dtype=torch.uint64).pin_memory()
+    off = 0
+    for q in reqs:
+        q.append(arena[off:off + q[2]])
+        off += q[2]
+    return reqs, arena
+
+
+def _pcts(lat):
+    a = np.sort(np.asarray(lat))
+    return float(np.percentile(a, 50)), float(np.percentile(a, 99))
+
+
+def _run_server_open_loop(lc, srv, reqs, arrivals):
+    """Submit request i at time arrivals[i] (seconds from start); returns
+    latencies (completion - intended arrival, seconds) and the makespan."""
+    import threading
+
+    n = len(reqs)
+    submit_at = np.zeros(n)
+    done = {}
+
+    def drainer():
+        while len(done) < n:
+            for c in srv.wait(1024, 100_000):
+                done[c["user"]] = (time.perf_counter(), c)
+
+    th = threading.Thread(target=drainer)
+    th.start()
+    t0 = time.perf_counter()
+    for i, q in enumerate(reqs):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        submit_at[i] = time.perf_counter()
+        srv.submit(q[0], q[1], q[2], q[3], 0 if q[4] is None else q[4].ctypes.data, q[5].data_ptr(), user=i)
+    th.join()
+    # completion = submission (taken here) + the server's own submit-to-completion time
+    fin = [submit_at[i] + 1e-6 * done[i][1]["latency_us"] for i in range(n)]
+    t_end = max(fin)
+    lat = [fin[i] - (t0 + arrivals[i]) for i in range(n)]
+    bad = [done[i][1]["status"] for i in range(n) if done[i][1]["status"] != 0]
+    assert not bad, f"failed requests: {bad[:5]}"
+    return lat, t_end - t0
+
+
+def _run_plain_open_loop(lc, cols, reqs, arrivals, stream):
+    """The plain path: one request at a time, synchronously, in arrival order."""
+    n = len(reqs)
+    lat = []
+    t0 = time.perf_counter()
+    for i, q in enumerate(reqs):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        c = lc.lc_serve_sync(cols, q[0], q[1], q[2], q[3], 0 if q[4] is None else q[4].ctypes.data, q[5].data_ptr(),
+                             stream=stream)
+        assert c["status"] == 0
+        lat.append(time.perf_counter() - (t0 + arrivals[i]))
+    return lat, time.perf_counter() - t0
+
+
+def run_serve(args):
+    """Serving: 64 device-resident compressed uint64 columns of 5e7 keys
+    (generators of the large-column workload, eps = 63), open-loop Poisson
+    arrivals swept to saturation, p50/p99 latency and keys/s of the continuous-
+    batching server against the plain synchronous per-request path."""
+    import torch
+
+    from paper_2412_10770_gb300 import build as lcbuild
+    from paper_2412_10770_gb300 import inputs, lc
+
+    lcbuild.build()
+    lc.load()
+    torch.cuda.set_device(0)
+    sys.setswitchinterval(1e-4)  # the submitting loop spins; let the draining thread run promptly
+    stream = torch.cuda.Stream()
+    cols, keys_n, key_max, raw = [], [], [], 0
+    t0 = time.time()
+    for c in range(args.columns):
+        k = inputs.column_device(GENS[c % 3], args.column_keys, seed=inputs.seed_for(4, c))
+        cols.append(lc.lc_compress(k, eps=63))
+        keys_n.append(k.numel())
+        key_max.append(int(k[-1].view(torch.int64).item()))
+        raw += 8 * k.numel()
+        del k
+    torch.cuda.synchronize()
+    t_build = time.time() - t0
+    comp = sum(lc.lc_size(c) for c in cols)
+    reqs, arena = _serve_requests(keys_n, key_max, args.requests, seed=inputs.seed_for(4, 99))
+    keys_per_req = np.array([q[2] for q in reqs], dtype=np.float64)
+    budget = int(args.budget_gb * (1 << 30))
+    srv = lc.lc_server_create(cols, budget, slots=args.slots)
+    # closed loop: everything at once -> the server's saturation throughput
+    lat, span = _run_server_open_loop(lc, srv, reqs[:200], np.zeros(200))  # warm-up
+    lat, span = _run_server_open_loop(lc, srv, reqs, np.zeros(len(reqs)))
+    x_srv = len(reqs) / span
+    lat_p, span_p = _run_plain_open_loop(lc, cols, reqs[:600], np.zeros(600), stream)
+    x_plain = 600 / span_p
+    rng = np.random.default_rng(3)
+    sweep = []
+    for f in (0.1, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5):
+        rate = f * x_srv
+        n = int(min(len(reqs), max(200, rate * 2.0)))
+        arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        arr -= arr[0]
+        ls, ss = _run_server_open_loop(lc, srv, reqs[:n], arr)
+        s50, s99 = _pcts(ls)
+        row = {"rate_frac_of_server_saturation": f, "rate_req_per_s": rate, "requests": n,
+               "server": {"p50_ms": 1e3 * s50, "p99_ms": 1e3 * s99, "req_per_s": n / ss,
+                          "keys_per_s": keys_per_req[:n].sum() / ss}}
+        if rate <= 3 * x_plain:  # the plain path falls behind without bound above its own capacity
+            lp, sp = _run_plain_open_loop(lc, cols, reqs[:n], arr, stream)
+            p50, p99 = _pcts(lp)
+            row["plain"] = {"p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99, "req_per_s": n / sp,
+                            "keys_per_s": keys_per_req[:n].sum() / sp}
+        sweep.append(row)
+    st = srv.stats()
+    srv.close()
+    for c in cols:
+        c.free()
+    line = {"metric": METRIC, "value": keys_per_req.sum() / span, "unit": "keys/s", "n_gpus": 1,
+            "steps": len(sweep), "warmup": 1, "ms_per_step": 1e3 * span, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"serving: {args.columns} resident uint64 columns x {args.column_keys} keys "
+                                   "(lognormal/piecewise/clusters, eps=63); requests 40% access 1-4096, 40% "
+                                   "lower_bound 1-4096, 20% range decode log-uniform [1, 1.6e7]; open-loop Poisson",
+                       "slots": args.slots, "hbm_budget_gb": args.budget_gb, "requests": len(reqs)},
+            "closed_loop": {"server_req_per_s": x_srv, "server_keys_per_s": keys_per_req.sum() / span,
+                            "server_p50_ms": 1e3 * _pcts(lat)[0], "server_p99_ms": 1e3 * _pcts(lat)[1],
+                            "plain_req_per_s": x_plain, "plain_keys_per_s": keys_per_req[:600].sum() / span_p,
+                            "plain_p50_ms": 1e3 * _pcts(lat_p)[0], "plain_p99_ms": 1e3 * _pcts(lat_p)[1]},
+            "sweep": sweep, "server_stats": st, "ratio": comp / raw, "build_s": t_build}
     print(json.dumps(line), flush=True)
 
 

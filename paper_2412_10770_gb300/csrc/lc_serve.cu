@@ -302,7 +302,7 @@ void scheduler(lc_server* s) {
                 continue;
             }
         }
-        if (active) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (active) std::this_thread::yield();
     }
 }
 

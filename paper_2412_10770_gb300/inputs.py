@@ -210,3 +210,38 @@ def posting_lists_device(n_lists: int, total: int, universe: int, seed: int, alp
         del key
         l0 = l1
     return out.view(torch.uint32), begin
+
+
+def column_device(kind: str, n: int, seed: int, device: str = "cuda"):
+    """The generators of ``column`` drawn on the GPU (same recipes, torch RNG),
+    for workloads with many large columns.  Returns a uint64 tensor."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    if kind == "lognormal":
+        z = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+        gaps = torch.floor(torch.exp(2.0 + 1.5 * z)).to(torch.int64) + 1
+        return torch.cumsum(gaps, 0).view(torch.uint64)
+    if kind == "piecewise":
+        regimes = max(1, min(1000, n))
+        edges = (torch.arange(regimes + 1, device=device, dtype=torch.int64) * n) // regimes
+        lens = edges[1:] - edges[:-1]
+        slopes = torch.exp(torch.empty(regimes, device=device, dtype=torch.float64).uniform_(
+            0.0, float(np.log(1e4)), generator=g))
+        base = 9 + torch.cumsum(torch.floor(slopes * lens.double()).to(torch.int64), 0) - \
+            torch.floor(slopes * lens.double()).to(torch.int64)
+        r = torch.repeat_interleave(torch.arange(regimes, device=device), lens)
+        t = torch.arange(n, device=device, dtype=torch.int64) - edges[:-1][r]
+        jit = torch.randint(-8, 9, (n,), generator=g, device=device, dtype=torch.int64)
+        k = base[r] + torch.floor(slopes[r] * t.double()).to(torch.int64) + jit
+        idx = torch.arange(n, device=device, dtype=torch.int64)
+        k = torch.cummax(k - idx, 0).values + idx
+        return k.view(torch.uint64)
+    if kind == "clusters":
+        gaps = torch.randint(1, 4, (n,), generator=g, device=device, dtype=torch.int64)
+        heads = torch.arange(0, n, 2000, device=device)
+        gaps[heads] = torch.randint(10**6, 10**9 + 1, (heads.numel(),), generator=g, device=device,
+                                    dtype=torch.int64)
+        return torch.cumsum(gaps, 0).view(torch.uint64)
+    raise ValueError(kind)
