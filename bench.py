@@ -318,6 +318,8 @@ def main():
     sampler.start()
     time.sleep(0.3)
     launches0 = lc.lc_launch_count()
+    lc.lc_timing_read()  # drop anything recorded before the timed region
+    lc.lc_timing_enable(True)
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     evs = []
@@ -327,6 +329,8 @@ def main():
     t_end.record(stream)
     torch.cuda.synchronize()
     launches = lc.lc_launch_count() - launches0
+    lc.lc_timing_enable(False)
+    ktimes = lc.lc_timing_read()
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end) / args.steps
     if pg:
@@ -367,18 +371,37 @@ def main():
                         "unit": "keys/s" if p in ("compress", "decode", "range_decode") else "queries/s",
                         "alg_gbs": alg[p] / sec / 1e9, "hbm_frac": alg[p] / sec / 1e9 / peak,
                         "per_column_ms": {g: ph_ms_col[g][p] / K for g in gens}}
-    dom = max(phases, key=lambda p: ph_ms[p])
-    dom_launch_ms = ph_ms[dom] / K / ncols
-    achieved = alg[dom] / ncols / (dom_launch_ms / 1e3) / 1e9
+    # per kernel: algorithmic bytes of all its launches in the timed region
+    L_all = sum(sizes[g][1] for g in gens)
+    W_all = sum(sizes[g][2] for g in gens)
+    segb = kb + 8 + 4 + 2 + 1
+    kalg = {
+        "fit_spec": K * (ncols * N * kb + ncols * N * 17 / 32),
+        "fit_chain": K * (ncols * N * 17 / 32 + ncols * N / 8),
+        "model": K * (ncols * N * kb + ncols * N / 8 + L_all * segb),
+        "pack": K * (ncols * N * kb + ncols * N / 8 + L_all * segb + 8 * W_all),
+        "decode": K * alg["decode"],
+        "decode_ranges": K * alg["range_decode"],
+        "access": K * alg["access"],
+        "lower_bound": K * alg["lower_bound"],
+    }
+    kernels = {}
+    for name, (nl, tms) in ktimes.items():
+        kernels[name] = {"launches": nl, "ms_per_launch": tms / max(nl, 1), "share": tms / (K * ms)}
+        if name in kalg and tms > 0:
+            kernels[name]["alg_gbs"] = kalg[name] / (tms / 1e3) / 1e9
+            kernels[name]["hbm_frac"] = kernels[name]["alg_gbs"] / peak
+    dom = max((k for k in kernels if k in kalg), key=lambda k: ktimes[k][1])
+    achieved = kernels[dom]["alg_gbs"]
     value = world * ncols * N / (ms / 1e3)
 
     line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": workload_config(args),
-            "phases": phase_out,
+            "phases": phase_out, "kernels": kernels,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
-                         "traffic": None},
+                         "ms_per_launch": kernels[dom]["ms_per_launch"], "traffic": None},
             "ratio": {g: blob_bytes[g] / (N * kb) for g in gens},
             "segments": {g: sizes[g][1] for g in gens},
             "clocks": clocks, "gpu_launches": launches}

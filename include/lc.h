@@ -274,6 +274,19 @@ int lc_version(void);
 /* Diagnostics: kernels this process has launched through the library so far. */
 uint64_t lc_launch_count(void);
 
+/* Tracing: while enabled, every kernel the library launches is bracketed by
+ * two CUDA events recorded on its own stream, and its device time is added to
+ * a per-kernel total.  lc_timing_read waits for the recorded work, returns up
+ * to `max` entries (name, launches, total milliseconds) and resets the totals.
+ * Enabling costs two event records per launch. */
+typedef struct {
+    char name[40];
+    uint64_t launches;
+    double total_ms;
+} lc_kernel_time;
+int lc_timing_enable(int on);
+int lc_timing_read(lc_kernel_time* out, int max, int* got);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,7 +5,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "lc_internal.h"
@@ -15,6 +18,36 @@ namespace lcx {
 static std::atomic<uint64_t> g_launches{0};
 
 void note_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+std::atomic<bool> g_timing{false};
+std::mutex g_timing_mu;
+struct TimedLaunch {
+    std::string name;
+    cudaEvent_t a, b;
+};
+std::vector<TimedLaunch> g_timed;
+std::map<std::string, std::pair<uint64_t, double>> g_totals;
+}  // namespace
+
+KTime::KTime(const char* n, cudaStream_t s) : name(n), st(s), a(nullptr), b(nullptr) {
+    if (!g_timing.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        a = b = nullptr;
+        return;
+    }
+    cudaEventRecord(a, st);
+}
+
+KTime::~KTime() {
+    if (!a) return;
+    cudaEventRecord(b, st);
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timed.push_back(TimedLaunch{name, a, b});
+}
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return LC_OK;
@@ -136,6 +169,39 @@ extern "C" {
 int lc_version(void) { return 10000; }
 
 uint64_t lc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int lc_timing_enable(int on) {
+    g_timing.store(on != 0);
+    return LC_OK;
+}
+
+int lc_timing_read(lc_kernel_time* out, int max, int* got) {
+    if (!got || (max > 0 && !out)) return LC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    for (TimedLaunch& t : g_timed) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            auto& e = g_totals[t.name];
+            e.first += 1;
+            e.second += ms;
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    g_timed.clear();
+    int n = 0;
+    for (auto& kv : g_totals) {
+        if (n >= max) break;
+        memset(out[n].name, 0, sizeof(out[n].name));
+        strncpy(out[n].name, kv.first.c_str(), sizeof(out[n].name) - 1);
+        out[n].launches = kv.second.first;
+        out[n].total_ms = kv.second.second;
+        ++n;
+    }
+    g_totals.clear();
+    *got = n;
+    return LC_OK;
+}
 
 const char* lc_strerror(int s) {
     switch (s) {

@@ -896,9 +896,12 @@ int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n, ScanOp op, voi
     const uint64_t nb = (n + kScanTile - 1) / kScanTile;
     if (tmp_bytes < nb * sizeof(uint64_t)) return LC_ERR_INTERNAL;
     uint64_t* part = (uint64_t*)tmp;
-    scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, op, part);
-    scan_parts<<<1, kScanThreads, 0, st>>>(part, nb);
-    scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, op, part, out);
+    {
+        KTime kt("scan", st);
+        scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, op, part);
+        scan_parts<<<1, kScanThreads, 0, st>>>(part, nb);
+        scan_final<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, op, part, out);
+    }
     note_launch(3);
     return cuda_status(cudaGetLastError());
 }
@@ -942,27 +945,39 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
             if (rc) return rc;
             attr[sizeof(KT) == 8] = true;
         }
-        spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.fix,
-                                                                        fs.exitS, fs.exitF, fs.sync, status);
-        chain_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0, st>>>(
-            keys, chunks_d, C, fs.spec, fs.fix, fs.exitS, fs.exitF, fs.sync, tbits, counts);
+        {
+            KTime kt("fit_spec", st);
+            spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.fix,
+                                                                            fs.exitS, fs.exitF, fs.sync, status);
+        }
+        {
+            KTime kt("fit_chain", st);
+            chain_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0, st>>>(
+                keys, chunks_d, C, fs.spec, fs.fix, fs.exitS, fs.exitF, fs.sync, tbits, counts);
+        }
         note_launch(2);
         int rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         return scan_exclusive(counts, csb, C, ScanOp::Identity, tmp, tmp_bytes, st);
     }
-    model_kernel<KT><<<(unsigned)C, kModelThreads, 0, st>>>(
-        keys, chunks_d, tbits, (const uint64_t*)(blob + lay.csb), (KT*)(blob + lay.icpt), (int64_t*)(blob + lay.slope),
-        (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start), (uint8_t*)(blob + lay.width), counts);
+    {
+        KTime kt("model", st);
+        model_kernel<KT><<<(unsigned)C, kModelThreads, 0, st>>>(
+            keys, chunks_d, tbits, (const uint64_t*)(blob + lay.csb), (KT*)(blob + lay.icpt), (int64_t*)(blob + lay.slope),
+            (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start), (uint8_t*)(blob + lay.width), counts);
+    }
     note_launch();
     int rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
     rc = scan_exclusive(counts, (uint64_t*)(blob + lay.cwb), C, ScanOp::BitsToEvenWords, tmp, tmp_bytes, st);
     if (rc) return rc;
-    pack_kernel<KT><<<(unsigned)C, kPackThreads, 0, st>>>(
-        keys, chunks_d, tbits, (const uint64_t*)(blob + lay.csb), (const uint64_t*)(blob + lay.cwb),
-        (const KT*)(blob + lay.icpt), (const int64_t*)(blob + lay.slope), (const uint32_t*)(blob + lay.bitoff),
-        (const uint16_t*)(blob + lay.start), (const uint8_t*)(blob + lay.width), (uint32_t*)(blob + lay.payload));
+    {
+        KTime kt("pack", st);
+        pack_kernel<KT><<<(unsigned)C, kPackThreads, 0, st>>>(
+            keys, chunks_d, tbits, (const uint64_t*)(blob + lay.csb), (const uint64_t*)(blob + lay.cwb),
+            (const KT*)(blob + lay.icpt), (const int64_t*)(blob + lay.slope), (const uint32_t*)(blob + lay.bitoff),
+            (const uint16_t*)(blob + lay.start), (const uint8_t*)(blob + lay.width), (uint32_t*)(blob + lay.payload));
+    }
     note_launch();
     return cuda_status(cudaGetLastError());
 }

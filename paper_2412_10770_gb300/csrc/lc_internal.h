@@ -184,4 +184,14 @@ int cuda_status(cudaError_t e);
 // Count of kernel launches issued by the library in this process.
 void note_launch(uint32_t k = 1);
 
+// Tracing (lc_timing_enable): brackets one launch with CUDA events on its
+// stream when tracing is on.  Use as { KTime kt("name", st); kernel<<<...>>>(); }
+struct KTime {
+    KTime(const char* name, cudaStream_t st);
+    ~KTime();
+    const char* name;
+    cudaStream_t st;
+    cudaEvent_t a, b;
+};
+
 }  // namespace lcx

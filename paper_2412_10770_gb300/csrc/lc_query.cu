@@ -601,7 +601,10 @@ static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_
         occ < 1)
         occ = 1;
     const uint64_t grid = std::min<uint64_t>(nt, (uint64_t)sm_count() * occ);
-    decode_kernel<KT><<<(unsigned)grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count, (KT*)out);
+    {
+        KTime kt("decode", st);
+        decode_kernel<KT><<<(unsigned)grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count, (KT*)out);
+    }
     note_launch();
     return cuda_status(cudaGetLastError());
 }
@@ -631,14 +634,19 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
     if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, tmp_b, st);
     if (!rc) {
         const unsigned grid = (unsigned)(sm_count() * 4);
+        const size_t smem = dec_smem(col->view.max_tile_segs);
         if (col->key_bytes == 4) {
-            if (!(rc = set_smem<uint32_t>()))
-                decode_ranges_kernel<uint32_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off,
-                                                                                   m, first, work_off, (uint32_t*)out);
+            if (!(rc = set_smem<uint32_t>())) {
+                KTime kt("decode_ranges", st);
+                decode_ranges_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(col->view, begin, count, out_off, m,
+                                                                               first, work_off, (uint32_t*)out);
+            }
         } else {
-            if (!(rc = set_smem<uint64_t>()))
-                decode_ranges_kernel<uint64_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off,
-                                                                                   m, first, work_off, (uint64_t*)out);
+            if (!(rc = set_smem<uint64_t>())) {
+                KTime kt("decode_ranges", st);
+                decode_ranges_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(col->view, begin, count, out_off, m,
+                                                                               first, work_off, (uint64_t*)out);
+            }
         }
         if (!rc) {
             note_launch();
@@ -652,8 +660,11 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st) {
     if (m == 0) return LC_OK;
     const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
-    if (col->key_bytes == 4) access_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, idx, m, (uint32_t*)out);
-    else access_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, idx, m, (uint64_t*)out);
+    {
+        KTime kt("access", st);
+        if (col->key_bytes == 4) access_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, idx, m, (uint32_t*)out);
+        else access_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, idx, m, (uint64_t*)out);
+    }
     note_launch();
     return cuda_status(cudaGetLastError());
 }
@@ -664,10 +675,13 @@ int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* ou
     const uint64_t ntop = v.top ? v.level_n[v.top] : v.L;
     const size_t smem = 8 * std::max<uint64_t>(ntop, 1);
     const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 6);
-    if (col->key_bytes == 4)
-        lower_bound_kernel<uint32_t><<<grid, 256, smem, st>>>(v, (const uint32_t*)vals, m, out);
-    else
-        lower_bound_kernel<uint64_t><<<grid, 256, smem, st>>>(v, (const uint64_t*)vals, m, out);
+    {
+        KTime kt("lower_bound", st);
+        if (col->key_bytes == 4)
+            lower_bound_kernel<uint32_t><<<grid, 256, smem, st>>>(v, (const uint32_t*)vals, m, out);
+        else
+            lower_bound_kernel<uint64_t><<<grid, 256, smem, st>>>(v, (const uint64_t*)vals, m, out);
+    }
     note_launch();
     return cuda_status(cudaGetLastError());
 }

@@ -33,7 +33,8 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
            "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
            "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free", "lc_server_create", "lc_server_submit",
-           "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync")
+           "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
+           "lc_timing_enable", "lc_timing_read")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -53,6 +54,10 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("segments", ctypes.c_uint64),
                 ("words", ctypes.c_uint64), ("lists", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
                 ("eps", ctypes.c_uint64), ("key_bytes", ctypes.c_uint32), ("chunk_log2", ctypes.c_uint32)]
+
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
 
 class _Request(ctypes.Structure):
@@ -126,6 +131,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_server_stats": ([p, ctypes.POINTER(_ServerStats)], i32),
         "lc_server_destroy": ([p], i32),
         "lc_serve_sync": ([p, ctypes.c_int, ctypes.POINTER(_Request), p, ctypes.POINTER(_Completion)], i32),
+        "lc_timing_enable": ([ctypes.c_int], i32),
+        "lc_timing_read": ([ctypes.POINTER(_KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -504,3 +511,18 @@ def lc_serve_sync(cols, op: int, column: int, count: int, begin: int = 0, inp: i
     c = _Completion()
     _check(lib.lc_serve_sync(arr, len(cols), ctypes.byref(r), _stream(stream), ctypes.byref(c)), "lc_serve_sync")
     return _completion_dict(c)
+
+
+# ---------------------------------------------------------------- tracing
+
+
+def lc_timing_enable(on: bool = True) -> None:
+    _check(load().lc_timing_enable(1 if on else 0), "lc_timing_enable")
+
+
+def lc_timing_read() -> dict:
+    """Per-kernel device time recorded since the last read: {name: (launches, total_ms)}."""
+    buf = (_KernelTime * 64)()
+    got = ctypes.c_int()
+    _check(load().lc_timing_read(buf, 64, ctypes.byref(got)), "lc_timing_read")
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(got.value)}
