@@ -36,6 +36,11 @@
  *   - Keys are unsigned integers of key_bytes = 4 or 8 bytes, little-endian.
  *   - An lc_column owns its device memory; free it with lc_free.  A column may
  *     be read (decode, access, lower_bound) from several streams at once.
+ *   - Device memory comes from the device's default stream-ordered pool
+ *     (cudaMallocAsync).  The first lc_compress / lc_compress_batch /
+ *     lc_deserialize on a device raises that pool's release threshold to
+ *     8 GiB, so that up to 8 GiB of freed blocks stay mapped for the next
+ *     column instead of being returned to the driver at every synchronisation.
  *   - Device-side errors (an index >= N in lc_access) are recorded in the
  *     column's status word and reported by lc_status.
  */

@@ -4,6 +4,7 @@
 // and lc_query.cu.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -47,6 +48,21 @@ KTime::~KTime() {
     cudaEventRecord(b, st);
     std::lock_guard<std::mutex> lk(g_timing_mu);
     g_timed.push_back(TimedLaunch{name, a, b});
+}
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+HTime::HTime(const char* n) : name(n), t0(g_timing.load(std::memory_order_relaxed) ? now_ms() : -1.0) {}
+
+HTime::~HTime() {
+    if (t0 < 0) return;
+    const double dt = now_ms() - t0;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    auto& e = g_totals[std::string("host:") + name];
+    e.first += 1;
+    e.second += dt;
 }
 
 int cuda_status(cudaError_t e) {
@@ -120,10 +136,31 @@ static std::vector<uint8_t> build_prefix(const lc_column* col, const uint64_t* l
     return b;
 }
 
+// Keep up to kPoolRetain bytes of freed pool memory mapped (once per device):
+// a column's blob, directories and scratch are allocated and freed per call,
+// and re-mapping them after every synchronisation costs milliseconds.
+constexpr uint64_t kPoolRetain = 8ull << 30;
+
+static void retain_pool(int dev) {
+    static std::once_flag once[64];
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(once[dev], [dev] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        uint64_t cur = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < kPoolRetain) {
+            uint64_t thr = kPoolRetain;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
 static lc_column* new_column() {
     lc_column* c = new (std::nothrow) lc_column;
     if (!c) return nullptr;
     memset((void*)c, 0, sizeof(*c));
+    cudaGetDevice(&c->device);
+    retain_pool(c->device);
     return c;
 }
 
@@ -144,9 +181,14 @@ static uint64_t bound_words(uint64_t n, uint64_t eps) {
 // Builds the empty-N or full column from a finished device blob.
 static int finish_column(lc_column* col, cudaStream_t st, const uint64_t* lb, const uint64_t* lcb, const uint64_t* le,
                          const uint8_t* lg) {
-    std::vector<uint8_t> prefix = build_prefix(col, lb, lcb, le, lg);
-    int rc = finish_blob(col, prefix.data(), prefix.size(), st);
+    int rc;
+    {
+        HTime ht("finish_blob");
+        std::vector<uint8_t> prefix = build_prefix(col, lb, lcb, le, lg);
+        rc = finish_blob(col, prefix.data(), prefix.size(), st);
+    }
     if (rc) return rc;
+    HTime ht("derived");
     return build_derived(col, st);
 }
 
@@ -222,6 +264,7 @@ const char* lc_strerror(int s) {
 
 void lc_free(lc_column* col) {
     if (!col) return;
+    HTime ht("free");
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != col->device) cudaSetDevice(col->device);
@@ -623,6 +666,7 @@ int lc_status(const lc_column* col, void* stream) {
     if (s) cudaMemset(col->status, 0, 4);
     if (s & kStOutOfRange) return LC_ERR_OUT_OF_RANGE;
     if (s & kStUnsorted) return LC_ERR_UNSORTED;
+    if (s & kStTimeout) return LC_ERR_TIMEOUT;
     if (s) return LC_ERR_INTERNAL;
     return LC_OK;
 }

@@ -7,14 +7,16 @@
 //                 block (S) and a re-walk from the predicted entry (F), on keys
 //                 staged in shared memory.
 //   chain_kernel  one warp per chunk chains the blocks in order (R): the true
-//                 anchors as one bit per key, and the segment count per chunk.
+//                 anchors as one bit per key, and the segment count per chunk;
+//                 the slope of every segment longer than 64 keys (its walk
+//                 ends with the segment's cone).
 //   scan          chunk_seg_begin.
-//   model_kernel  one CTA per chunk.  Every segment's cone is the intersection
-//                 of its keys' slope intervals, so with the anchors known it is a
-//                 segmented max/min over keys (exact rational comparisons, one
-//                 division per cone edge).  Then the slope (floor midpoint),
-//                 the width (bit length of the largest zigzag residual) and the
-//                 bit offsets.  Writes the segment arrays of the blob.
+//   fit_short_kernel  one CTA per 8192-key window, one thread per 32-key
+//                 block: the cone, slope and width of every segment of at most
+//                 64 keys that starts in the block (sequential, keys in shared
+//                 memory); longer segments queue their width pass.
+//   long_width_kernel  one warp per 2048-key piece of a long segment.
+//   bitoff_kernel one CTA per chunk: bit offsets (a scan of w (n-1)).
 //   scan          chunk_word_begin.
 //   pack_kernel   one CTA per chunk, 2048-key windows assembled in shared memory
 //                 with shared atomics, then stored as whole 32-bit words.
@@ -50,9 +52,10 @@ __device__ __forceinline__ uint64_t ldk(const KT* __restrict__ K, uint32_t i) {
 // every key, and the first lane whose cone is empty is the next anchor.  The
 // next step's keys are loaded while this step computes; keys further ahead are
 // prefetched into L2.  Called with all 32 lanes active and warp-uniform
-// arguments.
+// arguments.  *fin receives the cone of the segment's keys (every lane).
 template <typename KT>
-__device__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, int64_t eps, uint32_t lane) {
+__device__ __forceinline__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, int64_t eps, uint32_t lane,
+                              Frac* fin) {
     const uint64_t kx = ldk(K, x);
     Frac cone = frac_open();
     uint32_t p = x + 1;
@@ -78,7 +81,10 @@ __device__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, 
                                            !frac_gt((int64_t)D - eps, d, cone.X, cone.E) &&
                                            (D + (uint64_t)eps + 1) * (uint64_t)cone.F >= cone.Y * (uint64_t)d);
             if (__all_sync(0xFFFFFFFFu, inside)) {
-                if (p + 32 >= n) return n;
+                if (p + 32 >= n) {
+                    *fin = cone;
+                    return n;
+                }
                 p += 32;
                 continue;
             }
@@ -110,13 +116,25 @@ __device__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, 
         if (frac_gt(cone.X, cone.E, v.X, v.E)) { v.X = cone.X; v.E = cone.E; }
         if (cone.Y * (uint64_t)v.F < v.Y * (uint64_t)cone.F) { v.Y = cone.Y; v.F = cone.F; }
         const uint32_t badm = __ballot_sync(0xFFFFFFFFu, !frac_ok(v));
-        if (badm) return min(p + (uint32_t)(__ffs(badm) - 1), n);
+        if (badm) {
+            // the cone just before the first key that empties it
+            const int bl = __ffs(badm) - 1;
+            const int src = bl > 0 ? bl - 1 : 0;
+            Frac f;
+            f.X = __shfl_sync(0xFFFFFFFFu, v.X, src);
+            f.E = __shfl_sync(0xFFFFFFFFu, v.E, src);
+            f.Y = __shfl_sync(0xFFFFFFFFu, v.Y, src);
+            f.F = __shfl_sync(0xFFFFFFFFu, v.F, src);
+            *fin = bl > 0 ? f : cone;
+            return min(p + (uint32_t)bl, n);
+        }
         cone.X = __shfl_sync(0xFFFFFFFFu, v.X, 31);
         cone.E = __shfl_sync(0xFFFFFFFFu, v.E, 31);
         cone.Y = __shfl_sync(0xFFFFFFFFu, v.Y, 31);
         cone.F = __shfl_sync(0xFFFFFFFFu, v.F, 31);
         p += 32;
     }
+    *fin = cone;
     return n;
 }
 
@@ -129,6 +147,38 @@ constexpr int kSpecThreads = kWinKeys / kFB;    // 256
 constexpr uint32_t kStageKeys = kWinKeys + kFB + kFCap;
 constexpr uint32_t kStageSlots = kStageKeys + kStageKeys / 32 + 1;
 constexpr int kChainThreads = 128;              // four chunks per CTA, one warp each
+constexpr uint32_t kShortMax = 64;              // segments of at most this many keys: one thread fits each
+constexpr uint32_t kPiece = 2048;               // keys per work item of a long segment's width pass
+
+// A segment longer than kShortMax keys, as its walk in the chain found it.
+struct LongInfo {
+    int64_t M;     // slope
+    uint32_t end;  // next anchor (chunk-relative) or the chunk's length
+    uint32_t pad;
+};
+// The width pass of one long segment: keys key0 + [1, n), running max of the
+// zigzag residuals in zmax.
+struct LongItem {
+    uint64_t key0;
+    int64_t M;
+    uint32_t n;
+    uint32_t zmax;
+    uint64_t pad;
+};
+// A long segment met by a window of fit_short_kernel: segment j, anchored at
+// chunk position a, len keys, slope M; its pieces start at poff in the window.
+struct WinLong {
+    uint64_t j;
+    int64_t M;
+    uint32_t a, len, poff, pad;
+};
+constexpr uint32_t kLongPerWin = kWinKeys / (kShortMax + 1) + 1;  // segments > 64 keys starting in 8192 keys
+// Keys key0 + [t0, t1) of long segment `item`.
+struct Piece {
+    uint32_t item;
+    uint32_t t0, t1;
+    uint32_t pad;
+};
 
 // A window's keys staged in shared memory: local key q sits in slot q + q/32,
 // so that lanes walking 32 consecutive 32-key blocks read distinct banks.
@@ -259,12 +309,17 @@ spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, c
 // ballot over 32 blocks takes the whole run of consistent blocks at once.
 // Elsewhere the warp walks the cone itself (32 keys per step) until it meets a
 // speculative anchor.  Output: the chunk's anchor bitmap and segment count.
+// Every segment longer than kShortMax keys is found by such a walk (the
+// speculative walks stop kFCap keys past their block), and the walk ends with
+// the segment's cone: its slope and end are recorded at the anchor's block
+// (at most one such segment starts in a block).
 template <typename KT>
-__global__ void __launch_bounds__(kChainThreads)
+__global__ void __launch_bounds__(kChainThreads, 1)
 chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, uint64_t C,
              const uint32_t* __restrict__ spec_g, const uint32_t* __restrict__ fix_g,
              const uint32_t* __restrict__ exitS_g, const uint32_t* __restrict__ exitF_g,
-             const uint8_t* __restrict__ sync_g, uint32_t* __restrict__ tbits, uint32_t* __restrict__ counts) {
+             const uint8_t* __restrict__ sync_g, uint32_t* __restrict__ tbits, uint32_t* __restrict__ counts,
+             LongInfo* __restrict__ longinfo) {
     const uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     if (c >= C) return;  // whole warps leave together
     const uint32_t lane = threadIdx.x & 31u;
@@ -274,6 +329,14 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
     const int64_t eps = cd.eps;
     const uint64_t gb = cd.bitword_begin;
     uint32_t* __restrict__ T = tbits + gb;
+    const uint64_t* __restrict__ magic = g_magic;
+    // walk the segment anchored at a; record it when it is long
+    auto walk = [&](uint32_t a) {
+        Frac f;
+        const uint32_t e = warp_walk(K, a, n, eps, lane, &f);
+        if (e - a > kShortMax && lane == 0) longinfo[gb + (a >> 5)] = LongInfo{frac_slope(f, magic), e, 0u};
+        return e;
+    };
     uint32_t x = 0, knext = 0, total = 0;
     while (x < n) {
         const uint32_t k = x / kFB;
@@ -297,7 +360,7 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
             total += __reduce_add_sync(0xFFFFFFFFu, lane < r ? (uint32_t)__popc(m) : 0u);
             uint32_t xl = __shfl_sync(0xFFFFFFFFu, eF, r - 1);
             const uint32_t ml = __shfl_sync(0xFFFFFFFFu, m, r - 1);
-            if (xl == kNone) xl = warp_walk(K, (k + r - 1) * kFB + 31u - (uint32_t)__clz(ml), n, eps, lane);
+            if (xl == kNone) xl = walk((k + r - 1) * kFB + 31u - (uint32_t)__clz(ml));
             knext = k + r;
             x = xl;
         } else {
@@ -308,11 +371,11 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
                 if ((sm >> (xn - b)) & 1u) {
                     m |= sm & (0xFFFFFFFFu << (xn - b));
                     xn = __ldg(exitS_g + gb + k);
-                    if (xn == kNone) xn = warp_walk(K, b + 31u - (uint32_t)__clz(m), n, eps, lane);
+                    if (xn == kNone) xn = walk(b + 31u - (uint32_t)__clz(m));
                     break;
                 }
                 m |= 1u << (xn - b);
-                xn = warp_walk(K, xn, n, eps, lane);
+                xn = walk(xn);
             }
             if (lane == 0) T[k] = m;
             total += __popc(m);
@@ -370,365 +433,213 @@ struct MaxOp {
 
 // ------------------------------------------------------------------ model
 
-// Rational running extremes of one piece of a segment: max over keys of
-// (D - eps)/d and min over keys of (D + eps + 1)/d.
-struct Cone {
-    int64_t X;   // numerator of the max lower slope / 2^32
-    uint64_t Y;  // numerator of the min upper slope / 2^32
-    uint32_t E, F;
-    uint32_t has;
-};
-
-__device__ __forceinline__ void cone_merge(Cone& c, const Cone& o) {
-    if (!o.has) return;
-    if (!c.has) { c = o; return; }
-    if (o.X * (int64_t)c.E > c.X * (int64_t)o.E) { c.X = o.X; c.E = o.E; }
-    if (o.Y * (uint64_t)c.F < c.Y * (uint64_t)o.F) { c.Y = o.Y; c.F = o.F; }
-}
-
-// Slope of a closed segment: the floor midpoint of [LO, HI] with
-// LO = ceil(2^32 X/E) and HI = min(ceil(2^32 Y/F) - 1, INT64_MAX); 0 for a
-// single key.
-__device__ __forceinline__ int64_t cone_slope(const Cone& c, const uint64_t* __restrict__ magic) {
-    if (!c.has) return 0;
-    const int64_t LO = ceil_q32(c.X, c.E, magic);
-    int64_t HI;
-    if (c.Y >= ((uint64_t)c.F << 31)) HI = INT64_MAX;
-    else HI = ceil_q32((int64_t)c.Y, c.F, magic) - 1;
-    return LO + (int64_t)(((uint64_t)HI - (uint64_t)LO) >> 1);
-}
-
-__device__ __forceinline__ bool tbit(const uint32_t* s_T, uint32_t i) { return (s_T[i >> 5] >> (i & 31u)) & 1u; }
-
-__device__ __forceinline__ Cone shfl_up_cone(const Cone& v, int off) {
-    Cone u;
-    u.X = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
-    u.Y = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
-    u.E = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
-    u.F = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
-    u.has = __shfl_up_sync(0xFFFFFFFFu, v.has, off);
-    return u;
-}
-
-// Merge of one Cone per lane into every lane (butterfly).
-__device__ __forceinline__ Cone warp_reduce_cone(Cone v) {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        Cone u;
-        u.X = __shfl_xor_sync(0xFFFFFFFFu, v.X, m);
-        u.Y = __shfl_xor_sync(0xFFFFFFFFu, v.Y, m);
-        u.E = __shfl_xor_sync(0xFFFFFFFFu, v.E, m);
-        u.F = __shfl_xor_sync(0xFFFFFFFFu, v.F, m);
-        u.has = __shfl_xor_sync(0xFFFFFFFFu, v.has, m);
-        cone_merge(v, u);
-    }
-    return v;
-}
-
-__device__ __forceinline__ Cone shfl_cone(const Cone& v, int src) {
-    Cone u;
-    u.X = __shfl_sync(0xFFFFFFFFu, v.X, src);
-    u.Y = __shfl_sync(0xFFFFFFFFu, v.Y, src);
-    u.E = __shfl_sync(0xFFFFFFFFu, v.E, src);
-    u.F = __shfl_sync(0xFFFFFFFFu, v.F, src);
-    u.has = __shfl_sync(0xFFFFFFFFu, v.has, src);
-    return u;
-}
-
-// One CTA per chunk, eight warps, warp w on keys [w R, (w+1) R).  A warp steps
-// through its keys 32 at a time (lane = key, coalesced loads) carrying the open
-// segment across steps.  Pass 1: a segmented scan over the lanes (boundaries at
-// the anchors) of the exact rational extremes max (D-eps)/d and
-// min (D+eps+1)/d gives each segment's cone at its last key, hence its slope.
-// Pass 2: the same scan over the zigzag residuals gives each width.  A segment
-// still open at the end of a warp's keys (its "head") is finished from the
-// first pieces of the following warps.  Pass 3: the bit offsets, a scan over
-// the chunk's segments.
+// Segment models with the anchors known.  A segment's cone is the
+// intersection of its keys' slope intervals (Def. 2 with the anchored Q32
+// line), i.e. max (D-eps)/d and min (D+eps+1)/d over its keys; the slope is
+// the floor midpoint of the resulting integer interval, and the width is the
+// bit length of the largest zigzag residual under that slope (Sec. II-A).
+//
+// fit_short_kernel: one CTA per 8192-key window, keys staged in shared memory
+// (plus kShortMax keys of right halo), one thread per 32-key block: the
+// thread fits every segment that starts in its block and has at most
+// kShortMax keys, two short sequential passes (cone, then residuals), and
+// writes its intercept, start, slope and width.  A longer segment takes the
+// slope its chain walk recorded; its widths pass is queued as pieces of
+// kPiece keys (long_width_kernel) and its entry is finished by bitoff_kernel.
 template <typename KT>
-__global__ void __launch_bounds__(kModelThreads)
-model_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks,
-             const uint32_t* __restrict__ tbits, const uint64_t* __restrict__ csb, KT* __restrict__ icpt,
-             int64_t* __restrict__ slope, uint32_t* __restrict__ bitoff, uint16_t* __restrict__ start,
-             uint8_t* __restrict__ width, uint32_t* __restrict__ chunk_bits) {
-    constexpr uint32_t NW = kModelThreads / 32;
-    __shared__ uint32_t s_T[kMaxChunk / 32 + 1];
-    __shared__ Cone s_part[NW], s_head[NW];
-    __shared__ uint32_t s_cnt[NW], s_head_anchor[NW], s_part_z[NW], s_head_z[NW];
-    __shared__ int32_t s_last[NW];
-    __shared__ uint64_t s_head_rank[NW], s_head_ka[NW];
-    __shared__ int64_t s_head_M[NW];
-    __shared__ uint32_t s_scan[32];
-
-    const ChunkDesc cd = chunks[blockIdx.x];
+__global__ void __launch_bounds__(kSpecThreads)
+fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
+                 const uint32_t* __restrict__ tbits, const uint64_t* __restrict__ csb,
+                 const LongInfo* __restrict__ longinfo, KT* __restrict__ icpt, int64_t* __restrict__ slope,
+                 uint32_t* __restrict__ bitoff, uint16_t* __restrict__ start, uint8_t* __restrict__ width,
+                 LongItem* __restrict__ items, uint32_t* __restrict__ nitems, uint32_t items_cap,
+                 Piece* __restrict__ pieces, uint32_t* __restrict__ npieces, uint32_t pieces_cap,
+                 uint32_t* __restrict__ status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    constexpr uint32_t kWords = kWinKeys / kFB;
+    __shared__ uint32_t s_T[kWords + 4];
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_base, s_nlong, s_item0, s_piece0;
+    __shared__ WinLong s_long[kLongPerWin];
+    const WinDesc wd = wins[blockIdx.x];
+    const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
-    const uint32_t n = cd.n;
+    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
     const int64_t eps = cd.eps;
-    const uint64_t* __restrict__ magic = g_magic;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
-    const uint32_t nwords = (n + 31) / 32;
-    for (uint32_t q = tid; q < nwords; q += kModelThreads) s_T[q] = tbits[cd.bitword_begin + q];
-    if (tid == 0) s_T[nwords] = 0;
-    const uint32_t R = ((n + NW * 32 - 1) / (NW * 32)) * 32;
-    const uint32_t r0 = min(n, w * R), r1 = min(n, r0 + R);
-    __syncthreads();
-    {
-        uint32_t cnt = 0;
-        int32_t last = -1;
-        for (uint32_t q = (r0 >> 5) + lane; q < ((r1 + 31) >> 5); q += 32) {
-            const uint32_t bits = s_T[q];
-            cnt += __popc(bits);
-            if (bits) last = max(last, (int32_t)(q * 32 + 31 - __clz(bits)));
-        }
-        cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-        last = __reduce_max_sync(0xFFFFFFFFu, last);
-        if (lane == 0) {
-            s_cnt[w] = cnt;
-            s_last[w] = last;
-            s_part[w].has = 0;
-            s_head_anchor[w] = kNone;
-            s_part_z[w] = 0;
-            s_head_z[w] = 0;
-        }
-    }
-    __syncthreads();
+    const uint32_t tid = threadIdx.x;
+    const uint32_t top = min(n, w1 + kShortMax);
+    KT* s = (KT*)smem;
+    for (uint32_t q = tid; q < top - w0; q += kSpecThreads) s[q + (q >> 5)] = __ldg(K + w0 + q);
+    const uint32_t* __restrict__ T = tbits + cd.bitword_begin;
+    const uint32_t k0 = w0 / kFB, nT = (top - w0 + kFB - 1) / kFB;
+    for (uint32_t q = tid; q < kWords + 4; q += kSpecThreads) s_T[q] = q < nT ? T[k0 + q] : 0u;
+    // anchors of the chunk before this window
     uint32_t before = 0;
-    int32_t prev = -1;
-    for (uint32_t u = 0; u < w; ++u) {
-        before += s_cnt[u];
-        prev = max(prev, s_last[u]);
+    for (uint32_t q = tid; q < k0; q += kSpecThreads) before += __popc(T[q]);
+    before = __reduce_add_sync(0xFFFFFFFFu, before);
+    if ((tid & 31u) == 0) s_warp[tid >> 5] = before;
+    if (tid == 0) s_nlong = 0;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kSpecThreads / 32; ++w) t += s_warp[w];
+        s_base = t;
     }
-    const uint64_t seg0 = csb[blockIdx.x];
-    const bool empty = r0 >= r1;
-    const bool foreign0 = !empty && !tbit(s_T, r0);
-    const uint32_t a_first = foreign0 ? (uint32_t)prev : r0;
-    const uint64_t ka_first = foreign0 ? ldk(K, a_first) : 0;
-
-    // pass 1: cones and slopes
-    {
-        uint32_t a_c = a_first;
-        uint64_t ka_c = ka_first;
-        bool foreign = foreign0, open = false;
-        Cone cc{0, 0, 0, 0, 0};
-        uint64_t rank_p = seg0 + before;
-        Cone acc{0, 0, 0, 0, 0};  // per-lane part of the open segment from steps without anchors
-        bool acc_used = false;
-        uint64_t Kn = r0 + lane < r1 ? ldk(K, r0 + lane) : 0;
-        for (uint32_t p = r0; p < r1; p += 32) {
-            const uint32_t i = p + lane;
-            const bool in = i < r1;
-            const uint64_t Ki = Kn;  // loaded during the previous step
-            if (i + 32 < r1) Kn = ldk(K, i + 32);
-            if (i + kWalkAhead < r1) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
-            uint32_t word = s_T[p >> 5];
-            if (r1 - p < 32) word &= (1u << (r1 - p)) - 1u;
-            const bool ends = in && (i + 1 >= n || tbit(s_T, i + 1));
-            if (word == 0 && !__any_sync(0xFFFFFFFFu, ends)) {
-                // no segment starts or ends here: each lane folds its own key
-                if (in) {
-                    const uint64_t D = Ki - ka_c;
-                    Cone u;
-                    u.X = (int64_t)D - eps;
-                    u.Y = D + (uint64_t)eps + 1;
-                    u.E = u.F = i - a_c;
-                    u.has = 1;
-                    cone_merge(acc, u);
+    __syncthreads();
+    const Staged<KT> st{s, w0};
+    const uint32_t nw = (w1 - w0 + kFB - 1) / kFB;
+    const uint32_t word = tid < nw ? s_T[tid] : 0u;
+    const uint32_t pre = block_excl_scan<uint32_t>(__popc(word), AddOp(), 0u, s_warp, nullptr);
+    uint64_t j = csb[wd.chunk] + s_base + pre;
+    const uint64_t* __restrict__ magic = g_magic;
+    for (uint32_t rest = word; rest; rest &= rest - 1, ++j) {
+        const uint32_t a = w0 + tid * kFB + (uint32_t)(__ffs(rest) - 1);
+        // next anchor among the kShortMax keys after a (bit t: key a + 1 + t)
+        const uint32_t q = a + 1 - w0, qi = q >> 5, sh = q & 31u;
+        const uint64_t lo64 = ((uint64_t)s_T[qi + 1] << 32) | s_T[qi];
+        uint64_t nxt = sh ? (lo64 >> sh) | ((uint64_t)s_T[qi + 2] << (64u - sh)) : lo64;
+        const uint32_t left = n - a - 1;  // keys after a in the chunk
+        if (left < 64) nxt &= (1ull << left) - 1;
+        uint32_t b;
+        if (nxt) b = a + 1 + (uint32_t)(__ffsll((long long)nxt) - 1);
+        else if (left < kShortMax) b = n;
+        else b = kNone;
+        const uint64_t ka = st(a);
+        icpt[j] = (KT)ka;
+        start[j] = (uint16_t)a;
+        if (b != kNone) {
+            int64_t M = 0;
+            uint32_t zmax = 0;
+            if (b - a >= 2) {
+                Frac c;
+                {
+                    const uint64_t D = st(a + 1) - ka;
+                    c.X = (int64_t)D - eps;
+                    c.E = 1;
+                    c.Y = D + (uint64_t)eps + 1;
+                    c.F = 1;
                 }
-                acc_used = true;
+                for (uint32_t i = a + 2; i < b; ++i) {
+                    const uint64_t D = st(i) - ka;
+                    const uint32_t d = i - a;
+                    const int64_t xl = (int64_t)D - eps;
+                    const uint64_t yh = D + (uint64_t)eps + 1;
+                    if (frac_gt(xl, d, c.X, c.E)) { c.X = xl; c.E = d; }
+                    if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { c.Y = yh; c.F = d; }
+                }
+                M = frac_slope(c, magic);
+                for (uint32_t i = a + 1; i < b; ++i)
+                    zmax = max(zmax, zigzag32((int64_t)(st(i) - ka) - line_at(M, i - a)));
+            }
+            slope[j] = M;
+            width[j] = (uint8_t)(32u - __clz(zmax));
+        } else {
+            const LongInfo li = longinfo[cd.bitword_begin + (a >> 5)];
+            slope[j] = 0;
+            width[j] = 0;
+            if (li.end <= a + kShortMax || li.end > n) {  // no walk recorded it: cannot happen
+                atomicOr(status, kStInternal);
                 continue;
             }
-            if (acc_used) {
-                cone_merge(cc, warp_reduce_cone(acc));
-                acc.has = 0;
-                acc_used = false;
-            }
-            const bool isa = (word >> lane) & 1u;
-            const uint32_t le = word & (0xFFFFFFFFu >> (31u - lane));
-            const int hl = le ? 31 - __clz(le) : -1;
-            const uint64_t kh = __shfl_sync(0xFFFFFFFFu, Ki, hl >= 0 ? hl : (int)lane);
-            const uint64_t ka = hl >= 0 ? kh : ka_c;
-            const uint32_t a = hl >= 0 ? p + (uint32_t)hl : a_c;
-            Cone v{0, 0, 0, 0, 0};
-            if (in && !isa) {
-                const uint64_t D = Ki - ka;
-                v.X = (int64_t)D - eps;
-                v.Y = D + (uint64_t)eps + 1;
-                v.E = v.F = i - a;
-                v.has = 1;
-            }
-            const uint32_t seg_lo = hl >= 0 ? (uint32_t)hl : 0u;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const Cone u = shfl_up_cone(v, off);
-                if (lane >= (uint32_t)off && lane - off >= seg_lo) cone_merge(v, u);
-            }
-            if (hl < 0) cone_merge(v, cc);
-            if (ends) {
-                if (hl < 0 && foreign) {
-                    s_part[w] = v;
-                } else {
-                    const uint64_t j = hl >= 0 ? rank_p + __popc(le) - 1 : rank_p - 1;
-                    slope[j] = cone_slope(v, magic);
-                    start[j] = (uint16_t)a;
-                    icpt[j] = (KT)ka;
-                }
-            }
-            const int ll = (int)min(31u, r1 - p - 1);
-            const bool end_ll = __shfl_sync(0xFFFFFFFFu, ends, ll);
-            const int hll = __shfl_sync(0xFFFFFFFFu, hl, ll);
-            const Cone vl = shfl_cone(v, ll);
-            const uint64_t kal = __shfl_sync(0xFFFFFFFFu, ka, ll);
-            if (hll >= 0) {
-                foreign = false;
-                a_c = p + (uint32_t)hll;
-                ka_c = kal;
-            } else if (end_ll) {
-                foreign = false;
-            }
-            if (end_ll) cc.has = 0;
-            else cc = vl;
-            rank_p += __popc(word);
-            open = !end_ll;
-        }
-        if (acc_used) {
-            cone_merge(cc, warp_reduce_cone(acc));
-            open = true;
-        }
-        if (lane == 0 && open) {
-            if (foreign) {
-                s_part[w] = cc;
-            } else {
-                s_head[w] = cc;
-                s_head_anchor[w] = a_c;
-                s_head_rank[w] = rank_p - 1;
-                s_head_ka[w] = ka_c;
-            }
+            const uint32_t q = atomicAdd(&s_nlong, 1u);  // at most one per 65 keys: fits
+            if (q < kLongPerWin) s_long[q] = WinLong{j, li.M, a, li.end - a};
         }
     }
+    // the window's long segments: one reservation of items and pieces for the CTA
     __syncthreads();
-    const uint32_t nruns = (n + R - 1) / R;
-    if (tid < NW && s_head_anchor[tid] != kNone) {
-        Cone h = s_head[tid];
-        uint32_t u = tid + 1;
-        for (; u < nruns; ++u) {
-            cone_merge(h, s_part[u]);
-            if (s_cnt[u] > 0) break;
+    const uint32_t nl = min(s_nlong, kLongPerWin);
+    if (tid == 0) {
+        uint32_t np = 0;
+        for (uint32_t q = 0; q < nl; ++q) {
+            s_long[q].poff = np;
+            np += (s_long[q].len - 1 + kPiece - 1) / kPiece;
         }
-        const int64_t M = cone_slope(h, magic);
-        const uint64_t j = s_head_rank[tid];
-        slope[j] = M;
-        start[j] = (uint16_t)s_head_anchor[tid];
-        icpt[j] = (KT)s_head_ka[tid];
-        s_head_M[tid] = M;
+        uint32_t i0 = 0, p0 = 0;
+        if (nl) {
+            i0 = atomicAdd(nitems, nl);
+            p0 = atomicAdd(npieces, np);
+        }
+        const bool fits = s_nlong <= kLongPerWin && i0 + nl <= items_cap && p0 + np <= pieces_cap;
+        if (!fits) atomicOr(status, kStInternal);  // beyond the proven bounds: cannot happen
+        s_item0 = i0;
+        s_piece0 = p0;
+        s_nlong = fits ? nl : 0u;
     }
     __syncthreads();
+    for (uint32_t q = tid; q < s_nlong; q += kSpecThreads) {
+        const WinLong e = s_long[q];
+        const uint32_t it = s_item0 + q;
+        items[it] = LongItem{cd.key_begin + e.a, e.M, e.len, 0u, 0ull};
+        const uint32_t np = (e.len - 1 + kPiece - 1) / kPiece;
+        for (uint32_t p = 0; p < np; ++p)
+            pieces[s_piece0 + e.poff + p] = Piece{it, 1 + p * kPiece, min(e.len, 1 + (p + 1) * kPiece), 0u};
+        slope[e.j] = e.M;
+        width[e.j] = 0xFF;  // finished by bitoff_kernel
+        bitoff[e.j] = it;
+    }
+}
 
-    // pass 2: widths
-    {
-        uint32_t a_c = a_first;
-        uint64_t ka_c = ka_first;
-        int64_t M_c = foreign0 ? s_head_M[a_first / R] : 0;
-        bool foreign = foreign0, open = false;
-        uint32_t z_c = 0;
-        const uint32_t my_head = s_head_anchor[w];
-        uint64_t rank_p = seg0 + before;
-        uint32_t zacc = 0;
-        bool acc_used = false;
-        uint64_t Kn = r0 + lane < r1 ? ldk(K, r0 + lane) : 0;
-        for (uint32_t p = r0; p < r1; p += 32) {
-            const uint32_t i = p + lane;
-            const bool in = i < r1;
-            const uint64_t Ki = Kn;  // loaded during the previous step
-            if (i + 32 < r1) Kn = ldk(K, i + 32);
-            if (i + kWalkAhead < r1) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
-            uint32_t word = s_T[p >> 5];
-            if (r1 - p < 32) word &= (1u << (r1 - p)) - 1u;
-            const bool ends = in && (i + 1 >= n || tbit(s_T, i + 1));
-            if (word == 0 && !__any_sync(0xFFFFFFFFu, ends)) {
-                if (in) zacc = max(zacc, zigzag32((int64_t)(Ki - ka_c) - line_at(M_c, i - a_c)));
-                acc_used = true;
-                continue;
-            }
-            if (acc_used) {
-                z_c = max(z_c, __reduce_max_sync(0xFFFFFFFFu, zacc));
-                zacc = 0;
-                acc_used = false;
-            }
-            const bool isa = (word >> lane) & 1u;
-            const uint32_t le = word & (0xFFFFFFFFu >> (31u - lane));
-            const int hl = le ? 31 - __clz(le) : -1;
-            const uint64_t kh = __shfl_sync(0xFFFFFFFFu, Ki, hl >= 0 ? hl : (int)lane);
-            const uint64_t ka = hl >= 0 ? kh : ka_c;
-            const uint32_t a = hl >= 0 ? p + (uint32_t)hl : a_c;
-            const uint64_t j = hl >= 0 ? rank_p + __popc(le) - 1 : rank_p - 1;
-            int64_t M = M_c;
-            if (hl >= 0) M = a == my_head ? s_head_M[w] : slope[j];
-            uint32_t z = (in && !isa) ? zigzag32((int64_t)(Ki - ka) - line_at(M, i - a)) : 0u;
-            const uint32_t seg_lo = hl >= 0 ? (uint32_t)hl : 0u;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, z, off);
-                if (lane >= (uint32_t)off && lane - off >= seg_lo) z = max(z, u);
-            }
-            if (hl < 0) z = max(z, z_c);
-            if (ends) {
-                if (hl < 0 && foreign) s_part_z[w] = z;
-                else width[j] = (uint8_t)(32u - __clz(z));
-            }
-            const int ll = (int)min(31u, r1 - p - 1);
-            const bool end_ll = __shfl_sync(0xFFFFFFFFu, ends, ll);
-            const int hll = __shfl_sync(0xFFFFFFFFu, hl, ll);
-            const uint32_t zl = __shfl_sync(0xFFFFFFFFu, z, ll);
-            const int64_t Ml = __shfl_sync(0xFFFFFFFFu, M, ll);
-            const uint64_t kal = __shfl_sync(0xFFFFFFFFu, ka, ll);
-            if (hll >= 0) {
-                foreign = false;
-                a_c = p + (uint32_t)hll;
-                ka_c = kal;
-                M_c = Ml;
-            } else if (end_ll) {
-                foreign = false;
-            }
-            z_c = end_ll ? 0u : zl;
-            rank_p += __popc(word);
-            open = !end_ll;
+// The widths pass of the long segments: one warp per piece of kPiece keys,
+// the piece's largest zigzag residual folded into its segment's zmax.
+// Pieces are zeroed before fit_short_kernel runs, so a slot that a failed
+// (and flagged) reservation left unwritten reads as an empty piece.
+template <typename KT>
+__global__ void __launch_bounds__(256)
+long_width_kernel(const KT* __restrict__ keys, LongItem* __restrict__ items, const Piece* __restrict__ pieces,
+                  const uint32_t* __restrict__ npieces, uint32_t pieces_cap) {
+    const uint32_t np = min(*npieces, pieces_cap);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < np; p += nwarps) {
+        const Piece pc = pieces[p];
+        if (pc.t0 >= pc.t1) continue;
+        const LongItem it = items[pc.item];
+        const KT* __restrict__ K = keys + it.key0;
+        const uint64_t ka = ldk(K, 0);
+        uint32_t z = 0;
+        uint32_t t = pc.t0 + lane;
+        for (; t + 96 < pc.t1; t += 128) {
+            const uint64_t k0 = ldk(K, t), k1 = ldk(K, t + 32), k2 = ldk(K, t + 64), k3 = ldk(K, t + 96);
+            z = max(z, zigzag32((int64_t)(k0 - ka) - line_at(it.M, t)));
+            z = max(z, zigzag32((int64_t)(k1 - ka) - line_at(it.M, t + 32)));
+            z = max(z, zigzag32((int64_t)(k2 - ka) - line_at(it.M, t + 64)));
+            z = max(z, zigzag32((int64_t)(k3 - ka) - line_at(it.M, t + 96)));
         }
-        if (acc_used) {
-            z_c = max(z_c, __reduce_max_sync(0xFFFFFFFFu, zacc));
-            open = true;
-        }
-        if (lane == 0 && open) {
-            if (foreign) s_part_z[w] = z_c;
-            else s_head_z[w] = z_c;
-        }
+        for (; t < pc.t1; t += 32) z = max(z, zigzag32((int64_t)(ldk(K, t) - ka) - line_at(it.M, t)));
+        z = __reduce_max_sync(0xFFFFFFFFu, z);
+        if (lane == 0 && z) atomicMax(&items[pc.item].zmax, z);
     }
-    __syncthreads();
-    if (tid < NW && s_head_anchor[tid] != kNone) {
-        uint32_t z = s_head_z[tid];
-        for (uint32_t u = tid + 1; u < nruns; ++u) {
-            z = max(z, s_part_z[u]);
-            if (s_cnt[u] > 0) break;
-        }
-        width[s_head_rank[tid]] = (uint8_t)(32u - __clz(z));
-    }
-    __syncthreads();
+}
 
-    // pass 3: bit offsets of the chunk's segments, in order
-    const uint64_t s1 = csb[blockIdx.x + 1];
+// One CTA per chunk: the long segments' widths, then the bit offsets of the
+// chunk's segments in order (a scan of w (n - 1)), and the chunk's bit count.
+__global__ void __launch_bounds__(256)
+bitoff_kernel(const ChunkDesc* __restrict__ chunks, const uint64_t* __restrict__ csb,
+              const LongItem* __restrict__ items, uint32_t* __restrict__ bitoff, const uint16_t* __restrict__ start,
+              uint8_t* __restrict__ width, uint32_t* __restrict__ chunk_bits) {
+    __shared__ uint32_t s_scan[32];
+    const uint32_t n = chunks[blockIdx.x].n;
+    const uint64_t s0 = csb[blockIdx.x], s1 = csb[blockIdx.x + 1];
     uint32_t carry = 0;
-    for (uint64_t b0 = seg0; b0 < s1; b0 += kModelThreads) {
-        const uint64_t j = b0 + tid;
+    for (uint64_t b0 = s0; b0 < s1; b0 += blockDim.x) {
+        const uint64_t j = b0 + threadIdx.x;
         uint32_t bits = 0;
         if (j < s1) {
+            uint32_t w = width[j];
+            if (w == 0xFF) {
+                w = 32u - __clz(items[bitoff[j]].zmax);
+                width[j] = (uint8_t)w;
+            }
             const uint32_t st = start[j];
             const uint32_t en = j + 1 < s1 ? (uint32_t)start[j + 1] : n;
-            bits = (uint32_t)width[j] * (en - st - 1);
+            bits = w * (en - st - 1);
         }
         uint32_t tot;
         const uint32_t ex = block_excl_scan<uint32_t>(bits, AddOp(), 0u, s_scan, &tot);
         if (j < s1) bitoff[j] = carry + ex;
         carry += tot;
     }
-    if (tid == 0) chunk_bits[blockIdx.x] = carry;
+    if (threadIdx.x == 0) chunk_bits[blockIdx.x] = carry;
 }
 
 // ------------------------------------------------------------------ pack
@@ -923,12 +834,26 @@ static int ensure_magic(int dev) {
     return LC_OK;
 }
 
+static int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
 struct FitScratch {
     const WinDesc* wins;
     uint64_t nwins;
     uint32_t *spec, *fix, *exitS, *exitF;
     uint8_t* sync;
+    LongInfo* longinfo;
+    LongItem* items;
+    Piece* pieces;
+    uint32_t* counters;  // [0] long items, [1] pieces
+    uint32_t items_cap, pieces_cap;
 };
+
+constexpr uint32_t kShortSlots = (kWinKeys + kShortMax) + (kWinKeys + kShortMax) / 32 + 1;
 
 template <typename KT>
 static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, const FitScratch& fs, uint32_t* tbits,
@@ -953,7 +878,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         {
             KTime kt("fit_chain", st);
             chain_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0, st>>>(
-                keys, chunks_d, C, fs.spec, fs.fix, fs.exitS, fs.exitF, fs.sync, tbits, counts);
+                keys, chunks_d, C, fs.spec, fs.fix, fs.exitS, fs.exitF, fs.sync, tbits, counts, fs.longinfo);
         }
         note_launch(2);
         int rc = cuda_status(cudaGetLastError());
@@ -961,12 +886,33 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         return scan_exclusive(counts, csb, C, ScanOp::Identity, tmp, tmp_bytes, st);
     }
     {
-        KTime kt("model", st);
-        model_kernel<KT><<<(unsigned)C, kModelThreads, 0, st>>>(
-            keys, chunks_d, tbits, (const uint64_t*)(blob + lay.csb), (KT*)(blob + lay.icpt), (int64_t*)(blob + lay.slope),
-            (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start), (uint8_t*)(blob + lay.width), counts);
+        static bool attr[2] = {false, false};
+        const size_t smem = sizeof(KT) * kShortSlots;
+        if (!attr[sizeof(KT) == 8]) {
+            int rc = cuda_status(
+                cudaFuncSetAttribute(fit_short_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (rc) return rc;
+            attr[sizeof(KT) == 8] = true;
+        }
+        KTime kt("model_short", st);
+        fit_short_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(
+            keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
+            (int64_t*)(blob + lay.slope), (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start),
+            (uint8_t*)(blob + lay.width), fs.items, fs.counters, fs.items_cap, fs.pieces, fs.counters + 1,
+            fs.pieces_cap, status);
     }
-    note_launch();
+    {
+        KTime kt("model_long", st);
+        long_width_kernel<KT><<<(unsigned)(device_sms() * 8), 256, 0, st>>>(keys, fs.items, fs.pieces, fs.counters + 1,
+                                                                          fs.pieces_cap);
+    }
+    {
+        KTime kt("bitoff", st);
+        bitoff_kernel<<<(unsigned)C, 256, 0, st>>>(chunks_d, (const uint64_t*)(blob + lay.csb), fs.items,
+                                                   (uint32_t*)(blob + lay.bitoff), (const uint16_t*)(blob + lay.start),
+                                                   (uint8_t*)(blob + lay.width), counts);
+    }
+    note_launch(3);
     int rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
     rc = scan_exclusive(counts, (uint64_t*)(blob + lay.cwb), C, ScanOp::BitsToEvenWords, tmp, tmp_bytes, st);
@@ -1004,7 +950,16 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     const size_t off_tmp = al(off_counts + (C + 1) * 4);
     const size_t off_status = al(off_tmp + tmp_bytes);
     const size_t off_csb = al(off_status + 256);
-    const size_t scratch_bytes = off_csb + (C + 1) * sizeof(uint64_t);
+    // long segments (> kShortMax keys): at most one per 32-key block, N / (kShortMax + 1) in all
+    uint64_t nkeys = 0;
+    for (uint64_t c = 0; c < C; ++c) nkeys += chunks_h[c].n;
+    const uint64_t items_cap = std::min<uint64_t>(nkeys / (kShortMax + 1) + 1, 0xFFFFFFFFull);
+    const uint64_t pieces_cap = std::min<uint64_t>(items_cap + nkeys / kPiece + 1, 0xFFFFFFFFull);
+    const size_t off_long = al(off_csb + (C + 1) * sizeof(uint64_t));
+    const size_t off_items = al(off_long + bitwords * sizeof(LongInfo));
+    const size_t off_pieces = al(off_items + items_cap * sizeof(LongItem));
+    const size_t off_counters = al(off_pieces + pieces_cap * sizeof(Piece));
+    const size_t scratch_bytes = off_counters + 256;
     uint8_t* scratch = nullptr;
     if (cudaMallocAsync((void**)&scratch, scratch_bytes, st) != cudaSuccess) return LC_ERR_NOMEM;
     ChunkDesc* chunks_d = (ChunkDesc*)(scratch + off_chunks);
@@ -1021,6 +976,12 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     void* tmp = scratch + off_tmp;
     uint32_t* status = (uint32_t*)(scratch + off_status);
     uint64_t* csb_tmp = (uint64_t*)(scratch + off_csb);
+    fs.longinfo = (LongInfo*)(scratch + off_long);
+    fs.items = (LongItem*)(scratch + off_items);
+    fs.pieces = (Piece*)(scratch + off_pieces);
+    fs.counters = (uint32_t*)(scratch + off_counters);
+    fs.items_cap = (uint32_t)items_cap;
+    fs.pieces_cap = (uint32_t)pieces_cap;
     uint64_t total = 0;
     uint32_t h_status = 0;
     auto fail = [&](int code) {
@@ -1035,8 +996,15 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     if (rc) return fail(rc);
     rc = cuda_status(cudaMemsetAsync(status, 0, 4, st));
     if (rc) return fail(rc);
+    rc = cuda_status(cudaMemsetAsync(fs.longinfo, 0, bitwords * sizeof(LongInfo), st));
+    if (rc) return fail(rc);
+    rc = cuda_status(cudaMemsetAsync(fs.counters, 0, 8, st));
+    if (rc) return fail(rc);
+    rc = cuda_status(cudaMemsetAsync(fs.pieces, 0, pieces_cap * sizeof(Piece), st));
+    if (rc) return fail(rc);
 
     // stage 0: anchors and segment counts
+    HTime ht0("fit_stage0");
     if (kb == 4)
         rc = run_pipeline<uint32_t>((const uint32_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 0);
@@ -1052,6 +1020,7 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     if (rc) return fail(rc);
     if (h_status & kStUnsorted) return fail(LC_ERR_UNSORTED);
     const uint64_t L = total;
+    HTime ht1("fit_stage1");
 
     // the blob, with the payload sized by the paper's bound of
     // ceil(log2(2 eps + 1)) bits per residual (plus per-chunk padding)
@@ -1076,9 +1045,11 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     if (rc) return fail(rc);
     rc = cuda_status(cudaMemcpyAsync(&total, col->blob + lay.cwb + 8 * C, 8, cudaMemcpyDeviceToHost, st));
     if (rc) return fail(rc);
+    rc = cuda_status(cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st));
+    if (rc) return fail(rc);
     rc = cuda_status(cudaStreamSynchronize(st));
     if (rc) return fail(rc);
-    if (total > payload_bound_words) return fail(LC_ERR_INTERNAL);
+    if (total > payload_bound_words || (h_status & kStInternal)) return fail(LC_ERR_INTERNAL);
     col->W = total;
     col->lay = make_layout(kb, C, L, col->W, col->NL, col->list_mode != 0);
     cudaFreeAsync(scratch, st);

@@ -21,6 +21,7 @@ enum : uint32_t {
     kStUnsorted = 1u,
     kStOutOfRange = 2u,
     kStInternal = 4u,
+    kStTimeout = 8u,
 };
 
 // One chunk of the fit: keys [key_begin, key_begin + n) of the input, error
@@ -52,14 +53,20 @@ struct SrvReq {
 };
 
 // A decode tile: keys [key_begin, key_begin + n) of chunk `chunk`; its first
-// and last keys lie in segments seg_lo and seg_hi (global segment indices).
+// and last keys lie in segments seg_lo and seg_hi (global segment indices);
+// their residuals lie in the 32-bit payload words [pw0, pw0 + pwn) (pw0 and
+// pwn multiples of 4, so that the window is a 16-byte aligned run).
 struct TileDesc {
     uint64_t key_begin;
     uint64_t seg_lo;
     uint64_t seg_hi;
+    uint64_t pw0;
     uint32_t chunk;
     uint32_t n;
+    uint32_t pwn;
+    uint32_t pad;
 };
+static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
 
 // Derived (not serialized) directories of a column, built on the device when a
 // column is created.  They put everything one random query needs into few
@@ -81,11 +88,12 @@ struct RankWord {
     uint64_t bits;
     uint64_t before;
 };
-// The sampled intercept levels used by lower_bound: level d >= 1 holds
-// icpt[16^d k]; level 0 is seg_icpt itself.  The top level has at most
-// kTopMax entries and is staged in shared memory.
-constexpr int kMaxLevels = 12;
-constexpr uint32_t kTopMax = 4096;
+// The radix table used by lower_bound: the value range [kmin, kmax] of the
+// intercepts is cut into B = 2^b equal buckets of 2^rdx_shift values, and
+// rdx[q] = the number of segments whose intercept is < kmin + q 2^rdx_shift
+// (q = 0..B).  A value x in bucket q has its last segment with intercept < x
+// among rdx[q] - 1 .. rdx[q+1] - 1.
+constexpr uint32_t kRdxMaxLog = 22;
 
 // Byte offsets of every array inside an LCF1 blob.
 struct Layout {
@@ -112,9 +120,9 @@ struct ColView {
     const uint64_t* chunk_tile_begin;  // [C+1]
     const SegRec* recs;                // [L]
     const RankWord* rank;              // [ceil(N / 64)]
-    const uint64_t* level[kMaxLevels]; // sampled intercepts, level[0] unused (seg_icpt)
-    uint64_t level_n[kMaxLevels];
-    uint32_t top;                      // index of the top level (staged in shared memory)
+    const uint64_t* rdx;               // radix table over the intercepts [B + 1]
+    uint64_t kmin, kmax;               // first and last key
+    uint32_t rdx_shift;                // bucket width 2^rdx_shift
     uint32_t max_tile_segs;            // most segments meeting one decode tile
     uint32_t key_bytes;
     uint32_t* status;
@@ -136,7 +144,7 @@ struct lc_column {
     lcx::TileDesc* tiles;     // device, derived
     uint64_t ntiles;
     uint64_t* chunk_tile_begin;  // device [C+1], derived
-    uint8_t* derived2;           // device: SegRec, RankWord and intercept levels
+    uint8_t* derived2;           // device: SegRec, RankWord and the radix table
     uint32_t* status;            // device status word
     uint64_t* h_ckb;             // host copy of chunk_key_begin [C+1]
     uint64_t* h_ctb;             // host copy of chunk_tile_begin [C+1]
@@ -192,6 +200,15 @@ struct KTime {
     const char* name;
     cudaStream_t st;
     cudaEvent_t a, b;
+};
+
+// Host wall time of a phase of a call (reported by lc_timing_read under
+// "host:<name>", synchronisations included), recorded while tracing is on.
+struct HTime {
+    explicit HTime(const char* name);
+    ~HTime();
+    const char* name;
+    double t0;
 };
 
 }  // namespace lcx

@@ -99,6 +99,15 @@ __device__ __forceinline__ bool frac_step(uint64_t D, uint32_t d, int64_t eps, F
     return true;
 }
 
+// The slope of a closed segment from its cone: the floor midpoint of
+// [LO, HI] with LO = ceil(2^32 X/E) and HI = ceil(2^32 Y/F) - 1, capped at
+// INT64_MAX (the fraction 2^31/1 or above).
+__device__ __forceinline__ int64_t frac_slope(const Frac& c, const uint64_t* __restrict__ magic) {
+    const int64_t LO = ceil_q32(c.X, c.E, magic);
+    const int64_t HI = c.Y >= ((uint64_t)c.F << 31) ? INT64_MAX : ceil_q32((int64_t)c.Y, c.F, magic) - 1;
+    return LO + (int64_t)(((uint64_t)HI - (uint64_t)LO) >> 1);
+}
+
 __device__ __forceinline__ uint32_t zigzag32(int64_t r) {
     return (uint32_t)(((uint64_t)r << 1) ^ (uint64_t)(r >> 63));
 }

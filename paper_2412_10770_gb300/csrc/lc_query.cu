@@ -20,10 +20,19 @@ namespace {
 
 constexpr int kDecThreads = 256;
 constexpr uint32_t kMaxSegsPerTile = kTile + 1;
-constexpr size_t kDecSmem = (size_t)kMaxSegsPerTile * 24 + 64 * 4 * 2 + (kTile + 4) * 4;
+constexpr uint32_t kRankPerTile = kTile / 64 + 1;  // rank words a tile's keys can touch
+constexpr uint32_t kPayWords = kTile + 16;          // payload words a tile can need (32-bit)
 
-// Shared memory of one decode CTA when no tile meets more than ms segments.
-__host__ __device__ constexpr size_t dec_smem(uint32_t ms) { return (size_t)ms * 24 + 64 * 4 * 2 + (kTile + 4) * 4; }
+// One stage of the decode pipeline in shared memory: the tile's rank words,
+// the records of its segments (at most ms) and its payload window.
+__host__ __device__ constexpr size_t dec_stage(uint32_t ms) {
+    return (size_t)kRankPerTile * 16 + (size_t)ms * 32 + (size_t)kPayWords * 4;
+}
+// Shared memory of one decode CTA (two stages) when no tile meets more than
+// ms segments.
+__host__ __device__ constexpr size_t dec_smem(uint32_t ms) { return 2 * dec_stage(ms); }
+constexpr size_t kDecSmem = dec_smem(kMaxSegsPerTile);
+constexpr uint32_t kSpinLimit = 1u << 22;  // mbarrier polls before a decode gives up (seconds)
 
 template <typename KT>
 __device__ __forceinline__ uint64_t ld_icpt(const void* icpt, uint64_t j) {
@@ -47,106 +56,209 @@ __device__ __forceinline__ uint64_t chunk_of(const ColView& v, uint64_t i) {
     return lo;
 }
 
-// Decode keys [lo_key, hi_key) of tile t into out[g - lo_key].
-template <typename KT>
-__device__ void decode_tile(const ColView& v, uint64_t t, uint64_t lo_key, uint64_t hi_key, KT* __restrict__ out,
-                            uint8_t* smem, uint32_t smem_segs = 0) {
-    const uint32_t ms = smem_segs ? smem_segs : v.max_tile_segs;
-    uint64_t* s_icpt = (uint64_t*)smem;
-    int64_t* s_slope = (int64_t*)(s_icpt + ms);
-    uint64_t* s_meta = (uint64_t*)(s_slope + ms);
-    uint32_t* s_bm = (uint32_t*)(s_meta + ms);
-    uint32_t* s_pref = s_bm + 64;
-    uint32_t* s_pay = s_pref + 64;
-    __shared__ uint32_t s_win[2];
+// ------------------------------------------------------------------ decode pipeline
+//
+// A persistent CTA decodes a list of work items (a tile of 2048 keys, the
+// wanted key range, the output).  Each tile's inputs are three contiguous runs
+// of device memory, so thread 0 fetches them with bulk copies (TMA,
+// cp.async.bulk) into one of two shared-memory stages, completing on that
+// stage's mbarrier, while the CTA decodes the previous tile from the other
+// stage: the rank words of the tile's keys, the 32-byte records of the
+// segments that meet it, and the payload words its residuals occupy (the
+// window precomputed in the tile directory, 16-byte aligned).  Every key then
+// needs only shared memory: its segment from the rank word (anchors before +
+// popcount), its model from the record, its residual from the payload window
+// (Fig. 2 decoding stage, K[i] = floor(f_j(i)) + Delta[i]); 32 consecutive
+// keys per warp, stored coalesced.
 
-    const uint32_t tid = threadIdx.x;
-    const TileDesc td = v.tiles[t];
-    const uint64_t c = td.chunk;
-    const uint64_t ckb = __ldg(v.ckb + c);
-    const uint32_t local0 = (uint32_t)(td.key_begin - ckb);
-    const uint32_t n = td.n;
-    const uint64_t j0 = td.seg_lo;
-    const uint32_t ns = (uint32_t)(td.seg_hi - j0 + 1);
+struct DecItem {
+    uint64_t kbeg;     // first key of the tile (global index)
+    uint64_t lo, hi;   // wanted keys [lo, hi) (global), clipped to the tile below
+    uint64_t j0;       // first segment of the tile
+    uint64_t r0;       // first rank word of the tile
+    uint64_t pbit0;    // global bit of the payload window's first word
+    void* out;         // output of key g: out[g - lo_key]
+    uint64_t lo_key;
+    uint32_t n;        // keys in the tile
+    uint32_t ns;       // segments meeting the tile
+    uint32_t ok;       // 0: nothing to decode (error or empty)
+    uint32_t pad;
+};
 
-    if (tid < 64) s_bm[tid] = 0;
-    __syncthreads();
-    for (uint32_t j = tid; j < ns; j += kDecThreads) {
-        const uint64_t g = j0 + j;
-        const uint32_t st = __ldg(v.start + g);
-        const uint32_t w = __ldg(v.width + g);
-        const uint32_t bo = __ldg(v.bitoff + g);
-        s_icpt[j] = ld_icpt<KT>(v.icpt, g);
-        s_slope[j] = __ldg(v.slope + g);
-        // chunk-relative bit of the residual of key i (> st): bo + w (i - st - 1)
-        const uint32_t base = bo - w * (st + 1);
-        s_meta[j] = (uint64_t)base | ((uint64_t)st << 32) | ((uint64_t)w << 48);
-        const uint32_t p = j ? st - local0 : 0;
-        atomicOr(&s_bm[p >> 5], 1u << (p & 31u));
-    }
-    __syncthreads();
-    if (tid < 32) {
-        // exclusive popcount prefix over the 64 bitmap words, two per lane
-        const uint32_t a = __popc(s_bm[2 * tid]), b = __popc(s_bm[2 * tid + 1]);
-        uint32_t inc = a + b;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, off);
-            if (tid >= (uint32_t)off) inc += o;
-        }
-        const uint32_t ex = inc - a - b;
-        s_pref[2 * tid] = ex;
-        s_pref[2 * tid + 1] = ex + a;
-        if (tid == 0) {
-            // payload window: from the tile's first residual to the end of its last
-            const uint64_t m0 = s_meta[0], m1 = s_meta[ns - 1];
-            const uint32_t st0 = (uint32_t)(m0 >> 32) & 0xFFFFu, w0 = (uint32_t)(m0 >> 48);
-            const uint32_t st1 = (uint32_t)(m1 >> 32) & 0xFFFFu, w1 = (uint32_t)(m1 >> 48);
-            const uint32_t lo_bit = (uint32_t)m0 + w0 * max(local0, st0 + 1);
-            const uint32_t hi_bit = (uint32_t)m1 + w1 * (max(local0 + n - 1, st1) + 1);
-            s_win[0] = lo_bit >> 5;
-            s_win[1] = ((hi_bit + 31) >> 5) - (lo_bit >> 5) + 1;
-        }
-    }
-    __syncthreads();
-    const uint32_t wlo = s_win[0], cnt = s_win[1];
-    const uint64_t pbase = 2 * __ldg(v.cwb + c) + wlo;
-    const uint64_t plimit = 2 * v.W;
-    for (uint32_t q = tid; q < cnt + 1; q += kDecThreads) {
-        const uint64_t gi = pbase + q;
-        s_pay[q] = gi < plimit ? __ldg(v.pay32 + gi) : 0u;
-    }
-    __syncthreads();
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-    const uint64_t kbeg = td.key_begin;
-    uint32_t p0 = 0, p1 = n;
-    if (lo_key > kbeg) p0 = (uint32_t)(lo_key - kbeg < (uint64_t)n ? lo_key - kbeg : (uint64_t)n);
-    if (hi_key < kbeg + n) p1 = (uint32_t)(hi_key > kbeg ? hi_key - kbeg : 0);
-    const uint32_t wbit = 32u * wlo;
-    for (uint32_t p = p0 + tid; p < p1; p += kDecThreads) {
-        const uint32_t wd = p >> 5;
-        const uint32_t j = s_pref[wd] + __popc(s_bm[wd] & (0xFFFFFFFFu >> (31u - (p & 31u)))) - 1;
-        const uint64_t meta = s_meta[j];
-        const uint32_t st = (uint32_t)(meta >> 32) & 0xFFFFu, w = (uint32_t)(meta >> 48);
-        const uint32_t i = local0 + p;
-        uint64_t key = s_icpt[j];
-        const uint32_t tt = i - st;
-        if (tt) {
-            const uint32_t lb = (uint32_t)meta + w * i - wbit;
-            const uint32_t z = extract_bits(s_pay[lb >> 5], s_pay[(lb >> 5) + 1], lb & 31u, w);
-            key += (uint64_t)(line_at(s_slope[j], tt) + (int64_t)unzigzag32(z));
-        }
-        out[kbeg + p - lo_key] = (KT)key;
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
     }
-    __syncthreads();
+    return false;
+}
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
-// Persistent: each CTA decodes tiles t0 + blockIdx.x, t0 + blockIdx.x + gridDim.x, ...
+struct DecStage {
+    RankWord* rank;
+    SegRec* rec;
+    uint32_t* pay;
+};
+
+__device__ __forceinline__ DecStage dec_stage_at(uint8_t* smem, uint32_t ms, uint32_t s) {
+    uint8_t* b = smem + s * dec_stage(ms);
+    DecStage d;
+    d.rank = (RankWord*)b;
+    d.rec = (SegRec*)(b + kRankPerTile * 16);
+    d.pay = (uint32_t*)(b + kRankPerTile * 16 + (size_t)ms * 32);
+    return d;
+}
+
+// Thread 0: fetch tile t of v into stage s; the item is written before the
+// arrive, so that the waiting threads see it.  A tile that does not fit the
+// stage (cannot happen: ms bounds every tile) or holds no wanted key is marked
+// and its barrier completed without copies.
+__device__ void dec_issue(const ColView& v, uint64_t t, uint64_t lo_key, uint64_t hi_key, void* out, uint32_t ms,
+                          const DecStage& sd, uint64_t* bar, DecItem* it) {
+    const TileDesc td = v.tiles[t];
+    DecItem d;
+    d.kbeg = td.key_begin;
+    d.n = td.n;
+    d.lo = max(lo_key, td.key_begin);
+    d.hi = min(hi_key, td.key_begin + td.n);
+    d.j0 = td.seg_lo;
+    d.r0 = td.key_begin >> 6;
+    d.pbit0 = 32ull * td.pw0;
+    d.out = out;
+    d.lo_key = lo_key;
+    const uint32_t ns = (uint32_t)(td.seg_hi - td.seg_lo + 1);
+    const uint32_t nr = (uint32_t)(((td.key_begin + td.n - 1) >> 6) - d.r0 + 1);
+    d.ns = ns;
+    d.pad = 0;
+    d.ok = d.lo < d.hi && ns <= ms && nr <= kRankPerTile && td.pwn <= kPayWords;
+    *it = d;
+    if (!d.ok) {
+        if (ns > ms || nr > kRankPerTile || td.pwn > kPayWords) atomicOr(v.status, kStInternal);
+        mbar_expect(bar, 0);
+        return;
+    }
+    mbar_expect(bar, nr * 16u + ns * 32u + td.pwn * 4u);
+    bulk_load(sd.rank, v.rank + d.r0, nr * 16u, bar);
+    bulk_load(sd.rec, v.recs + d.j0, ns * 32u, bar);
+    if (td.pwn) bulk_load(sd.pay, v.pay32 + td.pw0, td.pwn * 4u, bar);
+}
+
+// All threads: the wanted keys of the item in stage sd.
+template <typename KT>
+__device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd) {
+    KT* __restrict__ out = (KT*)d.out;
+    const uint32_t p0 = (uint32_t)(d.lo - d.kbeg), p1 = (uint32_t)(d.hi - d.kbeg);
+    for (uint32_t p = p0 + threadIdx.x; p < p1; p += kDecThreads) {
+        const uint64_t g = d.kbeg + p;
+        const RankWord rw = sd.rank[(g >> 6) - d.r0];
+        const uint64_t j = rw.before + __popcll(rw.bits & (~0ull >> (63u - (uint32_t)(g & 63u)))) - 1;
+        const SegRec r = sd.rec[min(j - d.j0, (uint64_t)d.ns - 1)];  // the clamp only guards shared memory
+        const uint32_t t = (uint32_t)(g - (r.kstart_w & ((1ull << 56) - 1)));
+        uint64_t key = r.icpt;
+        if (t) {
+            const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+            uint32_t z = 0;
+            if (w) {
+                const uint32_t lb = (uint32_t)(r.bit1 + (uint64_t)w * (t - 1) - d.pbit0);
+                const uint32_t q = min(lb >> 5, kPayWords - 2);
+                z = extract_bits(sd.pay[q], sd.pay[q + 1], lb & 31u, w);
+            }
+            key += (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(z));
+        }
+        out[g - d.lo_key] = (KT)key;
+    }
+}
+
+// The pipeline over work items w = blockIdx.x, blockIdx.x + gridDim.x, ...
+// < total; src(w, &view, &tile, &lo, &hi, &out) describes item w.
+template <typename KT, typename Src>
+__device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint32_t ms) {
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ DecItem s_item[2];
+    const uint64_t w0 = blockIdx.x;
+    if (w0 >= total) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0]);
+        mbar_init(&s_bar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const ColView* vv;
+    uint64_t t, lo, hi;
+    void* o;
+    if (threadIdx.x == 0) {
+        src(w0, &vv, &t, &lo, &hi, &o);
+        dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, 0), &s_bar[0], &s_item[0]);
+    }
+    uint32_t k = 0;
+    for (uint64_t w = w0; w < total; w += gridDim.x, ++k) {
+        const uint32_t s = k & 1u;
+        const uint64_t wn = w + gridDim.x;
+        if (threadIdx.x == 0 && wn < total) {
+            src(wn, &vv, &t, &lo, &hi, &o);
+            dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, s ^ 1u), &s_bar[s ^ 1u], &s_item[s ^ 1u]);
+        }
+        const bool got = mbar_wait(&s_bar[s], (k >> 1) & 1u);
+        if (__syncthreads_or(!got)) {
+            // a copy never completed: record it, wait (bounded) for the other
+            // stage's copies, and stop
+            if (threadIdx.x == 0) {
+                src(w, &vv, &t, &lo, &hi, &o);
+                atomicOr(vv->status, kStTimeout);
+                if (wn < total) mbar_wait(&s_bar[s ^ 1u], ((k + 1) >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const DecItem d = s_item[s];
+        if (d.ok) dec_compute<KT>(d, dec_stage_at(smem, ms, s));
+        __syncthreads();  // stage s is free for item k + 2
+    }
+}
+
+template <typename KT>
+struct WholeSrc {
+    const ColView* v;
+    uint64_t t0, begin, end;
+    KT* out;
+    __device__ void operator()(uint64_t w, const ColView** vv, uint64_t* t, uint64_t* lo, uint64_t* hi,
+                               void** o) const {
+        *vv = v;
+        *t = t0 + w;
+        *lo = begin;
+        *hi = end;
+        *o = out;
+    }
+};
+
+// Persistent: tiles t0 .. t0 + nt - 1, keys [begin, end) into out[g - begin].
 template <typename KT>
 __global__ void __launch_bounds__(kDecThreads) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
                                                              uint64_t end, KT* __restrict__ out) {
     extern __shared__ __align__(16) uint8_t smem[];
-    for (uint64_t t = blockIdx.x; t < nt; t += gridDim.x) decode_tile<KT>(v, t0 + t, begin, end, out, smem);
+    dec_pipeline<KT>(nt, WholeSrc<KT>{&v, t0, begin, end, out}, smem, v.max_tile_segs);
 }
 
 // Work items of a multi-range decode: range r covers tiles
@@ -171,23 +283,35 @@ __global__ void range_tiles_kernel(ColView v, const uint64_t* __restrict__ begin
 }
 
 template <typename KT>
+struct RangesSrc {
+    const ColView* v;
+    const uint64_t *begin, *count, *out_off, *first, *work_off;
+    uint64_t m;
+    KT* out;
+    __device__ void operator()(uint64_t w, const ColView** vv, uint64_t* t, uint64_t* lo, uint64_t* hi,
+                               void** o) const {
+        uint64_t a = 0, b = m - 1;  // last r with work_off[r] <= w
+        while (a < b) {
+            const uint64_t mid = (a + b + 1) >> 1;
+            if (work_off[mid] <= w) a = mid;
+            else b = mid - 1;
+        }
+        *vv = v;
+        *t = first[a] + (w - work_off[a]);
+        *lo = begin[a];
+        *hi = begin[a] + count[a];
+        *o = out + out_off[a];
+    }
+};
+
+template <typename KT>
 __global__ void __launch_bounds__(kDecThreads)
 decode_ranges_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
                      const uint64_t* __restrict__ out_off, uint64_t m, const uint64_t* __restrict__ first,
                      const uint64_t* __restrict__ work_off, KT* __restrict__ out) {
     extern __shared__ __align__(16) uint8_t smem[];
-    const uint64_t total = work_off[m];
-    for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
-        uint64_t lo = 0, hi = m - 1;  // last r with work_off[r] <= w
-        while (lo < hi) {
-            const uint64_t mid = (lo + hi + 1) >> 1;
-            if (work_off[mid] <= w) lo = mid;
-            else hi = mid - 1;
-        }
-        const uint64_t r = lo;
-        const uint64_t b = begin[r];
-        decode_tile<KT>(v, first[r] + (w - work_off[r]), b, b + count[r], out + out_off[r], smem);
-    }
+    dec_pipeline<KT>(work_off[m], RangesSrc<KT>{&v, begin, count, out_off, first, work_off, m, out}, smem,
+                     v.max_tile_segs);
 }
 
 // Key t of the segment whose record is r (Fig. 2: floor(f_j(i)) + Delta[i]).
@@ -216,18 +340,77 @@ __device__ __forceinline__ SegRec load_rec(const SegRec* p) {
 
 constexpr uint64_t kKeyMask = (1ull << 56) - 1;
 
+// L2 eviction priorities for the random lookups: directories that many queries
+// share (rank words, intercept levels, seg_icpt) are marked evict_last, the
+// per-query records and payload words evict_first, so that the streaming part
+// does not push the shared part out of L2.
+__device__ __forceinline__ uint64_t policy_keep() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_stream() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ ulonglong2 ld2_hint(const void* ptr, uint64_t pol) {
+    ulonglong2 r;
+    asm("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;" : "=l"(r.x), "=l"(r.y) : "l"(ptr), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld2x32_hint(const void* ptr, uint64_t pol) {
+    uint2 r;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(ptr), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint64_t ld64_hint(const void* ptr, uint64_t pol) {
+    uint64_t r;
+    asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(ptr), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld32_hint(const void* ptr, uint64_t pol) {
+    uint32_t r;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(ptr), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ SegRec load_rec_hint(const SegRec* p, uint64_t pol) {
+    const ulonglong2 a = ld2_hint(p, pol), b = ld2_hint((const ulonglong2*)p + 1, pol);
+    SegRec r;
+    r.icpt = a.x;
+    r.slope = (int64_t)a.y;
+    r.kstart_w = b.x;
+    r.bit1 = b.y;
+    return r;
+}
+
+// rec_key with the payload words read under an L2 policy.
+__device__ __forceinline__ uint64_t rec_key_hint(const ColView& v, const SegRec& r, uint32_t t, uint64_t pol) {
+    if (t == 0) return r.icpt;
+    const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+    const int64_t line = line_at(r.slope, t);
+    if (w == 0) return r.icpt + (uint64_t)line;
+    const uint64_t pos = r.bit1 + (uint64_t)w * (t - 1);
+    const uint64_t wi = pos >> 5;
+    const uint32_t lo = ld32_hint(v.pay32 + wi, pol);
+    const uint32_t hi = wi + 1 < 2 * v.W ? ld32_hint(v.pay32 + wi + 1, pol) : 0u;
+    return r.icpt + (uint64_t)(line + (int64_t)unzigzag32(extract_bits(lo, hi, (uint32_t)(pos & 31u), w)));
+}
+
 // Rank access: the segment of key i comes from one rank word (anchor bits +
 // anchors before), its model from one 32-byte record, its residual from the
 // payload: three dependent loads.  i < v.N.
-__device__ __forceinline__ uint64_t access_one(const ColView& v, uint64_t i) {
-    const ulonglong2 rw = __ldg((const ulonglong2*)(v.rank + (i >> 6)));
+__device__ __forceinline__ uint64_t access_one(const ColView& v, uint64_t i, uint64_t keep, uint64_t stream) {
+    const ulonglong2 rw = ld2_hint(v.rank + (i >> 6), keep);
     const uint64_t j = rw.y + __popcll(rw.x & (~0ull >> (63u - (uint32_t)(i & 63u)))) - 1;
-    const SegRec r = load_rec(v.recs + j);
-    return rec_key(v, r, (uint32_t)(i - (r.kstart_w & kKeyMask)));
+    const SegRec r = load_rec_hint(v.recs + j, stream);
+    return rec_key_hint(v, r, (uint32_t)(i - (r.kstart_w & kKeyMask)), stream);
 }
 
 template <typename KT>
 __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint64_t m, KT* __restrict__ out) {
+    const uint64_t keep = policy_keep(), stream = policy_stream();
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t i = idx[q];
         if (i >= v.N) {
@@ -235,52 +418,36 @@ __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint6
             out[q] = 0;
             continue;
         }
-        out[q] = (KT)access_one(v, i);
+        out[q] = (KT)access_one(v, i, keep, stream);
     }
 }
 
-// Entry k of the top intercept level: from `top_keys` when staged, else from
-// the level itself.
+// Value lower_bound: the first i with K[i] >= x (N if none).  The last
+// segment whose intercept (its first key) is < x lies in the radix bucket of
+// x, between rdx[q] - 1 and rdx[q+1] - 1: a binary search over that run of
+// seg_icpt (usually one or two entries) finds it.  Then the segment's own line
+// brackets the answer: every key lies within R = 2^(w-1) of floor(f), so keys
+// before t < (dx - R)/s are < x and the key at t >= (dx + R + 1)/s is >= x
+// (s = slope / 2^32, dx = x - intercept).  A binary search inside the bracket
+// finishes.  Dependent loads: one table entry pair, the intercept run, one
+// 32-byte record, the payload words of the bracket.
 template <typename KT>
-__device__ __forceinline__ uint64_t top_at(const ColView& v, const uint64_t* top_keys, uint64_t k) {
-    if (top_keys) return top_keys[k];
-    return v.top ? __ldg(v.level[v.top] + k) : ld_icpt<KT>(v.icpt, k);
-}
-
-// Value lower_bound: the last segment whose intercept (its first key) is < x is
-// found through the 16-ary sampled intercept levels (top level in shared
-// memory, the next ones L2-resident, the last a 128-byte run of seg_icpt); then
-// the segment's own line brackets the answer: every key lies within
-// R = 2^(w-1) of floor(f), so keys before t < (dx - R)/s are < x and the key at
-// t >= (dx + R + 1)/s is >= x (s = slope / 2^32, dx = x - intercept).  A
-// binary search inside the bracket finishes.
-template <typename KT>
-__device__ uint64_t lower_bound_one(const ColView& v, uint64_t x, const uint64_t* top_keys) {
-    const uint32_t top = v.top;
-    const uint64_t ntop = top ? v.level_n[top] : v.L;
-    if (v.L == 0 || top_at<KT>(v, top_keys, 0) >= x) return 0;
-    uint64_t lo = 0, hi = ntop - 1;  // last entry < x
-    while (lo < hi) {
-        const uint64_t mid = (lo + hi + 1) >> 1;
-        if (top_at<KT>(v, top_keys, mid) < x) lo = mid;
-        else hi = mid - 1;
+__device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x, uint64_t keep, uint64_t stream) {
+    if (v.L == 0 || x <= v.kmin) return 0;
+    if (x > v.kmax) return v.N;
+    const uint64_t q = (x - v.kmin) >> v.rdx_shift;
+    uint64_t lo = min(ld64_hint(v.rdx + q, keep), v.L), hi = min(ld64_hint(v.rdx + q + 1, keep), v.L);
+    while (lo < hi) {  // count of intercepts < x, within [rdx[q], rdx[q+1])
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint64_t k = sizeof(KT) == 8 ? ld64_hint((const uint64_t*)v.icpt + mid, keep)
+                                           : (uint64_t)ld32_hint((const uint32_t*)v.icpt + mid, keep);
+        if (k < x) lo = mid + 1;
+        else hi = mid;
     }
-    for (int d = (int)top - 1; d >= 0; --d) {
-        const uint64_t nd = d ? v.level_n[d] : v.L;
-        const uint64_t base = 16 * lo;
-        uint64_t a = base, b = min(base + 16, nd) - 1;
-        while (a < b) {
-            const uint64_t mid = (a + b + 1) >> 1;
-            const uint64_t key = d ? __ldg(v.level[d] + mid) : ld_icpt<KT>(v.icpt, mid);
-            if (key < x) a = mid;
-            else b = mid - 1;
-        }
-        lo = a;
-    }
-    const uint64_t j = lo;
-    const SegRec r = load_rec(v.recs + j);
+    const uint64_t j = lo ? lo - 1 : 0;  // lo >= 1 for sorted keys: icpt[0] = kmin < x
+    const SegRec r = load_rec_hint(v.recs + j, stream);
     const uint64_t ks = r.kstart_w & kKeyMask;
-    const uint64_t ke = j + 1 < v.L ? (__ldg(&v.recs[j + 1].kstart_w) & kKeyMask) : v.N;
+    const uint64_t ke = j + 1 < v.L ? (ld64_hint(&v.recs[j + 1].kstart_w, stream) & kKeyMask) : v.N;
     const uint32_t n = (uint32_t)(ke - ks);
     uint32_t a = 1, b = n;  // first t in [1, n) with key(t) >= x, or n
     if (n >= 32 && r.slope > 0) {
@@ -295,7 +462,7 @@ __device__ uint64_t lower_bound_one(const ColView& v, uint64_t x, const uint64_t
     }
     while (a < b) {
         const uint32_t mid = (a + b) >> 1;
-        if (rec_key(v, r, mid) < x) a = mid + 1;
+        if (rec_key_hint(v, r, mid, stream) < x) a = mid + 1;
         else b = mid;
     }
     return ks + a;
@@ -304,12 +471,9 @@ __device__ uint64_t lower_bound_one(const ColView& v, uint64_t x, const uint64_t
 template <typename KT>
 __global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m,
                                                           uint64_t* __restrict__ out) {
-    extern __shared__ uint64_t s_top[];
-    const uint64_t ntop = v.top ? v.level_n[v.top] : v.L;
-    for (uint64_t k = threadIdx.x; k < ntop; k += blockDim.x) s_top[k] = top_at<KT>(v, nullptr, k);
-    __syncthreads();
+    const uint64_t keep = policy_keep(), stream = policy_stream();
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
-        out[q] = lower_bound_one<KT>(v, (uint64_t)vals[q], s_top);
+        out[q] = lower_bound_one<KT>(v, (uint64_t)vals[q], keep, stream);
 }
 
 // ------------------------------------------------------------------ serving: multi-column batches
@@ -320,6 +484,7 @@ template <typename KT>
 __global__ void serve_query_kernel(const ColView* __restrict__ views, const SrvReq* __restrict__ reqs, uint32_t nreq,
                                    uint64_t nq, const uint64_t* __restrict__ qin, uint64_t* __restrict__ qout,
                                    uint32_t* __restrict__ status) {
+    const uint64_t keep = policy_keep(), stream = policy_stream();
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nq; q += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t lo = 0, hi = nreq - 1;
         while (lo < hi) {
@@ -335,33 +500,44 @@ __global__ void serve_query_kernel(const ColView* __restrict__ views, const SrvR
                 atomicOr(status, kStOutOfRange);
                 qout[q] = 0;
             } else {
-                qout[q] = access_one(v, x);
+                qout[q] = access_one(v, x, keep, stream);
             }
         } else {
-            qout[q] = lower_bound_one<KT>(v, x, nullptr);
+            qout[q] = lower_bound_one<KT>(v, x, keep, stream);
         }
     }
 }
 
 // Range decodes of one batch: work item w is tile first_tile + (w - work_off[r])
 // of request r, written to that request's own device buffer.
+struct ServeSrc {
+    const ColView* views;
+    const SrvReq* reqs;
+    const uint64_t* work_off;
+    uint32_t nreq;
+    __device__ void operator()(uint64_t w, const ColView** vv, uint64_t* t, uint64_t* lo, uint64_t* hi,
+                               void** o) const {
+        uint32_t a = 0, b = nreq - 1;
+        while (a < b) {
+            const uint32_t mid = (a + b + 1) >> 1;
+            if (work_off[mid] <= w) a = mid;
+            else b = mid - 1;
+        }
+        const SrvReq& rq = reqs[a];
+        *vv = views + rq.col;
+        *t = rq.first_tile + (w - work_off[a]);
+        *lo = rq.begin;
+        *hi = rq.begin + rq.count;
+        *o = (void*)rq.out;
+    }
+};
+
 template <typename KT>
 __global__ void __launch_bounds__(kDecThreads)
 serve_decode_kernel(const ColView* __restrict__ views, const SrvReq* __restrict__ reqs, uint32_t nreq,
                     const uint64_t* __restrict__ work_off, uint32_t smem_segs) {
     extern __shared__ __align__(16) uint8_t smem[];
-    const uint64_t total = work_off[nreq];
-    for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
-        uint32_t lo = 0, hi = nreq - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (work_off[mid] <= w) lo = mid;
-            else hi = mid - 1;
-        }
-        const SrvReq& rq = reqs[lo];
-        decode_tile<KT>(views[rq.col], rq.first_tile + (w - work_off[lo]), rq.begin, rq.begin + rq.count,
-                        (KT*)rq.out, smem, smem_segs);
-    }
+    dec_pipeline<KT>(work_off[nreq], ServeSrc{views, reqs, work_off, nreq}, smem, smem_segs);
 }
 
 // Derived directories: segment records and rank bits (one CTA per chunk).
@@ -391,10 +567,50 @@ __global__ void rank_before_kernel(RankWord* __restrict__ rank, uint64_t nw, con
         rank[q].before = before[q];
 }
 
+// Radix table: rdx[q] = the number of intercepts < kmin + q 2^shift, i.e.
+// the lower bound of the bucket's first value in seg_icpt, for q = 0..nb
+// (nb = the buckets [kmin, kmax] spans).  First every 64th entry by a binary
+// search over all intercepts, then the others by a binary search between
+// their two sampled neighbours (usually a run of a few entries), so that no
+// thread's work depends on how the values spread.  The searches stay inside
+// [0, L] whatever the intercepts hold (a blob read back from a caller need
+// not be sorted).
 template <typename KT>
-__global__ void level_kernel(ColView v, uint64_t* __restrict__ lvl, uint64_t n, uint64_t stride) {
-    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
-        lvl[k] = ld_icpt<KT>(v.icpt, k * stride);
+__device__ __forceinline__ uint64_t rdx_lower(const ColView& v, uint64_t q, uint64_t lo, uint64_t hi) {
+    if (q > ((~0ull - v.kmin) >> v.rdx_shift)) return hi;  // the bucket starts past 2^64 - 1
+    const uint64_t x = v.kmin + (q << v.rdx_shift);
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (ld_icpt<KT>(v.icpt, mid) < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename KT>
+__global__ void radix_coarse_kernel(ColView v, uint64_t* __restrict__ rdx, uint64_t nb) {
+    const uint64_t nc = nb / 64 + 1;  // entries 0, 64, ..., and nb
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c <= nc; c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = min(64 * c, nb);
+        rdx[q] = rdx_lower<KT>(v, q, 0, v.L);
+    }
+}
+
+template <typename KT>
+__global__ void radix_fine_kernel(ColView v, uint64_t* __restrict__ rdx, uint64_t nb) {
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nb; q += (uint64_t)gridDim.x * blockDim.x) {
+        if ((q & 63u) == 0) continue;
+        const uint64_t a = q & ~63ull, b = min(a + 64, nb);
+        rdx[q] = rdx_lower<KT>(v, q, rdx[a], max(rdx[a], rdx[b]));
+    }
+}
+
+// ends[0] = first key, ends[1] = last key (N >= 1).
+__global__ void ends_kernel(ColView v, uint64_t* __restrict__ ends) {
+    if (threadIdx.x == 0) {
+        ends[0] = v.key_bytes == 4 ? (uint64_t)__ldg((const uint32_t*)v.icpt) : __ldg((const uint64_t*)v.icpt);
+        ends[1] = access_one(v, v.N - 1, policy_keep(), policy_stream());
+    }
 }
 
 __global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles, uint32_t* __restrict__ max_segs) {
@@ -427,6 +643,22 @@ __global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles, uint32_
     d.seg_hi = last_start_le(local1);
     d.chunk = (uint32_t)c;
     d.n = n;
+    d.pad = 0;
+    // payload words of the residuals of keys local0..local1: from the first
+    // residual of seg_lo at or after local0 to the end of seg_hi's residuals up
+    // to local1, one word more (an extract reads a word pair), 16-byte aligned
+    {
+        const uint64_t base = 64 * v.cwb[c];
+        const uint32_t s0 = v.start[d.seg_lo], w0 = v.width[d.seg_lo];
+        const uint32_t s1 = v.start[d.seg_hi], w1 = v.width[d.seg_hi];
+        const uint64_t lo_bit = base + v.bitoff[d.seg_lo] + (uint64_t)w0 * (max(local0, s0 + 1) - s0 - 1);
+        const uint64_t hi_bit = base + v.bitoff[d.seg_hi] + (uint64_t)w1 * (local1 - s1);
+        const uint64_t wlo = (lo_bit >> 5) & ~3ull;
+        uint64_t whi = ((((hi_bit + 31) >> 5) + 1) + 3) & ~3ull;
+        if (whi > 2 * v.W) whi = 2 * v.W;
+        d.pw0 = wlo;
+        d.pwn = hi_bit > lo_bit && whi > wlo ? (uint32_t)(whi - wlo) : 0u;
+    }
     tiles[t] = d;
     atomicMax(max_segs, (uint32_t)(d.seg_hi - d.seg_lo + 1));
 }
@@ -475,29 +707,23 @@ int build_derived(lc_column* col, cudaStream_t st) {
     rc = cuda_status(cudaMemsetAsync(col->status, 0, 4, st));
     if (rc) return rc;
 
-    // segment records, rank words, sampled intercept levels
+    // segment records, rank words, the radix table over the intercepts
     const uint64_t nw = (N + 63) / 64;
-    uint32_t top = 0;
-    uint64_t level_n[kMaxLevels] = {L};
-    uint64_t level_off[kMaxLevels] = {0};
-    uint64_t lv_total = 0;
-    while (level_n[top] > kTopMax && top + 1 < (uint32_t)kMaxLevels) {
-        ++top;
-        level_n[top] = (level_n[top - 1] + 15) / 16;
-        level_off[top] = lv_total;
-        lv_total += level_n[top];
-    }
+    // (lower_bound needs sorted keys: no table in list mode)
+    uint32_t blog = 0;  // B = 2^blog buckets, about two per segment, at most 2^kRdxMaxLog
+    while (blog < kRdxMaxLog && (1ull << blog) < 2 * L) ++blog;
+    const uint64_t B = col->list_mode ? 0 : 1ull << blog;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t off_rank = al(sizeof(SegRec) * L);
-    const size_t off_lv = al(off_rank + sizeof(RankWord) * nw);
-    const size_t bytes2 = al(off_lv + 8 * lv_total) + 256;
+    const size_t off_rdx = al(off_rank + sizeof(RankWord) * nw);
+    const size_t bytes2 = al(off_rdx + (B ? 8 * (B + 1) : 0)) + 256;
     if (cudaMallocAsync((void**)&col->derived2, bytes2, st) != cudaSuccess) {
         col->derived2 = nullptr;
         return LC_ERR_NOMEM;
     }
     SegRec* recs = (SegRec*)col->derived2;
     RankWord* rank = (RankWord*)(col->derived2 + off_rank);
-    uint64_t* lv = (uint64_t*)(col->derived2 + off_lv);
+    uint64_t* rdx = (uint64_t*)(col->derived2 + off_rdx);
     if (nw) {
         rc = cuda_status(cudaMemsetAsync(rank, 0, sizeof(RankWord) * nw, st));
         if (rc) return rc;
@@ -518,11 +744,9 @@ int build_derived(lc_column* col, cudaStream_t st) {
     v.chunk_tile_begin = col->chunk_tile_begin;
     v.recs = recs;
     v.rank = rank;
-    for (int d = 0; d < kMaxLevels; ++d) {
-        v.level[d] = (d && d <= (int)top) ? lv + level_off[d] : nullptr;
-        v.level_n[d] = d <= (int)top ? level_n[d] : 0;
-    }
-    v.top = top;
+    v.rdx = B ? rdx : nullptr;
+    v.kmin = v.kmax = 0;
+    v.rdx_shift = 0;
     v.key_bytes = col->key_bytes;
     v.status = col->status;
     v.N = N;
@@ -535,9 +759,12 @@ int build_derived(lc_column* col, cudaStream_t st) {
     if (C) {
         rc = cuda_status(cudaMemsetAsync(col->status + 1, 0, 4, st));
         if (rc) return rc;
-        tile_dir_kernel<<<(unsigned)((col->ntiles + 255) / 256), 256, 0, st>>>(v, col->tiles, col->status + 1);
-        if (col->key_bytes == 4) rec_kernel<uint32_t><<<(unsigned)C, 128, 0, st>>>(v, recs, rank);
-        else rec_kernel<uint64_t><<<(unsigned)C, 128, 0, st>>>(v, recs, rank);
+        {
+            KTime kt("derived", st);
+            tile_dir_kernel<<<(unsigned)((col->ntiles + 255) / 256), 256, 0, st>>>(v, col->tiles, col->status + 1);
+            if (col->key_bytes == 4) rec_kernel<uint32_t><<<(unsigned)C, 128, 0, st>>>(v, recs, rank);
+            else rec_kernel<uint64_t><<<(unsigned)C, 128, 0, st>>>(v, recs, rank);
+        }
         note_launch(2);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
@@ -556,24 +783,41 @@ int build_derived(lc_column* col, cudaStream_t st) {
             note_launch();
             rc = cuda_status(cudaGetLastError());
         }
-        for (uint32_t d = 1; !rc && d <= top; ++d) {
-            uint64_t stride = 1;
-            for (uint32_t e = 0; e < d; ++e) stride *= 16;
-            const unsigned gl = (unsigned)std::min<uint64_t>((level_n[d] + 255) / 256, 65535);
-            if (col->key_bytes == 4) level_kernel<uint32_t><<<gl, 256, 0, st>>>(v, lv + level_off[d], level_n[d], stride);
-            else level_kernel<uint64_t><<<gl, 256, 0, st>>>(v, lv + level_off[d], level_n[d], stride);
-            note_launch();
-            rc = cuda_status(cudaGetLastError());
-        }
         cudaFreeAsync(t, st);
         if (rc) return rc;
-        uint32_t ms = 0;
-        rc = cuda_status(cudaMemcpyAsync(&ms, col->status + 1, 4, cudaMemcpyDeviceToHost, st));
+        // first and last key, and the most segments one decode tile meets
+        uint64_t* ends = (uint64_t*)(col->status + 2);
+        ends_kernel<<<1, 32, 0, st>>>(v, ends);
+        note_launch();
+        uint64_t h[3] = {0, 0, 0};
+        rc = cuda_status(cudaMemcpyAsync(h, col->status, 24, cudaMemcpyDeviceToHost, st));
         if (rc) return rc;
         rc = cuda_status(cudaStreamSynchronize(st));
         if (rc) return rc;
-        v.max_tile_segs = std::max<uint32_t>(ms, 1);
-        return LC_OK;
+        v.max_tile_segs = std::max<uint32_t>((uint32_t)(h[0] >> 32), 1);
+        v.kmin = h[1];
+        v.kmax = h[2];
+        if (!B) return LC_OK;
+        uint32_t sh = 0;
+        while (sh < 64 && ((v.kmax - v.kmin) >> sh) >= B) ++sh;
+        v.rdx_shift = sh;
+        const uint64_t nb = v.kmax >= v.kmin ? ((v.kmax - v.kmin) >> sh) + 1 : 1;  // buckets in use, <= B
+        {
+            KTime kt("derived_radix", st);
+            const unsigned gc = (unsigned)std::min<uint64_t>((nb / 64 + 2 + 255) / 256, 65535);
+            const unsigned gf = (unsigned)std::min<uint64_t>((nb + 255) / 256, 65535);
+            if (col->key_bytes == 4) {
+                radix_coarse_kernel<uint32_t><<<gc, 256, 0, st>>>(v, rdx, nb);
+                radix_fine_kernel<uint32_t><<<gf, 256, 0, st>>>(v, rdx, nb);
+            } else {
+                radix_coarse_kernel<uint64_t><<<gc, 256, 0, st>>>(v, rdx, nb);
+                radix_fine_kernel<uint64_t><<<gf, 256, 0, st>>>(v, rdx, nb);
+            }
+        }
+        note_launch(2);
+        rc = cuda_status(cudaGetLastError());
+        if (rc) return rc;
+        return cuda_status(cudaStreamSynchronize(st));
     }
     v.max_tile_segs = 1;
     return cuda_status(cudaStreamSynchronize(st));
@@ -672,15 +916,19 @@ int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cud
 int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* out, cudaStream_t st) {
     if (m == 0) return LC_OK;
     const ColView& v = col->view;
-    const uint64_t ntop = v.top ? v.level_n[v.top] : v.L;
-    const size_t smem = 8 * std::max<uint64_t>(ntop, 1);
-    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 6);
+    // one query per thread, as many CTAs as stay resident (grid-stride)
+    int occ = 0;
+    const cudaError_t oe = col->key_bytes == 4
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lower_bound_kernel<uint32_t>, 256, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lower_bound_kernel<uint64_t>, 256, 0);
+    if (oe != cudaSuccess || occ < 1) occ = 1;
+    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * occ);
     {
         KTime kt("lower_bound", st);
         if (col->key_bytes == 4)
-            lower_bound_kernel<uint32_t><<<grid, 256, smem, st>>>(v, (const uint32_t*)vals, m, out);
+            lower_bound_kernel<uint32_t><<<grid, 256, 0, st>>>(v, (const uint32_t*)vals, m, out);
         else
-            lower_bound_kernel<uint64_t><<<grid, 256, smem, st>>>(v, (const uint64_t*)vals, m, out);
+            lower_bound_kernel<uint64_t><<<grid, 256, 0, st>>>(v, (const uint64_t*)vals, m, out);
     }
     note_launch();
     return cuda_status(cudaGetLastError());

@@ -263,3 +263,40 @@ def test_full_size_column(kind, eps):
     assert np.array_equal(host(lc.lc_lower_bound(col, dev(q))), np.searchsorted(keys, q, side="left"))
     assert lc.lc_status(col) == lc.LC_OK
     col.free()
+
+
+def _lower_bound_matches(keys, eps, check_bytes=True):
+    col = lc.lc_compress(dev(keys), eps=eps)
+    if check_bytes:
+        assert lc.lc_serialize(col) == oracle.compress(keys, eps, 16)
+    rng = np.random.default_rng(7)
+    k = keys.astype(np.int64) if keys.dtype == np.uint32 else keys
+    lo, hi = int(keys[0]), int(keys[-1])
+    q = np.concatenate([
+        rng.integers(max(0, lo - 5), hi + 6, size=100_000, dtype=np.uint64).astype(keys.dtype),
+        keys, np.maximum(keys, 1) - 1, np.minimum(keys, np.iinfo(keys.dtype).max - 1) + 1,
+        np.array([0, hi, np.iinfo(keys.dtype).max], dtype=keys.dtype),
+    ]).astype(keys.dtype)
+    got = host(lc.lc_lower_bound(col, dev(q)))
+    assert np.array_equal(got, np.searchsorted(keys, q, side="left"))
+    col.free()
+
+
+@pytest.mark.parametrize("dt", [np.uint32, np.uint64])
+@pytest.mark.parametrize("n,eps", [(1, 0), (20, 0), (3000, 0), (300_000, 0), (300_000, 7)])
+def test_lower_bound_radix_table_shapes(n, eps, dt):
+    """lower_bound against searchsorted: one segment, a few, and many segments
+    per radix bucket; queries on, between and outside the keys."""
+    keys = inputs.lognormal_gaps(n, seed=n + eps, mu=1.0, sigma=1.0, dtype=dt)
+    _lower_bound_matches(keys, eps)
+
+
+def test_lower_bound_skewed_buckets_and_capped_table():
+    # nearly all intercepts in the first radix bucket: a long run of the table
+    rng = np.random.default_rng(11)
+    dense = np.cumsum(rng.integers(1, 4, size=400_000, dtype=np.uint64)).astype(np.uint64)
+    keys = np.concatenate([dense, np.array([1 << 60, (1 << 60) + 7], np.uint64)])
+    _lower_bound_matches(keys, 0)
+    # more than 2^21 segments: the table stops growing at 2^22 buckets
+    big = inputs.lognormal_gaps(6_000_000, seed=12, mu=1.0, sigma=1.0)
+    _lower_bound_matches(big, 0, check_bytes=False)
