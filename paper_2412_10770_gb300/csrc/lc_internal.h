@@ -74,13 +74,15 @@ static_assert(sizeof(TileDesc) == 48, "TileDesc layout");
 //
 // SegRec: one segment's model in 32 bytes (one sector): intercept K[s_j],
 // Q32 slope, the global index of its anchor with the width in the top byte,
-// and the global payload bit of its residual t = 1.
+// and the global payload bit of its residual t = 1 with the segment's key
+// count n_j - 1 in the top 16 bits.
 struct SegRec {
     uint64_t icpt;
     int64_t slope;
     uint64_t kstart_w;  // anchor key index (low 56 bits) | width << 56
-    uint64_t bit1;
+    uint64_t bit1_n;    // payload bit of residual 1 (low 48 bits) | (n_j - 1) << 48
 };
+constexpr uint64_t kBitMask = (1ull << 48) - 1;
 // RankWord: anchor bits of keys [64q, 64q + 64) and the number of anchors
 // before key 64q, so that the segment of key i is
 // before + popcount(bits & mask(i)) - 1.

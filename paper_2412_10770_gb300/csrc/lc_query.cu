@@ -165,29 +165,29 @@ __device__ void dec_issue(const ColView& v, uint64_t t, uint64_t lo_key, uint64_
     if (td.pwn) bulk_load(sd.pay, v.pay32 + td.pw0, td.pwn * 4u, bar);
 }
 
-// All threads: the wanted keys of the item in stage sd.
+// All threads: the wanted keys of the item in stage sd.  Everything inside a
+// tile is 32-bit: positions, segment offsets and payload bits relative to the
+// tile (the low 32 bits of the global values suffice because every difference
+// taken is below 2^32).  The anchor (t = 0) takes a zero-width field, so no
+// key branches; four keys per thread are in flight at once.
 template <typename KT>
 __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd) {
-    KT* __restrict__ out = (KT*)d.out;
     const uint32_t p0 = (uint32_t)(d.lo - d.kbeg), p1 = (uint32_t)(d.hi - d.kbeg);
+    KT* __restrict__ out = (KT*)d.out + (d.lo - d.lo_key) - p0;  // out[p]: key kbeg + p
+    const uint32_t kb32 = (uint32_t)d.kbeg, koff = kb32 & 63u;
+    const uint32_t j0 = (uint32_t)d.j0, pb0 = (uint32_t)d.pbit0, nsm1 = d.ns - 1;
+#pragma unroll 4
     for (uint32_t p = p0 + threadIdx.x; p < p1; p += kDecThreads) {
-        const uint64_t g = d.kbeg + p;
-        const RankWord rw = sd.rank[(g >> 6) - d.r0];
-        const uint64_t j = rw.before + __popcll(rw.bits & (~0ull >> (63u - (uint32_t)(g & 63u)))) - 1;
-        const SegRec r = sd.rec[min(j - d.j0, (uint64_t)d.ns - 1)];  // the clamp only guards shared memory
-        const uint32_t t = (uint32_t)(g - (r.kstart_w & ((1ull << 56) - 1)));
-        uint64_t key = r.icpt;
-        if (t) {
-            const uint32_t w = (uint32_t)(r.kstart_w >> 56);
-            uint32_t z = 0;
-            if (w) {
-                const uint32_t lb = (uint32_t)(r.bit1 + (uint64_t)w * (t - 1) - d.pbit0);
-                const uint32_t q = min(lb >> 5, kPayWords - 2);
-                z = extract_bits(sd.pay[q], sd.pay[q + 1], lb & 31u, w);
-            }
-            key += (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(z));
-        }
-        out[g - d.lo_key] = (KT)key;
+        const uint32_t g = kb32 + p;
+        const RankWord rw = sd.rank[(koff + p) >> 6];
+        const uint32_t jr = (uint32_t)rw.before - j0 + (uint32_t)__popcll(rw.bits << (63u - (g & 63u))) - 1u;
+        const SegRec r = sd.rec[min(jr, nsm1)];  // the clamp only guards shared memory
+        const uint32_t t = g - (uint32_t)r.kstart_w;
+        const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+        const uint32_t lb = (uint32_t)r.bit1_n - pb0 + w * (t - 1u);
+        const uint32_t q = min(lb >> 5, kPayWords - 2);
+        const uint32_t z = extract_bits(sd.pay[q], sd.pay[q + 1], lb & 31u, t ? w : 0u);
+        out[p] = (KT)(r.icpt + (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(z)));
     }
 }
 
@@ -255,7 +255,7 @@ struct WholeSrc {
 
 // Persistent: tiles t0 .. t0 + nt - 1, keys [begin, end) into out[g - begin].
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
+__global__ void __launch_bounds__(kDecThreads, 8) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
                                                              uint64_t end, KT* __restrict__ out) {
     extern __shared__ __align__(16) uint8_t smem[];
     dec_pipeline<KT>(nt, WholeSrc<KT>{&v, t0, begin, end, out}, smem, v.max_tile_segs);
@@ -305,7 +305,7 @@ struct RangesSrc {
 };
 
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads)
+__global__ void __launch_bounds__(kDecThreads, 8)
 decode_ranges_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
                      const uint64_t* __restrict__ out_off, uint64_t m, const uint64_t* __restrict__ first,
                      const uint64_t* __restrict__ work_off, KT* __restrict__ out) {
@@ -320,7 +320,7 @@ __device__ __forceinline__ uint64_t rec_key(const ColView& v, const SegRec& r, u
     const uint32_t w = (uint32_t)(r.kstart_w >> 56);
     const int64_t line = line_at(r.slope, t);
     if (w == 0) return r.icpt + (uint64_t)line;
-    const uint64_t pos = r.bit1 + (uint64_t)w * (t - 1);
+    const uint64_t pos = (r.bit1_n & kBitMask) + (uint64_t)w * (t - 1);
     const uint64_t wi = pos >> 5;  // < 2W: the residual's bits lie inside the payload
     const uint32_t lo = __ldg(v.pay32 + wi);
     const uint32_t hi = wi + 1 < 2 * v.W ? __ldg(v.pay32 + wi + 1) : 0u;
@@ -334,7 +334,7 @@ __device__ __forceinline__ SegRec load_rec(const SegRec* p) {
     r.icpt = a.x;
     r.slope = (int64_t)a.y;
     r.kstart_w = b.x;
-    r.bit1 = b.y;
+    r.bit1_n = b.y;
     return r;
 }
 
@@ -381,7 +381,7 @@ __device__ __forceinline__ SegRec load_rec_hint(const SegRec* p, uint64_t pol) {
     r.icpt = a.x;
     r.slope = (int64_t)a.y;
     r.kstart_w = b.x;
-    r.bit1 = b.y;
+    r.bit1_n = b.y;
     return r;
 }
 
@@ -391,7 +391,7 @@ __device__ __forceinline__ uint64_t rec_key_hint(const ColView& v, const SegRec&
     const uint32_t w = (uint32_t)(r.kstart_w >> 56);
     const int64_t line = line_at(r.slope, t);
     if (w == 0) return r.icpt + (uint64_t)line;
-    const uint64_t pos = r.bit1 + (uint64_t)w * (t - 1);
+    const uint64_t pos = (r.bit1_n & kBitMask) + (uint64_t)w * (t - 1);
     const uint64_t wi = pos >> 5;
     const uint32_t lo = ld32_hint(v.pay32 + wi, pol);
     const uint32_t hi = wi + 1 < 2 * v.W ? ld32_hint(v.pay32 + wi + 1, pol) : 0u;
@@ -447,8 +447,7 @@ __device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x
     const uint64_t j = lo ? lo - 1 : 0;  // lo >= 1 for sorted keys: icpt[0] = kmin < x
     const SegRec r = load_rec_hint(v.recs + j, stream);
     const uint64_t ks = r.kstart_w & kKeyMask;
-    const uint64_t ke = j + 1 < v.L ? (ld64_hint(&v.recs[j + 1].kstart_w, stream) & kKeyMask) : v.N;
-    const uint32_t n = (uint32_t)(ke - ks);
+    const uint32_t n = (uint32_t)(r.bit1_n >> 48) + 1u;
     uint32_t a = 1, b = n;  // first t in [1, n) with key(t) >= x, or n
     if (n >= 32 && r.slope > 0) {
         const uint32_t w = (uint32_t)(r.kstart_w >> 56);
@@ -533,7 +532,7 @@ struct ServeSrc {
 };
 
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads)
+__global__ void __launch_bounds__(kDecThreads, 8)
 serve_decode_kernel(const ColView* __restrict__ views, const SrvReq* __restrict__ reqs, uint32_t nreq,
                     const uint64_t* __restrict__ work_off, uint32_t smem_segs) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -545,13 +544,17 @@ template <typename KT>
 __global__ void rec_kernel(ColView v, SegRec* __restrict__ recs, RankWord* __restrict__ rank) {
     const uint64_t c = blockIdx.x;
     const uint64_t ckb = v.ckb[c], bit0 = 64 * v.cwb[c];
-    for (uint64_t j = v.csb[c] + threadIdx.x; j < v.csb[c + 1]; j += blockDim.x) {
-        const uint64_t k = ckb + v.start[j];
+    const uint64_t s1 = v.csb[c + 1];
+    const uint32_t nc = (uint32_t)(v.ckb[c + 1] - ckb);
+    for (uint64_t j = v.csb[c] + threadIdx.x; j < s1; j += blockDim.x) {
+        const uint32_t a = v.start[j];
+        const uint32_t e = j + 1 < s1 ? (uint32_t)v.start[j + 1] : nc;
+        const uint64_t k = ckb + a;
         SegRec r;
         r.icpt = ld_icpt<KT>(v.icpt, j);
         r.slope = v.slope[j];
         r.kstart_w = k | ((uint64_t)v.width[j] << 56);
-        r.bit1 = bit0 + v.bitoff[j];
+        r.bit1_n = (bit0 + v.bitoff[j]) | ((uint64_t)(e - a - 1) << 48);
         recs[j] = r;
         atomicOr((unsigned long long*)&rank[k >> 6].bits, 1ull << (k & 63u));
     }
@@ -686,6 +689,8 @@ int set_smem() {
 
 int build_derived(lc_column* col, cudaStream_t st) {
     const uint64_t C = col->C, L = col->L, N = col->N;
+    // the segment records hold key indices in 56 bits and payload bits in 48
+    if (N >= (1ull << 56) || col->W >= (1ull << 42)) return LC_ERR_UNSUPPORTED;
     // host: tiles per chunk from the chunk directory
     std::vector<uint64_t> ctb(C + 1, 0);
     for (uint64_t c = 0; c < C; ++c) {
