@@ -3,17 +3,20 @@
 // arithmetic so that the bytes equal those of the CPU definition.
 //
 // Pipeline for C chunks (each chunk is independent: segments never cross one):
-//   spec_kernel   one CTA per 8192-key window; speculative greedy per 32-key
-//                 block (S) and a re-walk from the predicted entry (F), on keys
-//                 staged in shared memory.
-//   chain_kernel  one warp per chunk chains the blocks in order (R): the true
-//                 anchors as one bit per key, and the segment count per chunk;
-//                 the slope of every segment longer than 64 keys (its walk
-//                 ends with the segment's cone).
+//   spec_kernel   one CTA per 8192-key window, keys staged in shared memory;
+//                 one thread per 64-key span runs the greedy from 96 keys
+//                 before its span (a warm-up that almost always brings it onto
+//                 the true chain) and records its anchors, entry and exit per
+//                 32-key block.
+//   chain_kernel  one warp per chunk follows the blocks in order: a ballot
+//                 accepts every run of blocks whose walks join up, the warp
+//                 walks the cone itself elsewhere; the true anchors as one bit
+//                 per key, the segment count per chunk, and the slope of every
+//                 segment longer than 96 keys (its walk ends with the cone).
 //   scan          chunk_seg_begin.
 //   fit_short_kernel  one CTA per 8192-key window, one thread per 32-key
 //                 block: the cone, slope and width of every segment of at most
-//                 64 keys that starts in the block (sequential, keys in shared
+//                 96 keys that starts in the block (sequential, keys in shared
 //                 memory); longer segments queue their width pass.
 //   long_width_kernel  one warp per 2048-key piece of a long segment.
 //   bitoff_kernel one CTA per chunk: bit offsets (a scan of w (n-1)).
@@ -35,8 +38,6 @@ __device__ uint64_t g_magic[kMaxChunk];
 namespace {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;     // segment end not found within the walk limit
-constexpr uint32_t kInvalid = 0xFFFFFFFEu;  // (F) had no entry point
-constexpr int kModelThreads = 256;
 constexpr int kPackThreads = 256;
 constexpr uint32_t kWin = 2048;             // keys per pack window
 constexpr uint32_t kWalkAhead = 32 * 32;    // keys the warp walk prefetches into L2 ahead of its step
@@ -46,108 +47,138 @@ __device__ __forceinline__ uint64_t ldk(const KT* __restrict__ K, uint32_t i) {
     return (uint64_t)__ldg(K + i);
 }
 
-// The greedy cone (Def. 2, shrinking-cone reading) with a whole warp: each
-// step takes 32 keys (one per lane), an inclusive max/min scan over the lanes of
-// their slope fractions (frac_step's reading, no division) gives the cone after
-// every key, and the first lane whose cone is empty is the next anchor.  The
-// next step's keys are loaded while this step computes; keys further ahead are
-// prefetched into L2.  Called with all 32 lanes active and warp-uniform
-// arguments.  *fin receives the cone of the segment's keys (every lane).
+// Key i as a cone element relative to the anchor (x, kx): the real Q32
+// slopes it admits are [2^32 (D - eps)/d, 2^32 (D + eps + 1)/d) (frac_step's
+// reading).  A key whose lower bound reaches the int64 cap pins the lower
+// bound above every upper one; a key past the chunk is the identity.
+__device__ __forceinline__ Frac key_frac(uint64_t Ki, uint32_t i, uint32_t x, uint64_t kx, uint32_t n, int64_t eps) {
+    Frac v;
+    const uint32_t d = i - x;
+    const uint64_t D = Ki - kx;
+    if (i >= n) {
+        v = frac_open();
+    } else if (D < ((uint64_t)d << 31) + (uint64_t)eps) {
+        v.X = (int64_t)D - eps;
+        v.E = d;
+        v.Y = D + (uint64_t)eps + 1;
+        v.F = d;
+    } else {
+        v.X = (1ll << 47) - 1;
+        v.E = 1;
+        v.Y = 1ull << 31;
+        v.F = 1;
+    }
+    return v;
+}
+
+// Intersection of two cones: the larger lower fraction, the smaller upper.
+__device__ __forceinline__ void frac_meet(Frac& v, const Frac& o) {
+    if (frac_gt(o.X, o.E, v.X, v.E)) { v.X = o.X; v.E = o.E; }
+    if (o.Y * (uint64_t)v.F < v.Y * (uint64_t)o.F) { v.Y = o.Y; v.F = o.F; }
+}
+
+__device__ __forceinline__ Frac shfl_frac(const Frac& v, int src) {
+    Frac f;
+    f.X = __shfl_sync(0xFFFFFFFFu, v.X, src);
+    f.E = __shfl_sync(0xFFFFFFFFu, v.E, src);
+    f.Y = __shfl_sync(0xFFFFFFFFu, v.Y, src);
+    f.F = __shfl_sync(0xFFFFFFFFu, v.F, src);
+    return f;
+}
+
+constexpr uint32_t kWalkLane = 8;                 // keys per lane in one step of the warp walk
+constexpr uint32_t kWalkStep = 32 * kWalkLane;    // 256 keys per step
+
+// The greedy cone (Def. 2, shrinking-cone reading) with a whole warp, 256
+// keys per step: lane l intersects the slope intervals of keys p + 8l ..
+// p + 8l + 7, an inclusive scan over the lanes gives the cone after every
+// lane's keys, and the first lane whose cone is empty holds the next anchor,
+// which that lane finds key by key from the cone before it.  The keys of the
+// next step are loaded while this one computes.  Called with all 32 lanes
+// active and warp-uniform arguments.  *fin receives the cone of the
+// segment's keys (every lane).
 template <typename KT>
 __device__ __forceinline__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, int64_t eps, uint32_t lane,
                               Frac* fin) {
     const uint64_t kx = ldk(K, x);
     Frac cone = frac_open();
     uint32_t p = x + 1;
-    // the keys of the next four steps are in flight in a register ring
-    uint64_t k1 = p + lane < n ? ldk(K, p + lane) : 0;
-    uint64_t k2 = p + 32 + lane < n ? ldk(K, p + 32 + lane) : 0;
-    uint64_t k3 = p + 64 + lane < n ? ldk(K, p + 64 + lane) : 0;
-    uint64_t k4 = p + 96 + lane < n ? ldk(K, p + 96 + lane) : 0;
+    uint64_t cur[kWalkLane], nxt[kWalkLane];
+#pragma unroll
+    for (uint32_t u = 0; u < kWalkLane; ++u) {
+        const uint32_t i = p + kWalkLane * lane + u;
+        nxt[u] = i < n ? ldk(K, i) : 0;
+    }
     while (p < n) {
-        const uint32_t i = p + lane;
-        const uint64_t Ki = k1;
-        k1 = k2;
-        k2 = k3;
-        k3 = k4;
-        k4 = i + 128 < n ? ldk(K, i + 128) : 0;
-        if (i + kWalkAhead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + i + kWalkAhead));
-        const uint32_t d = i - x;
-        const uint64_t D = Ki - kx;
-        // fast path: every key's slope interval contains the carried cone, so the
-        // cone does not move and every key joins
-        {
-            const bool inside = i >= n || (D < ((uint64_t)d << 31) + (uint64_t)eps &&
-                                           !frac_gt((int64_t)D - eps, d, cone.X, cone.E) &&
-                                           (D + (uint64_t)eps + 1) * (uint64_t)cone.F >= cone.Y * (uint64_t)d);
-            if (__all_sync(0xFFFFFFFFu, inside)) {
-                if (p + 32 >= n) {
-                    *fin = cone;
-                    return n;
-                }
-                p += 32;
-                continue;
+#pragma unroll
+        for (uint32_t u = 0; u < kWalkLane; ++u) cur[u] = nxt[u];
+        const uint32_t pn = p + kWalkStep;
+        if (pn < n) {
+#pragma unroll
+            for (uint32_t u = 0; u < kWalkLane; ++u) {
+                const uint32_t i = pn + kWalkLane * lane + u;
+                nxt[u] = i < n ? ldk(K, i) : 0;
             }
+            if (pn + kWalkAhead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + pn + kWalkAhead + 8 * lane));
         }
-        // this lane's key as fractions; a key that cannot join pins the lower bound above any upper one
-        Frac v;
-        if (i < n && D < ((uint64_t)d << 31) + (uint64_t)eps) {
-            v.X = (int64_t)D - eps;
-            v.E = d;
-            v.Y = D + (uint64_t)eps + 1;
-            v.F = d;
-        } else {
-            v.X = (1ll << 47) - 1;
-            v.E = 1;
-            v.Y = 1ull << 31;
-            v.F = 1;
-        }
+        const uint32_t i0 = p + kWalkLane * lane;
+        Frac v = frac_open();
+#pragma unroll
+        for (uint32_t u = 0; u < kWalkLane; ++u) frac_meet(v, key_frac(cur[u], i0 + u, x, kx, n, eps));
+        // inclusive scan of the lanes' cones, then the carried cone
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const int64_t ox = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
-            const uint32_t oe = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
-            const uint64_t oy = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
-            const uint32_t of = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
-            if (lane >= (uint32_t)off) {
-                if (frac_gt(ox, oe, v.X, v.E)) { v.X = ox; v.E = oe; }
-                if (oy * (uint64_t)v.F < v.Y * (uint64_t)of) { v.Y = oy; v.F = of; }
-            }
+            Frac o;
+            o.X = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
+            o.E = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
+            o.Y = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
+            o.F = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
+            if (lane >= (uint32_t)off) frac_meet(v, o);
         }
-        if (frac_gt(cone.X, cone.E, v.X, v.E)) { v.X = cone.X; v.E = cone.E; }
-        if (cone.Y * (uint64_t)v.F < v.Y * (uint64_t)cone.F) { v.Y = cone.Y; v.F = cone.F; }
+        frac_meet(v, cone);
         const uint32_t badm = __ballot_sync(0xFFFFFFFFu, !frac_ok(v));
         if (badm) {
-            // the cone just before the first key that empties it
+            // lane bl holds the first key that empties the cone: find it from the cone before the lane
             const int bl = __ffs(badm) - 1;
-            const int src = bl > 0 ? bl - 1 : 0;
-            Frac f;
-            f.X = __shfl_sync(0xFFFFFFFFu, v.X, src);
-            f.E = __shfl_sync(0xFFFFFFFFu, v.E, src);
-            f.Y = __shfl_sync(0xFFFFFFFFu, v.Y, src);
-            f.F = __shfl_sync(0xFFFFFFFFu, v.F, src);
-            *fin = bl > 0 ? f : cone;
-            return min(p + (uint32_t)bl, n);
+            const Frac before = shfl_frac(v, bl > 0 ? bl - 1 : 0);
+            Frac c = bl > 0 ? before : cone;
+            uint32_t brk = 0;
+            if (lane == (uint32_t)bl) {
+                brk = kWalkLane;
+#pragma unroll
+                for (uint32_t u = 0; u < kWalkLane; ++u) {
+                    if (brk != kWalkLane) continue;
+                    Frac t = c;
+                    frac_meet(t, key_frac(cur[u], i0 + u, x, kx, n, eps));
+                    if (!frac_ok(t)) brk = u;
+                    else c = t;
+                }
+            }
+            brk = __shfl_sync(0xFFFFFFFFu, brk, bl);
+            *fin = shfl_frac(c, bl);
+            return min(p + kWalkLane * (uint32_t)bl + brk, n);
         }
-        cone.X = __shfl_sync(0xFFFFFFFFu, v.X, 31);
-        cone.E = __shfl_sync(0xFFFFFFFFu, v.E, 31);
-        cone.Y = __shfl_sync(0xFFFFFFFFu, v.Y, 31);
-        cone.F = __shfl_sync(0xFFFFFFFFu, v.F, 31);
-        p += 32;
+        cone = shfl_frac(v, 31);
+        p = pn;
     }
     *fin = cone;
     return n;
 }
 
-// ------------------------------------------------------------------ fit: speculation (S) and re-walk (F)
+// ------------------------------------------------------------------ fit: speculation with a warm-up walk
 
 constexpr uint32_t kFB = 32;                    // keys per fit block: one 32-bit word of anchor bits
-constexpr uint32_t kWinKeys = 8192;             // keys per speculation window, one CTA, one block per thread
-constexpr uint32_t kFCap = 32;                  // (S)/(F) follow a segment at most this far past its block
-constexpr int kSpecThreads = kWinKeys / kFB;    // 256
-constexpr uint32_t kStageKeys = kWinKeys + kFB + kFCap;
-constexpr uint32_t kStageSlots = kStageKeys + kStageKeys / 32 + 1;
+constexpr uint32_t kWinKeys = 8192;             // keys per window, one CTA
+constexpr uint32_t kSpan = 64;                  // keys per speculating thread (two blocks)
+constexpr uint32_t kWarm = 96;                  // keys a speculative walk runs before its span
+constexpr uint32_t kFCap = 32;                  // a speculative walk follows a segment at most this far past its span
+constexpr int kSpecThreads = kWinKeys / kSpan;  // 128
+constexpr uint32_t kSpecKeys = kWarm + kWinKeys + kFCap;
+constexpr uint32_t kSpecSlots = kSpecKeys + kSpecKeys / 64 + 1;
+constexpr int kShortThreads = kWinKeys / kFB;   // 256: one thread per block in fit_short_kernel
 constexpr int kChainThreads = 128;              // four chunks per CTA, one warp each
-constexpr uint32_t kShortMax = 64;              // segments of at most this many keys: one thread fits each
+constexpr uint32_t kShortMax = 96;              // segments of at most this many keys: one thread fits each
+static_assert(kShortMax == 96 && kShortMax > kSpan + kFCap - 1, "a speculative walk closes segments of at most kSpan + kFCap - 1 keys");
 constexpr uint32_t kPiece = 2048;               // keys per work item of a long segment's width pass
 
 // A segment longer than kShortMax keys, as its walk in the chain found it.
@@ -172,7 +203,7 @@ struct WinLong {
     int64_t M;
     uint32_t a, len, poff, pad;
 };
-constexpr uint32_t kLongPerWin = kWinKeys / (kShortMax + 1) + 1;  // segments > 64 keys starting in 8192 keys
+constexpr uint32_t kLongPerWin = kWinKeys / (kShortMax + 1) + 1;  // segments > 96 keys starting in 8192 keys
 // Keys key0 + [t0, t1) of long segment `item`.
 struct Piece {
     uint32_t item;
@@ -191,134 +222,165 @@ struct Staged {
         return (uint64_t)s[q + (q >> 5)];
     }
 };
+// The same with one pad slot per 64 keys, for lanes 64 keys apart.
+template <typename KT>
+struct Staged64 {
+    const KT* s;
+    uint32_t base;
+    __device__ __forceinline__ uint64_t operator()(uint32_t i) const {
+        const uint32_t q = i - base;
+        return (uint64_t)s[q + (q >> 6)];
+    }
+};
 
-// One CTA per window of 8192 keys of one chunk (plus one block of left halo
-// and kFCap keys of right halo, all staged in shared memory).
-//   (S) every thread runs the greedy from its block's first key: the
-//       speculative anchors of the block, and the anchor that follows the
-//       block's last segment (exitS, kNone if it runs past kFCap).
-//   (F) every thread assumes the true segment entering its block k ends at
-//       exitS[k-1] and re-walks the greedy from there until it meets a
-//       speculative anchor (the greedy from one anchor is deterministic, so
-//       from there on the speculation is exact); exitF is where the true path
-//       leaves the block under that assumption.
-// Per block: spec, fix (F's anchors before the meeting point), sync (offset of
-// the meeting point, 0xFF if none), exitS, exitF.  Also checks sortedness.
+// The cone of frac_step with 32-bit numerators, for walks whose key range
+// (plus eps + 1) stays below 2^31: then every D - eps and D + eps + 1 fits in
+// an int32 and every cross product in 48 bits, and the int64 cap on the
+// slope (2^31 per key) can never be reached.  Same decisions as frac_step.
+struct Frac32 {
+    int32_t X;
+    uint32_t E;
+    uint32_t Y;
+    uint32_t F;
+};
+__device__ __forceinline__ Frac32 frac32_open() { return Frac32{INT32_MIN, 1u, 0x7FFFFFFFu, 1u}; }
+__device__ __forceinline__ bool frac32_step(uint32_t D, uint32_t d, int32_t eps, Frac32& c) {
+    const int32_t xl = (int32_t)D - eps;
+    const uint32_t yh = D + (uint32_t)eps + 1u;
+    Frac32 n = c;
+    if ((int64_t)xl * c.E > (int64_t)c.X * d) { n.X = xl; n.E = d; }
+    if ((uint64_t)yh * c.F < (uint64_t)c.Y * d) { n.Y = yh; n.F = d; }
+    if (n.X >= 0 && (uint64_t)(uint32_t)n.X * n.F >= (uint64_t)n.Y * n.E) return false;
+    c = n;
+    return true;
+}
+
+// One thread's speculative walk: the greedy from `p` (taken as an anchor)
+// over keys [p, lim), recording its anchors at positions [s0, s0 + 96) as
+// bits (s0 is the thread's span start).  Returns true if the walk reached lim
+// inside a segment (its next anchor is then unknown unless lim is the
+// chunk's end).
+template <bool kNarrow, typename ST>
+__device__ __forceinline__ void spec_walk(const ST& st, uint32_t p, uint32_t lim, uint32_t s0, int64_t eps,
+                                          uint32_t bits[3]) {
+    uint32_t x = p;
+    uint64_t kx = st(p);
+    if (p >= s0) bits[(p - s0) >> 5] |= 1u << ((p - s0) & 31u);
+    if (kNarrow) {
+        Frac32 c = frac32_open();
+        for (uint32_t i = p + 1; i < lim; ++i) {
+            const uint64_t Ki = st(i);
+            if (frac32_step((uint32_t)(Ki - kx), i - x, (int32_t)eps, c)) continue;
+            x = i;
+            kx = Ki;
+            c = frac32_open();
+            if (i >= s0) bits[(i - s0) >> 5] |= 1u << ((i - s0) & 31u);
+        }
+    } else {
+        Frac c = frac_open();
+        for (uint32_t i = p + 1; i < lim; ++i) {
+            const uint64_t Ki = st(i);
+            if (frac_step(Ki - kx, i - x, eps, c)) continue;
+            x = i;
+            kx = Ki;
+            c = frac_open();
+            if (i >= s0) bits[(i - s0) >> 5] |= 1u << ((i - s0) & 31u);
+        }
+    }
+}
+
+// First set bit at position >= from in the 96-bit mask, or kNone.
+__device__ __forceinline__ uint32_t first_bit_from(const uint32_t bits[3], uint32_t from) {
+#pragma unroll
+    for (uint32_t w = 0; w < 3; ++w) {
+        if (from >= 32 * (w + 1)) continue;
+        const uint32_t sh = from > 32 * w ? from - 32 * w : 0u;
+        const uint32_t m = bits[w] & (0xFFFFFFFFu << sh);
+        if (m) return 32 * w + (uint32_t)(__ffs(m) - 1);
+    }
+    return kNone;
+}
+
+// One CTA per window of 8192 keys of one chunk; keys [w0 - kWarm, w1 + kFCap)
+// staged in shared memory.  Thread t owns the span of blocks 2t, 2t+1 and
+// runs the greedy from kWarm keys before the span (from the chunk start if
+// that is closer) to kFCap keys past it.  Greedy walks from different starts
+// meet after a few segments, so by the span the walk is almost always on the
+// true chain; the chain kernel checks that (a block is exact iff the walk
+// enters it where the previous block's walk leaves it) and walks itself where
+// it does not hold.  Per block: the walk's anchors in the block (spec), its
+// first anchor at or after the block's start (entry) and after its end
+// (exit); kNone if the walk stopped inside a segment before reaching it, the
+// chunk's length if the chunk ends first.  Also checks sortedness.
 template <typename KT>
 __global__ void __launch_bounds__(kSpecThreads)
 spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
-            uint32_t* __restrict__ spec_g, uint32_t* __restrict__ fix_g, uint32_t* __restrict__ exitS_g,
-            uint32_t* __restrict__ exitF_g, uint8_t* __restrict__ sync_g, uint32_t* __restrict__ status) {
+            uint32_t* __restrict__ spec_g, uint32_t* __restrict__ entry_g, uint32_t* __restrict__ exit_g,
+            uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ uint32_t s_spec[kSpecThreads + 1], s_exitS[kSpecThreads + 1];
     const WinDesc wd = wins[blockIdx.x];
     const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
     const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
     const int64_t eps = cd.eps;
     const uint32_t tid = threadIdx.x;
-    const uint32_t base = w0 >= kFB ? w0 - kFB : 0;
+    const uint32_t base = w0 >= kWarm ? w0 - kWarm : 0;
     const uint32_t top = min(n, w1 + kFCap);
     KT* s = (KT*)smem;
-    for (uint32_t q = tid; q < top - base; q += kSpecThreads) s[q + (q >> 5)] = __ldg(K + base + q);
+    for (uint32_t q = tid; q < top - base; q += kSpecThreads) s[q + (q >> 6)] = __ldg(K + base + q);
     __syncthreads();
-    const Staged<KT> st{s, base};
+    const Staged64<KT> st{s, base};
     bool unsorted = false;
     for (uint32_t i = max(w0, 1u) + tid; i < w1; i += kSpecThreads) unsorted |= st(i - 1) > st(i);
     if (w0 == 0 && cd.check_prev && tid == 0) unsorted |= __ldg(K - 1) > __ldg(K);
     if (unsorted) atomicOr(status, kStUnsorted);
 
-    const uint32_t kfirst = w0 / kFB - (w0 > 0 ? 1u : 0u);
-    const uint32_t nb = (w1 + kFB - 1) / kFB - kfirst;
-    // (S): one flat loop per block; a key that empties the cone starts the next
-    // segment inside the block, or ends the walk past the block's end
-    for (uint32_t lb = tid; lb < nb; lb += kSpecThreads) {
-        const uint32_t b = (kfirst + lb) * kFB, e = min(b + kFB, n), lim = min(n, e + kFCap);
-        uint32_t mask = 1u, x = b, ex = lim >= n ? n : kNone;
-        uint64_t kx = st(b);
-        Frac cone = frac_open();
-        for (uint32_t i = b + 1; i < lim; ++i) {
-            const uint64_t Ki = st(i);
-            if (frac_step(Ki - kx, i - x, eps, cone)) continue;
-            if (i >= e) {
-                ex = i;
-                break;
-            }
-            mask |= 1u << (i - b);
-            x = i;
-            kx = Ki;
-            cone = frac_open();
-        }
-        s_spec[lb] = mask;
-        s_exitS[lb] = ex;
+    const uint32_t s0 = w0 + tid * kSpan;  // this thread's span [s0, s0 + 64) (may start past w1)
+    const bool active = s0 < w1;
+    const uint32_t p = s0 >= base + kWarm ? s0 - kWarm : base;
+    const uint32_t lim = active ? min(n, s0 + kSpan + kFCap) : p + 1;
+    // the walk may use 32-bit numerators when its whole key range allows it (warp-uniform choice)
+    const uint64_t span_keys = active ? st(lim - 1) - st(p) : 0;
+    const bool narrow = __all_sync(0xFFFFFFFFu, span_keys + (uint64_t)eps + 1 < (1ull << 31));
+    uint32_t bits[3] = {0u, 0u, 0u};
+    if (active) {
+        if (narrow) spec_walk<true>(st, p, lim, s0, eps, bits);
+        else spec_walk<false>(st, p, lim, s0, eps, bits);
     }
-    __syncthreads();
-    // (F): from the entry block k-1 predicts, until a speculative anchor
-    for (uint32_t lb = (w0 > 0 ? 1u : 0u) + tid; lb < nb; lb += kSpecThreads) {
-        const uint32_t k = kfirst + lb;
-        const uint32_t b = k * kFB, e = min(b + kFB, n), lim = min(n, e + kFCap);
-        const uint32_t x0 = k == 0 ? 0u : s_exitS[lb - 1];
-        uint32_t fm = 0, sync = 0xFF, exf;
-        if (x0 == kNone) {
-            exf = kInvalid;
-        } else if (x0 >= e) {
-            exf = x0;  // the entering segment covers the whole block
-        } else {
-            const uint32_t sm = s_spec[lb];
-            exf = lim >= n ? n : kNone;
-            if ((sm >> (x0 - b)) & 1u) {
-                sync = x0 - b;
-            } else {
-                fm = 1u << (x0 - b);
-                uint32_t x = x0;
-                uint64_t kx = st(x0);
-                Frac cone = frac_open();
-                for (uint32_t i = x0 + 1; i < lim; ++i) {
-                    const uint64_t Ki = st(i);
-                    if (frac_step(Ki - kx, i - x, eps, cone)) continue;
-                    if (i >= e) {
-                        exf = i;
-                        break;
-                    }
-                    if ((sm >> (i - b)) & 1u) {
-                        sync = i - b;
-                        break;
-                    }
-                    fm |= 1u << (i - b);
-                    x = i;
-                    kx = Ki;
-                    cone = frac_open();
-                }
-            }
-            if (sync != 0xFF) exf = s_exitS[lb];
-        }
-        const uint64_t g = cd.bitword_begin + k;
-        spec_g[g] = s_spec[lb];
-        exitS_g[g] = s_exitS[lb];
-        fix_g[g] = fm;
-        sync_g[g] = (uint8_t)sync;
-        exitF_g[g] = exf;
+    if (!active) return;
+    // the walk's next anchor after lim is unknown unless the chunk ends there
+    const uint32_t tail = lim >= n ? n : kNone;
+#pragma unroll
+    for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t b = s0 + h * kFB;
+        if (b >= w1) break;
+        const uint32_t e = min(b + kFB, n);
+        const uint32_t fe = first_bit_from(bits, h * kFB), fx = first_bit_from(bits, e - s0);
+        const uint64_t g = cd.bitword_begin + b / kFB;
+        spec_g[g] = bits[h] & (e - b < 32 ? (1u << (e - b)) - 1u : 0xFFFFFFFFu);
+        entry_g[g] = fe != kNone ? s0 + fe : tail;
+        exit_g[g] = fx != kNone ? s0 + fx : tail;
     }
 }
 
-// ------------------------------------------------------------------ fit: the true chain (R)
+// ------------------------------------------------------------------ fit: the true chain
 
-// One warp per chunk follows the true anchors block by block.  Where the true
-// path enters block k exactly at exitS[k-1], (F) already holds the answer for
-// block k, and block k+1's assumption holds too iff exitF[k] == exitS[k]; so a
-// ballot over 32 blocks takes the whole run of consistent blocks at once.
-// Elsewhere the warp walks the cone itself (32 keys per step) until it meets a
-// speculative anchor.  Output: the chunk's anchor bitmap and segment count.
-// Every segment longer than kShortMax keys is found by such a walk (the
-// speculative walks stop kFCap keys past their block), and the walk ends with
-// the segment's cone: its slope and end are recorded at the anchor's block
-// (at most one such segment starts in a block).
+// One warp per chunk follows the true anchors block by block.  At an exact
+// anchor x of block k that the speculative walk of block k also passes
+// through, the walk is exact from x on; the blocks after it stay exact as long
+// as each one's walk enters where the previous one's leaves (a ballot over 32
+// blocks takes the whole run at once).  Elsewhere the warp walks one segment
+// itself (32 keys per step, or 256 while the cone does not move) and looks
+// again.  Output: the chunk's anchor bitmap and segment count.  Every segment
+// longer than kShortMax keys is found by such a walk (the speculative walks
+// stop kFCap keys past their span), and the walk ends with the segment's
+// cone: its slope and end are recorded at the anchor's block (at most one such
+// segment starts in a block).
 template <typename KT>
-__global__ void __launch_bounds__(kChainThreads, 1)
+__global__ void __launch_bounds__(kChainThreads, 6)
 chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, uint64_t C,
-             const uint32_t* __restrict__ spec_g, const uint32_t* __restrict__ fix_g,
-             const uint32_t* __restrict__ exitS_g, const uint32_t* __restrict__ exitF_g,
-             const uint8_t* __restrict__ sync_g, uint32_t* __restrict__ tbits, uint32_t* __restrict__ counts,
+             const uint32_t* __restrict__ spec_g, const uint32_t* __restrict__ entry_g,
+             const uint32_t* __restrict__ exit_g, uint32_t* __restrict__ tbits, uint32_t* __restrict__ counts,
              LongInfo* __restrict__ longinfo) {
     const uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     if (c >= C) return;  // whole warps leave together
@@ -337,49 +399,51 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
         if (e - a > kShortMax && lane == 0) longinfo[gb + (a >> 5)] = LongInfo{frac_slope(f, magic), e, 0u};
         return e;
     };
-    uint32_t x = 0, knext = 0, total = 0;
+    uint32_t x = 0, knext = 0, total = 0, pm = 0;  // pm: anchors of block knext found so far
     while (x < n) {
-        const uint32_t k = x / kFB;
+        const uint32_t k = x / kFB, b = k * kFB;
+        if (k != knext) pm = 0;
         for (uint32_t q = knext + lane; q < k; q += 32) T[q] = 0;
-        const bool entry_ok = k == 0 ? x == 0 : x == __ldg(exitS_g + gb + k - 1);
-        if (entry_ok) {
+        knext = k;
+        const uint32_t m0 = __ldg(spec_g + gb + k);
+        if ((m0 >> (x - b)) & 1u) {
+            // x is on block k's walk: exact from x on; extend over consistent blocks
             const uint32_t kb = k + lane;
             const bool valid = kb < nblk;
-            uint32_t eS = kNone, eF = kInvalid, m = 0;
+            uint32_t m = 0, ex = kNone, ent = kNone;
             if (valid) {
-                eS = __ldg(exitS_g + gb + kb);
-                eF = __ldg(exitF_g + gb + kb);
-                const uint32_t so = __ldg(sync_g + gb + kb);
-                m = __ldg(fix_g + gb + kb) | (so != 0xFF ? __ldg(spec_g + gb + kb) & (0xFFFFFFFFu << so) : 0u);
+                m = __ldg(spec_g + gb + kb);
+                ex = __ldg(exit_g + gb + kb);
+                ent = __ldg(entry_g + gb + kb);
             }
-            const uint32_t okm = __ballot_sync(0xFFFFFFFFu, valid && eF == eS && eF != kNone);
-            const uint32_t nvalid = __popc(__ballot_sync(0xFFFFFFFFu, valid));
-            uint32_t r = ~okm ? (uint32_t)__ffs(~okm) : 32u;  // lanes 0..r-1 follow one another
-            r = min(r, nvalid);
+            if (lane == 0) m = pm | (m & (0xFFFFFFFFu << (x - b)));
+            const uint32_t exp = __shfl_up_sync(0xFFFFFFFFu, ex, 1);
+            const bool cons = valid && (lane == 0 || (ent == exp && exp != kNone));
+            const uint32_t okm = __ballot_sync(0xFFFFFFFFu, cons);
+            const uint32_t r = ~okm ? (uint32_t)__ffs(~okm) - 1u : 32u;  // lanes 0..r-1 follow one another (r >= 1)
             if (lane < r) T[kb] = m;
             total += __reduce_add_sync(0xFFFFFFFFu, lane < r ? (uint32_t)__popc(m) : 0u);
-            uint32_t xl = __shfl_sync(0xFFFFFFFFu, eF, r - 1);
-            const uint32_t ml = __shfl_sync(0xFFFFFFFFu, m, r - 1);
-            if (xl == kNone) xl = walk((k + r - 1) * kFB + 31u - (uint32_t)__clz(ml));
+            uint32_t xl = __shfl_sync(0xFFFFFFFFu, ex, r - 1);
+            if (xl == kNone) {
+                // the last walk stopped inside a segment: walk it from its anchor
+                const uint32_t nz = __ballot_sync(0xFFFFFFFFu, lane < r && m != 0u);  // lane 0 holds x: nz != 0
+                const uint32_t h = 31u - (uint32_t)__clz(nz);
+                const uint32_t mh = __shfl_sync(0xFFFFFFFFu, m, h);
+                xl = walk((k + h) * kFB + 31u - (uint32_t)__clz(mh));
+            }
             knext = k + r;
+            pm = 0;
             x = xl;
         } else {
-            const uint32_t b = k * kFB, e = min(b + kFB, n);
-            const uint32_t sm = __ldg(spec_g + gb + k);
-            uint32_t m = 0, xn = x;
-            while (xn < e) {
-                if ((sm >> (xn - b)) & 1u) {
-                    m |= sm & (0xFFFFFFFFu << (xn - b));
-                    xn = __ldg(exitS_g + gb + k);
-                    if (xn == kNone) xn = walk(b + 31u - (uint32_t)__clz(m));
-                    break;
-                }
-                m |= 1u << (xn - b);
-                xn = walk(xn);
+            // walk one segment from x and look again
+            pm |= 1u << (x - b);
+            const uint32_t xn = walk(x);
+            if (xn >= b + kFB || xn >= n) {
+                if (lane == 0) T[k] = pm;
+                total += __popc(pm);
+                knext = k + 1;
+                pm = 0;
             }
-            if (lane == 0) T[k] = m;
-            total += __popc(m);
-            knext = k + 1;
             x = xn;
         }
     }
@@ -447,7 +511,7 @@ struct MaxOp {
 // slope its chain walk recorded; its widths pass is queued as pieces of
 // kPiece keys (long_width_kernel) and its entry is finished by bitoff_kernel.
 template <typename KT>
-__global__ void __launch_bounds__(kSpecThreads)
+__global__ void __launch_bounds__(kShortThreads)
 fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
                  const uint32_t* __restrict__ tbits, const uint64_t* __restrict__ csb,
                  const LongInfo* __restrict__ longinfo, KT* __restrict__ icpt, int64_t* __restrict__ slope,
@@ -469,20 +533,20 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     const uint32_t tid = threadIdx.x;
     const uint32_t top = min(n, w1 + kShortMax);
     KT* s = (KT*)smem;
-    for (uint32_t q = tid; q < top - w0; q += kSpecThreads) s[q + (q >> 5)] = __ldg(K + w0 + q);
+    for (uint32_t q = tid; q < top - w0; q += kShortThreads) s[q + (q >> 5)] = __ldg(K + w0 + q);
     const uint32_t* __restrict__ T = tbits + cd.bitword_begin;
     const uint32_t k0 = w0 / kFB, nT = (top - w0 + kFB - 1) / kFB;
-    for (uint32_t q = tid; q < kWords + 4; q += kSpecThreads) s_T[q] = q < nT ? T[k0 + q] : 0u;
+    for (uint32_t q = tid; q < kWords + 4; q += kShortThreads) s_T[q] = q < nT ? T[k0 + q] : 0u;
     // anchors of the chunk before this window
     uint32_t before = 0;
-    for (uint32_t q = tid; q < k0; q += kSpecThreads) before += __popc(T[q]);
+    for (uint32_t q = tid; q < k0; q += kShortThreads) before += __popc(T[q]);
     before = __reduce_add_sync(0xFFFFFFFFu, before);
     if ((tid & 31u) == 0) s_warp[tid >> 5] = before;
     if (tid == 0) s_nlong = 0;
     __syncthreads();
     if (tid == 0) {
         uint32_t t = 0;
-        for (int w = 0; w < kSpecThreads / 32; ++w) t += s_warp[w];
+        for (int w = 0; w < kShortThreads / 32; ++w) t += s_warp[w];
         s_base = t;
     }
     __syncthreads();
@@ -494,14 +558,22 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     const uint64_t* __restrict__ magic = g_magic;
     for (uint32_t rest = word; rest; rest &= rest - 1, ++j) {
         const uint32_t a = w0 + tid * kFB + (uint32_t)(__ffs(rest) - 1);
-        // next anchor among the kShortMax keys after a (bit t: key a + 1 + t)
+        // next anchor among the kShortMax = 96 keys after a (bit t: key a + 1 + t)
         const uint32_t q = a + 1 - w0, qi = q >> 5, sh = q & 31u;
         const uint64_t lo64 = ((uint64_t)s_T[qi + 1] << 32) | s_T[qi];
-        uint64_t nxt = sh ? (lo64 >> sh) | ((uint64_t)s_T[qi + 2] << (64u - sh)) : lo64;
+        const uint64_t hi64 = ((uint64_t)s_T[qi + 3] << 32) | s_T[qi + 2];
+        uint64_t nlo = sh ? (lo64 >> sh) | (hi64 << (64u - sh)) : lo64;  // t = 0..63
+        uint32_t nhi = (uint32_t)(hi64 >> sh);                            // t = 64..95
         const uint32_t left = n - a - 1;  // keys after a in the chunk
-        if (left < 64) nxt &= (1ull << left) - 1;
+        if (left < 64) {
+            nlo &= (1ull << left) - 1;
+            nhi = 0;
+        } else if (left < 96) {
+            nhi &= (1u << (left - 64)) - 1u;
+        }
         uint32_t b;
-        if (nxt) b = a + 1 + (uint32_t)(__ffsll((long long)nxt) - 1);
+        if (nlo) b = a + 1 + (uint32_t)(__ffsll((long long)nlo) - 1);
+        else if (nhi) b = a + 65 + (uint32_t)(__ffs(nhi) - 1);
         else if (left < kShortMax) b = n;
         else b = kNone;
         const uint64_t ka = st(a);
@@ -566,7 +638,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
         s_nlong = fits ? nl : 0u;
     }
     __syncthreads();
-    for (uint32_t q = tid; q < s_nlong; q += kSpecThreads) {
+    for (uint32_t q = tid; q < s_nlong; q += kShortThreads) {
         const WinLong e = s_long[q];
         const uint32_t it = s_item0 + q;
         items[it] = LongItem{cd.key_begin + e.a, e.M, e.len, 0u, 0ull};
@@ -844,8 +916,7 @@ static int device_sms() {
 struct FitScratch {
     const WinDesc* wins;
     uint64_t nwins;
-    uint32_t *spec, *fix, *exitS, *exitF;
-    uint8_t* sync;
+    uint32_t *spec, *entry, *exit;
     LongInfo* longinfo;
     LongItem* items;
     Piece* pieces;
@@ -863,7 +934,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
     const Layout& lay = col->lay;
     if (stage == 0) {
         static bool attr[2] = {false, false};
-        const size_t smem = sizeof(KT) * kStageSlots;
+        const size_t smem = sizeof(KT) * kSpecSlots;
         if (!attr[sizeof(KT) == 8]) {
             int rc = cuda_status(
                 cudaFuncSetAttribute(spec_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -872,13 +943,13 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         }
         {
             KTime kt("fit_spec", st);
-            spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.fix,
-                                                                            fs.exitS, fs.exitF, fs.sync, status);
+            spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.entry,
+                                                                            fs.exit, status);
         }
         {
             KTime kt("fit_chain", st);
             chain_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0, st>>>(
-                keys, chunks_d, C, fs.spec, fs.fix, fs.exitS, fs.exitF, fs.sync, tbits, counts, fs.longinfo);
+                keys, chunks_d, C, fs.spec, fs.entry, fs.exit, tbits, counts, fs.longinfo);
         }
         note_launch(2);
         int rc = cuda_status(cudaGetLastError());
@@ -895,7 +966,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
             attr[sizeof(KT) == 8] = true;
         }
         KTime kt("model_short", st);
-        fit_short_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(
+        fit_short_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, smem, st>>>(
             keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
             (int64_t*)(blob + lay.slope), (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start),
             (uint8_t*)(blob + lay.width), fs.items, fs.counters, fs.items_cap, fs.pieces, fs.counters + 1,
@@ -944,8 +1015,7 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     const size_t off_chunks = 0;
     const size_t off_wins = al(off_chunks + C * sizeof(ChunkDesc));
     const size_t off_blk = al(off_wins + nwins * sizeof(WinDesc));
-    const size_t off_sync = al(off_blk + 4 * 4 * bitwords);
-    const size_t off_bits = al(off_sync + bitwords);
+    const size_t off_bits = al(off_blk + 3 * 4 * bitwords);
     const size_t off_counts = al(off_bits + bitwords * 4);
     const size_t off_tmp = al(off_counts + (C + 1) * 4);
     const size_t off_status = al(off_tmp + tmp_bytes);
@@ -967,10 +1037,8 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     fs.wins = (const WinDesc*)(scratch + off_wins);
     fs.nwins = nwins;
     fs.spec = (uint32_t*)(scratch + off_blk);
-    fs.fix = fs.spec + bitwords;
-    fs.exitS = fs.fix + bitwords;
-    fs.exitF = fs.exitS + bitwords;
-    fs.sync = scratch + off_sync;
+    fs.entry = fs.spec + bitwords;
+    fs.exit = fs.entry + bitwords;
     uint32_t* tbits = (uint32_t*)(scratch + off_bits);
     uint32_t* counts = (uint32_t*)(scratch + off_counts);
     void* tmp = scratch + off_tmp;
