@@ -55,8 +55,11 @@ def parse_args():
     ap.add_argument("--queries", type=int, default=100_000_000)
     ap.add_argument("--windows", type=int, default=16384)
     ap.add_argument("--window-len", type=int, default=4096)
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
-                    help="2: large single column (default); 3: batched posting lists; 4: serving")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
+                    help="2: large single column (default); 3: batched posting lists; 4: serving; "
+                         "5: scale sweep over eps beside the FOR-delta bp128 baseline")
+    ap.add_argument("--sweep-n", type=int, default=1_000_000_000)
+    ap.add_argument("--sweep-eps", default="0,1,3,15,63,255,1023")
     ap.add_argument("--lists", type=int, default=1_000_000)
     ap.add_argument("--total", type=int, default=2_000_000_000)
     ap.add_argument("--per-list-sample", type=int, default=2000)
@@ -228,6 +231,9 @@ def main():
         return
     if args.config == 4:
         run_serve(args)
+        return
+    if args.config == 5:
+        run_sweep(args)
         return
     world, rank, local = dist_env()
     import torch
@@ -522,6 +528,98 @@ def run_batch(args):
             "batched_over_per_list": value / (skeys / tp),
             "ratio": size / (4 * N), "bits_per_id": 8 * size / N, "segments": segs,
             "tuning": table, "gen_s": t_gen, "tune_s": t_tune, "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
+def run_sweep(args):
+    """Scale sweep: N = 1e9 sorted uint64 keys from the lognormal-gap generator
+    (mu 3, sigma 2) and the piecewise-linear generator, drawn on the device;
+    for every eps, compress and full-decode throughput and the compression
+    ratio, beside the FOR-delta bp128 baseline (block 128) on the same keys.
+    Each measurement is the mean of --steps timed repetitions after --warmup
+    untimed ones (CUDA events on the launching stream; 8 GB inputs, larger
+    than L2)."""
+    import torch
+
+    from paper_2412_10770_gb300 import build as lcbuild
+    from paper_2412_10770_gb300 import inputs, lc
+
+    lcbuild.build()
+    lc.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    N = args.sweep_n
+    eps_list = [int(e) for e in args.sweep_eps.split(",")]
+    peak, kind = measured_peaks()
+    gens = {"lognormal": dict(mu=3.0, sigma=2.0), "piecewise": {}}
+    out = torch.empty(N, dtype=torch.uint64, device="cuda")
+    rows = []
+    tot_keys = 0
+    tot_ms = 0.0
+    launches0 = lc.lc_launch_count()
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    sampler.start()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    for gi, (g, kw) in enumerate(gens.items()):
+        keys = inputs.column_device(g, N, seed=inputs.seed_for(5, 1 + gi), **kw)
+        torch.cuda.synchronize()
+        codecs = [("for_bp128", None)] + [("lc", e) for e in eps_list]
+        for name, eps in codecs:
+            cms = dms = 0.0
+            size = segs = None
+            for it in range(args.warmup + args.steps):
+                if name == "lc":
+                    col, c_ms = timed(lambda: lc.lc_compress(keys, eps=eps, chunk_log2=16, stream=stream))
+                    _, d_ms = timed(lambda: lc.lc_decode(col, 0, N, out, stream=stream))
+                    size, segs = lc.lc_size(col), col.info["segments"]
+                else:
+                    col, c_ms = timed(lambda: lc.lc_for_compress(keys, stream=stream))
+                    _, d_ms = timed(lambda: lc.lc_for_decode(col, out, stream=stream))
+                    size = lc.lc_for_size(col)
+                if it == 0:
+                    assert torch.equal(out, keys), f"{name} eps={eps}: decode differs from the keys"
+                col.free()
+                if it >= args.warmup:
+                    cms += c_ms
+                    dms += d_ms
+            cms /= args.steps
+            dms /= args.steps
+            tot_keys += 2 * N
+            tot_ms += cms + dms
+            alg = 8 * N + size
+            rows.append({"generator": g, "codec": name, "eps": eps, "ratio": size / (8 * N),
+                         "bits_per_key": 8 * size / N, "segments": segs,
+                         "compress_ms": cms, "compress_keys_per_s": N / (cms / 1e3),
+                         "compress_alg_gbs": alg / (cms / 1e3) / 1e9,
+                         "compress_hbm_frac": alg / (cms / 1e3) / 1e9 / peak,
+                         "decode_ms": dms, "decode_keys_per_s": N / (dms / 1e3),
+                         "decode_alg_gbs": alg / (dms / 1e3) / 1e9, "decode_hbm_frac": alg / (dms / 1e3) / 1e9 / peak})
+        del keys
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    lcrows = [r for r in rows if r["codec"] == "lc"]
+    best = max(lcrows, key=lambda r: r["decode_hbm_frac"])
+    line = {"metric": METRIC, "value": tot_keys / (tot_ms / 1e3), "unit": "keys/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"scale sweep: N={N} sorted uint64 keys from the lognormal-gap (mu 3, sigma 2) "
+                                   f"and piecewise-linear generators, eps in {eps_list}, compress + full decode "
+                                   "per eps, beside FOR-delta bit-packing (block 128) on the same keys",
+                       "n_keys": N, "eps": eps_list, "generators": list(gens), "l2": "inputs (8 GB) larger than L2"},
+            "sweep": rows,
+            "roofline": {"bound": "hbm", "kernel": f"decode (lc, {best['generator']}, eps={best['eps']})",
+                         "achieved": best["decode_alg_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": best["decode_hbm_frac"], "peak_source": f"{kind} copy bandwidth (MEASURED_PEAKS.json)",
+                         "traffic": None},
+            "clocks": clocks, "gpu_launches": lc.lc_launch_count() - launches0}
     print(json.dumps(line), flush=True)
 
 

@@ -245,6 +245,31 @@ int lc_server_destroy(lc_server* server);
  * out, wait) on `stream`. */
 int lc_serve_sync(lc_column* const* cols, int ncols, const lc_request* req, void* stream, lc_completion* out);
 
+/* ------------------------------------------------------------ baseline codec */
+
+/* Frame-of-reference delta bit-packing in blocks of 128 keys ("FOR1"), the
+ * conventional codec the learned compressor is compared against in the scale
+ * sweep (the paper compares against such codecs in Sec. II-C, Fig. 3a).  Not
+ * part of the learned method.  Block b stores its first key, the bit length
+ * w_b of its largest gap, and its 128 gaps K[128b+i] - K[128b+i-1] (gap 0 is 0,
+ * gaps past N are 0) at w_b bits each, LSB-first in 4 w_b 32-bit words; block b
+ * starts at word 4 (w_0 + ... + w_{b-1}).  Layout: a 32-byte header ("FOR1",
+ * key_bytes u32, N u64, B u64 blocks, W u64 payload words), block_base
+ * (key_bytes x B), block_width (u8 x B), payload (u32 x W), each array 16-byte
+ * aligned with zero padding.
+ *   lc_for_compress: keys_dev as in lc_compress (device, non-decreasing, not
+ *     modified); synchronous; LC_ERR_UNSORTED if a key is below its
+ *     predecessor.  *out owns its device memory (lc_for_free).
+ *   lc_for_decode: all N keys into out_dev (device, N x key_bytes);
+ *     asynchronous on `stream`.
+ *   lc_for_size / lc_for_serialize: the exact FOR1 bytes (synchronous). */
+typedef struct lc_for lc_for;
+int lc_for_compress(const void* keys_dev, uint64_t n, int key_bytes, void* stream, lc_for** out);
+int lc_for_decode(const lc_for* f, void* out_dev, void* stream);
+int lc_for_size(const lc_for* f, uint64_t* bytes);
+int lc_for_serialize(const lc_for* f, void* host, uint64_t cap, uint64_t* len);
+void lc_for_free(lc_for* f);
+
 /* ------------------------------------------------------------ size, bytes, status */
 
 /* r = size(K^c) / size(K) with size(K) = N * key_bytes (Def. 1).  Returns a

@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lc_oracle.c")
+_SRC_FOR = os.path.join(_HERE, "for_bp128.c")
 _HDR = os.path.join(_HERE, "lc_oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liblcoracle.so")
 
@@ -43,11 +44,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11 + __int128, no intrinsics)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     stale = (not os.path.exists(_LIB)) or max(
-        os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
+        os.path.getmtime(_SRC), os.path.getmtime(_SRC_FOR), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall",
-                               "-Wextra", "-o", tmp, _SRC])
+                               "-Wextra", "-o", tmp, _SRC, _SRC_FOR])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +69,10 @@ def bind(path: str) -> ctypes.CDLL:
     lib.lco_access.argtypes = [p, u64, p, u64, p]
     lib.lco_lower_bound.argtypes = [p, u64, p, u64, p]
     lib.lco_free.argtypes = [p]
+    lib.lco_for_compress.argtypes = [p, u64, ctypes.c_int, pp, pu64]
+    lib.lco_for_decode.argtypes = [p, u64, p]
+    lib.lco_for_compress.restype = ctypes.c_int
+    lib.lco_for_decode.restype = ctypes.c_int
     for f in ("lco_compress", "lco_compress_lists", "lco_info", "lco_decode",
               "lco_access", "lco_lower_bound"):
         getattr(lib, f).restype = ctypes.c_int
@@ -159,4 +164,24 @@ def lower_bound(blob: bytes, values) -> np.ndarray:
     v = np.ascontiguousarray(values, dtype=_dtype(inf["key_bytes"]))
     out = np.empty(v.size, dtype=np.uint64)
     _check(_L().lco_lower_bound(blob, len(blob), v.ctypes.data, v.size, out.ctypes.data))
+    return out
+
+
+def for_compress(keys) -> bytes:
+    """The FOR1 blob of the frame-of-reference delta bit-packing baseline
+    (blocks of 128 keys; see for_bp128.c)."""
+    a = _keys_array(keys)
+    blob, n = ctypes.c_void_p(), ctypes.c_uint64()
+    _check(_L().lco_for_compress(a.ctypes.data, a.size, a.itemsize, ctypes.byref(blob), ctypes.byref(n)))
+    return _take_blob(blob, n.value)
+
+
+def for_decode(blob: bytes) -> np.ndarray:
+    """Every key of a FOR1 blob."""
+    if len(blob) < 32:
+        raise OracleError(-5)
+    kb = int.from_bytes(blob[4:8], "little")
+    n = int.from_bytes(blob[8:16], "little")
+    out = np.empty(n, dtype=_dtype(kb) if kb in (4, 8) else np.uint64)
+    _check(_L().lco_for_decode(blob, len(blob), out.ctypes.data))
     return out

@@ -104,6 +104,13 @@ int lco_lower_bound(const uint8_t* blob, uint64_t len, const void* v, uint64_t m
 
 void lco_free(void* p);
 
+/* The frame-of-reference delta bit-packing baseline ("FOR1", blocks of 128
+ * keys), defined in for_bp128.c: not the paper's method, the conventional
+ * codec the scale sweep compares against.  Compress writes a malloc'ed blob
+ * (lco_free); decode writes N keys. */
+int lco_for_compress(const void* keys, uint64_t n, int key_bytes, uint8_t** blob, uint64_t* len);
+int lco_for_decode(const uint8_t* blob, uint64_t len, void* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -212,17 +212,28 @@ def posting_lists_device(n_lists: int, total: int, universe: int, seed: int, alp
     return out.view(torch.uint32), begin
 
 
-def column_device(kind: str, n: int, seed: int, device: str = "cuda"):
+def column_device(kind: str, n: int, seed: int, device: str = "cuda", mu: float = 2.0, sigma: float = 1.5,
+                  block: int = 1 << 27):
     """The generators of ``column`` drawn on the GPU (same recipes, torch RNG),
-    for workloads with many large columns.  Returns a uint64 tensor."""
+    for workloads with many large columns.  ``mu`` and ``sigma`` parametrise the
+    lognormal gaps (drawn ``block`` at a time).  Returns a uint64 tensor."""
     import torch
 
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     if kind == "lognormal":
-        z = torch.randn(n, generator=g, device=device, dtype=torch.float64)
-        gaps = torch.floor(torch.exp(2.0 + 1.5 * z)).to(torch.int64) + 1
-        return torch.cumsum(gaps, 0).view(torch.uint64)
+        out = torch.empty(n, dtype=torch.int64, device=device)
+        acc = 0
+        for b in range(0, n, block):
+            m = min(block, n - b)
+            z = torch.randn(m, generator=g, device=device, dtype=torch.float64)
+            gaps = torch.floor(torch.exp(mu + sigma * z)).to(torch.int64) + 1
+            del z
+            torch.cumsum(gaps, 0, out=out[b:b + m])
+            out[b:b + m] += acc
+            acc = int(out[b + m - 1])
+            del gaps
+        return out.view(torch.uint64)
     if kind == "piecewise":
         regimes = max(1, min(1000, n))
         edges = (torch.arange(regimes + 1, device=device, dtype=torch.int64) * n) // regimes

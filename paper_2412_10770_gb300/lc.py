@@ -34,7 +34,8 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
            "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free", "lc_server_create", "lc_server_submit",
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
-           "lc_timing_enable", "lc_timing_read")
+           "lc_timing_enable", "lc_timing_read",
+           "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -133,6 +134,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_serve_sync": ([p, ctypes.c_int, ctypes.POINTER(_Request), p, ctypes.POINTER(_Completion)], i32),
         "lc_timing_enable": ([ctypes.c_int], i32),
         "lc_timing_read": ([ctypes.POINTER(_KernelTime), ctypes.c_int, ctypes.POINTER(ctypes.c_int)], i32),
+        "lc_for_compress": ([p, u64, i32, p, pp], i32),
+        "lc_for_decode": ([p, p, p], i32),
+        "lc_for_size": ([p, pu64], i32),
+        "lc_for_serialize": ([p, p, u64, pu64], i32),
+        "lc_for_free": ([p], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -526,3 +532,64 @@ def lc_timing_read() -> dict:
     got = ctypes.c_int()
     _check(load().lc_timing_read(buf, 64, ctypes.byref(got)), "lc_timing_read")
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(got.value)}
+
+
+# ---------------------------------------------------------------- baseline codec (FOR-delta, block 128)
+
+
+class ForColumn:
+    """An lc_for handle: the frame-of-reference delta bit-packing baseline."""
+
+    def __init__(self, handle: int, n: int, key_bytes: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.n = n
+        self.key_bytes = key_bytes
+
+    def free(self) -> None:
+        if self.handle and self.handle.value and _lib is not None:
+            _lib.lc_for_free(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def lc_for_compress(keys: torch.Tensor, stream=None) -> ForColumn:
+    lib = load()
+    _dev(keys, "keys")
+    kb = _key_bytes(keys)
+    h = ctypes.c_void_p()
+    _check(lib.lc_for_compress(keys.data_ptr(), keys.numel(), kb, _stream(stream), ctypes.byref(h)),
+           "lc_for_compress")
+    return ForColumn(h.value, keys.numel(), kb)
+
+
+def lc_for_decode(f: ForColumn, out=None, stream=None) -> torch.Tensor:
+    lib = load()
+    if out is None:
+        out = torch.empty(f.n, dtype=key_dtype(f.key_bytes), device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_for_decode(f.handle, out.data_ptr(), _stream(stream)), "lc_for_decode")
+    return out
+
+
+def lc_for_size(f: ForColumn) -> int:
+    n = ctypes.c_uint64()
+    _check(load().lc_for_size(f.handle, ctypes.byref(n)), "lc_for_size")
+    return n.value
+
+
+def lc_for_serialize(f: ForColumn) -> bytes:
+    lib = load()
+    n = ctypes.c_uint64()
+    lib.lc_for_serialize(f.handle, None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib.lc_for_serialize(f.handle, buf, n.value, ctypes.byref(n)), "lc_for_serialize")
+    return buf.raw[: n.value]
+
+
+def lc_for_free(f: ForColumn) -> None:
+    f.free()

@@ -20,6 +20,7 @@ from paper_2412_10770_gb300 import inputs
 from test_oracle_pins import _tiny_cases, check_greedy, check_invariants
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lc_oracle.c")
+SRC_FOR = os.path.join(os.path.dirname(oracle.__file__), "for_bp128.c")
 HDR = os.path.join(os.path.dirname(oracle.__file__), "lc_oracle.h")
 
 MUTANTS = {
@@ -35,6 +36,15 @@ MUTANTS = {
     "chunks_do_not_restart": ("ch[c].key_end = (c + 1) * cs < n ? (c + 1) * cs : n;",
                               "ch[c].key_end = n;"),
 }
+# mistakes planted in the FOR-delta bp128 baseline's reference (for_bp128.c)
+FOR_MUTANTS = {
+    "for_first_gap_not_zero": ("if (i == 0 || k >= n) return 0;", "if (k == 0 || k >= n) return 0;"),
+    "for_width_one_bit_short": ("width[b] = fo_bitlen(m);", "width[b] = fo_bitlen(m >> 1);"),
+    "for_gap_bit_position_shifted": ("const uint64_t bit = (uint64_t)i * w + t; /* bit of the block payload */",
+                                     "const uint64_t bit = (uint64_t)i * w + t + 1; /* bit of the block payload */"),
+    "for_block_words_not_4w": ("word += 4 * (uint64_t)w;\n    }\n    free(width);",
+                               "word += 3 * (uint64_t)w;\n    }\n    free(width);"),
+}
 
 
 def _pin_suite():
@@ -49,24 +59,44 @@ def _pin_suite():
         check_invariants(keys, eps, blob)
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_planted_mistake_is_caught(name, tmp_path):
-    old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
-    (tmp_path / "lc_oracle.c").write_text(src.replace(old, new))
+def _for_pin_suite():
+    from test_for_pins import _cases, test_reference_roundtrips_and_matches_closed_form
+
+    for name, keys in _cases():
+        test_reference_roundtrips_and_matches_closed_form(name, keys)
+
+
+def _mutant_lib(tmp_path, lc_src: str, for_src: str) -> str:
+    (tmp_path / "lc_oracle.c").write_text(lc_src)
+    (tmp_path / "for_bp128.c").write_text(for_src)
     shutil.copy(HDR, tmp_path / "lc_oracle.h")
     lib = str(tmp_path / "libmutant.so")
     subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-fPIC", "-shared", "-o", lib,
-                           str(tmp_path / "lc_oracle.c")])
+                           str(tmp_path / "lc_oracle.c"), str(tmp_path / "for_bp128.c")])
+    return lib
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(FOR_MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    lc_src, for_src = open(SRC).read(), open(SRC_FOR).read()
+    if name in MUTANTS:
+        old, new = MUTANTS[name]
+        assert lc_src.count(old) == 1, f"mutation site for {name} not found exactly once"
+        lc_src, suite = lc_src.replace(old, new), _pin_suite
+    else:
+        old, new = FOR_MUTANTS[name]
+        assert for_src.count(old) == 1, f"mutation site for {name} not found exactly once"
+        for_src, suite = for_src.replace(old, new), _for_pin_suite
+    lib = _mutant_lib(tmp_path, lc_src, for_src)
     saved = oracle._L()
     oracle._lib = oracle.bind(lib)
     try:
         with pytest.raises((AssertionError, oracle.OracleError)):
-            _pin_suite()
+            suite()
     finally:
         oracle._lib = saved
 
 
 def test_unmutated_oracle_passes_the_same_suite():
     _pin_suite()
+    _for_pin_suite()
