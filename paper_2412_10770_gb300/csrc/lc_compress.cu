@@ -171,14 +171,13 @@ constexpr uint32_t kFB = 32;                    // keys per fit block: one 32-bi
 constexpr uint32_t kWinKeys = 8192;             // keys per window, one CTA
 constexpr uint32_t kSpan = 64;                  // keys per speculating thread (two blocks)
 constexpr uint32_t kWarm = 96;                  // keys a speculative walk runs before its span
-constexpr uint32_t kFCap = 32;                  // a speculative walk follows a segment at most this far past its span
 constexpr int kSpecThreads = kWinKeys / kSpan;  // 128
-constexpr uint32_t kSpecKeys = kWarm + kWinKeys + kFCap;
+constexpr uint32_t kSpecKeys = kWarm + kWinKeys + 96;  // a walk ends at most 96 keys past its span
 constexpr uint32_t kSpecSlots = kSpecKeys + kSpecKeys / 64 + 1;
 constexpr int kShortThreads = kWinKeys / kFB;   // 256: one thread per block in fit_short_kernel
 constexpr int kChainThreads = 128;              // four chunks per CTA, one warp each
 constexpr uint32_t kShortMax = 96;              // segments of at most this many keys: one thread fits each
-static_assert(kShortMax == 96 && kShortMax > kSpan + kFCap - 1, "a speculative walk closes segments of at most kSpan + kFCap - 1 keys");
+static_assert(kShortMax == 96, "the speculative walks and fit_short_kernel's anchor search assume 96");
 constexpr uint32_t kPiece = 2048;               // keys per work item of a long segment's width pass
 
 // A segment longer than kShortMax keys, as its walk in the chain found it.
@@ -244,73 +243,112 @@ struct Frac32 {
     uint32_t F;
 };
 __device__ __forceinline__ Frac32 frac32_open() { return Frac32{INT32_MIN, 1u, 0x7FFFFFFFu, 1u}; }
-__device__ __forceinline__ bool frac32_step(uint32_t D, uint32_t d, int32_t eps, Frac32& c) {
-    const int32_t xl = (int32_t)D - eps;
-    const uint32_t yh = D + (uint32_t)eps + 1u;
-    Frac32 n = c;
-    if ((int64_t)xl * c.E > (int64_t)c.X * d) { n.X = xl; n.E = d; }
-    if ((uint64_t)yh * c.F < (uint64_t)c.Y * d) { n.Y = yh; n.F = d; }
-    if (n.X >= 0 && (uint64_t)(uint32_t)n.X * n.F >= (uint64_t)n.Y * n.E) return false;
-    c = n;
-    return true;
+
+// What one speculative walk leaves for its two blocks: its anchors in each
+// block, its first anchor at or after the span's start (entry of block 0), at
+// or after the second block's start (exit of block 0 = entry of block 1), and
+// at or after the span's end (exit of block 1); kNone where the walk stopped
+// before finding it.
+struct SpecOut {
+    uint32_t m0, m1;
+    uint32_t ent, mid, ex;
+};
+
+__device__ __forceinline__ void spec_record(SpecOut& o, uint32_t i, uint32_t s0) {
+    const uint32_t r = i - s0;
+    if (r < 32) o.m0 |= 1u << r;
+    else if (r < 64) o.m1 |= 1u << (r - 32);
+    if (o.ent == kNone) o.ent = i;
+    if (o.mid == kNone && r >= 32) o.mid = i;
+    if (r >= 64) o.ex = i;
 }
 
 // One thread's speculative walk: the greedy from `p` (taken as an anchor)
-// over keys [p, lim), recording its anchors at positions [s0, s0 + 96) as
-// bits (s0 is the thread's span start).  Returns true if the walk reached lim
-// inside a segment (its next anchor is then unknown unless lim is the
-// chunk's end).
+// until its first anchor at or after s0 + 64 (the span's end) or the chunk's
+// end n.  A segment that would grow past kShortMax keys stops it (its end is
+// left to the chain, which walks long segments itself), so every segment the
+// walk closes has at most kShortMax keys.  The narrow walk reads 32-bit key
+// offsets from shared memory (exact differences: the walk's key range is
+// below 2^31); the wide one reads 64-bit keys from global memory.
 template <bool kNarrow, typename ST>
-__device__ __forceinline__ void spec_walk(const ST& st, uint32_t p, uint32_t lim, uint32_t s0, int64_t eps,
-                                          uint32_t bits[3]) {
+__device__ __forceinline__ SpecOut spec_walk(const ST& st, uint32_t p, uint32_t n, uint32_t s0, int64_t eps) {
+    SpecOut o{0u, 0u, kNone, kNone, kNone};
+    const uint32_t lim = min(n, s0 + kSpan + kShortMax);
     uint32_t x = p;
-    uint64_t kx = st(p);
-    if (p >= s0) bits[(p - s0) >> 5] |= 1u << ((p - s0) & 31u);
+    if (p >= s0) spec_record(o, p, s0);
+    uint32_t i = p + 1;
     if (kNarrow) {
-        Frac32 c = frac32_open();
-        for (uint32_t i = p + 1; i < lim; ++i) {
-            const uint64_t Ki = st(i);
-            if (frac32_step((uint32_t)(Ki - kx), i - x, (int32_t)eps, c)) continue;
-            x = i;
-            kx = Ki;
-            c = frac32_open();
-            if (i >= s0) bits[(i - s0) >> 5] |= 1u << ((i - s0) & 31u);
+        // branch-free steps: every lane runs the same instructions whether its
+        // key moves the cone, leaves it alone or starts a new segment
+        uint32_t kx = (uint32_t)st(p);
+        int32_t X = INT32_MIN;
+        uint32_t E = 1u, Y = 0x7FFFFFFFu, F = 1u;
+        const int32_t e32 = (int32_t)eps;
+        for (; i < lim && i - x <= kShortMax; ++i) {
+            const uint32_t Ki = (uint32_t)st(i);
+            const uint32_t D = Ki - kx, d = i - x;
+            const int32_t xl = (int32_t)D - e32;
+            const uint32_t yh = D + (uint32_t)e32 + 1u;
+            const bool lm = (int64_t)xl * E > (int64_t)X * d;
+            const bool hm = (uint64_t)yh * F < (uint64_t)Y * d;
+            const int32_t nX = lm ? xl : X;
+            const uint32_t nE = lm ? d : E, nY = hm ? yh : Y, nF = hm ? d : F;
+            const bool ok = nX < 0 || (uint64_t)(uint32_t)nX * nF < (uint64_t)nY * nE;
+            X = ok ? nX : INT32_MIN;
+            E = ok ? nE : 1u;
+            Y = ok ? nY : 0x7FFFFFFFu;
+            F = ok ? nF : 1u;
+            if (!ok) {
+                x = i;
+                kx = Ki;
+                if (i >= s0) {
+                    spec_record(o, i, s0);
+                    if (i >= s0 + kSpan) break;
+                }
+            }
         }
     } else {
+        uint64_t kx = st(p);
         Frac c = frac_open();
-        for (uint32_t i = p + 1; i < lim; ++i) {
+        for (; i < lim && i - x <= kShortMax; ++i) {
             const uint64_t Ki = st(i);
             if (frac_step(Ki - kx, i - x, eps, c)) continue;
             x = i;
             kx = Ki;
             c = frac_open();
-            if (i >= s0) bits[(i - s0) >> 5] |= 1u << ((i - s0) & 31u);
+            if (i >= s0) {
+                spec_record(o, i, s0);
+                if (i >= s0 + kSpan) break;
+            }
         }
     }
-}
-
-// First set bit at position >= from in the 96-bit mask, or kNone.
-__device__ __forceinline__ uint32_t first_bit_from(const uint32_t bits[3], uint32_t from) {
-#pragma unroll
-    for (uint32_t w = 0; w < 3; ++w) {
-        if (from >= 32 * (w + 1)) continue;
-        const uint32_t sh = from > 32 * w ? from - 32 * w : 0u;
-        const uint32_t m = bits[w] & (0xFFFFFFFFu << sh);
-        if (m) return 32 * w + (uint32_t)(__ffs(m) - 1);
+    // the walk ran into the chunk's end inside a segment of at most kShortMax keys: n is its next anchor
+    if (i >= n && i - x <= kShortMax) {
+        if (o.ent == kNone) o.ent = n;
+        if (o.mid == kNone) o.mid = n;
+        if (o.ex == kNone) o.ex = n;
     }
-    return kNone;
+    return o;
 }
 
-// One CTA per window of 8192 keys of one chunk; keys [w0 - kWarm, w1 + kFCap)
-// staged in shared memory.  Thread t owns the span of blocks 2t, 2t+1 and
-// runs the greedy from kWarm keys before the span (from the chunk start if
-// that is closer) to kFCap keys past it.  Greedy walks from different starts
-// meet after a few segments, so by the span the walk is almost always on the
-// true chain; the chain kernel checks that (a block is exact iff the walk
-// enters it where the previous block's walk leaves it) and walks itself where
-// it does not hold.  Per block: the walk's anchors in the block (spec), its
-// first anchor at or after the block's start (entry) and after its end
-// (exit); kNone if the walk stopped inside a segment before reaching it, the
+// Key i of a chunk from global memory (the wide speculative walk).
+template <typename KT>
+struct GlobalKeys {
+    const KT* K;
+    __device__ __forceinline__ uint64_t operator()(uint32_t i) const { return (uint64_t)__ldg(K + i); }
+};
+
+// One CTA per window of 8192 keys of one chunk; keys [w0 - kWarm, w1 + 96)
+// staged in shared memory as 32-bit offsets from the first staged key.
+// Thread t owns the span of blocks 2t, 2t+1 and runs the greedy from kWarm
+// keys before the span (from the chunk start if that is closer) to its first
+// anchor past the span.  Greedy walks from different starts meet after a few
+// segments, so by the span the walk is almost always on the true chain; the
+// chain kernel checks that (a block is exact iff the walk enters it where the
+// previous block's walk leaves it) and walks itself where it does not hold.
+// Per block: the walk's anchors in the block (spec), its first anchor at or
+// after the block's start (entry) and after its end (exit); kNone if the walk
+// stopped inside a segment of more than kShortMax keys before reaching it, the
 // chunk's length if the chunk ends first.  Also checks sortedness.
 template <typename KT>
 __global__ void __launch_bounds__(kSpecThreads)
@@ -325,41 +363,41 @@ spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, c
     const int64_t eps = cd.eps;
     const uint32_t tid = threadIdx.x;
     const uint32_t base = w0 >= kWarm ? w0 - kWarm : 0;
-    const uint32_t top = min(n, w1 + kFCap);
-    KT* s = (KT*)smem;
-    for (uint32_t q = tid; q < top - base; q += kSpecThreads) s[q + (q >> 6)] = __ldg(K + base + q);
-    __syncthreads();
-    const Staged64<KT> st{s, base};
+    const uint32_t top = min(n, w1 + 96);
+    // stage the low 32 bits of K[i] - K[base]: a difference of two staged
+    // values is exact whenever the true difference is below 2^32
+    uint32_t* s = (uint32_t*)smem;
+    const uint64_t kbase = (uint64_t)__ldg(K + base);
+#pragma unroll 4
+    for (uint32_t q = tid; q < top - base; q += kSpecThreads) s[q + (q >> 6)] = (uint32_t)((uint64_t)__ldg(K + base + q) - kbase);
+    // sortedness: key i against key i - 1 for i in [max(w0, 1), w1)
     bool unsorted = false;
-    for (uint32_t i = max(w0, 1u) + tid; i < w1; i += kSpecThreads) unsorted |= st(i - 1) > st(i);
+#pragma unroll 4
+    for (uint32_t i = max(w0, 1u) + tid; i < w1; i += kSpecThreads) unsorted |= __ldg(K + i - 1) > __ldg(K + i);
     if (w0 == 0 && cd.check_prev && tid == 0) unsorted |= __ldg(K - 1) > __ldg(K);
     if (unsorted) atomicOr(status, kStUnsorted);
+    __syncthreads();
+    const Staged64<uint32_t> st{s, base};
 
     const uint32_t s0 = w0 + tid * kSpan;  // this thread's span [s0, s0 + 64) (may start past w1)
     const bool active = s0 < w1;
     const uint32_t p = s0 >= base + kWarm ? s0 - kWarm : base;
-    const uint32_t lim = active ? min(n, s0 + kSpan + kFCap) : p + 1;
+    const uint32_t lim = active ? min(n, s0 + kSpan + kShortMax) : p + 1;
     // the walk may use 32-bit numerators when its whole key range allows it (warp-uniform choice)
-    const uint64_t span_keys = active ? st(lim - 1) - st(p) : 0;
+    const uint64_t span_keys = active ? (uint64_t)__ldg(K + lim - 1) - (uint64_t)__ldg(K + p) : 0;
     const bool narrow = __all_sync(0xFFFFFFFFu, span_keys + (uint64_t)eps + 1 < (1ull << 31));
-    uint32_t bits[3] = {0u, 0u, 0u};
-    if (active) {
-        if (narrow) spec_walk<true>(st, p, lim, s0, eps, bits);
-        else spec_walk<false>(st, p, lim, s0, eps, bits);
-    }
     if (!active) return;
-    // the walk's next anchor after lim is unknown unless the chunk ends there
-    const uint32_t tail = lim >= n ? n : kNone;
-#pragma unroll
-    for (uint32_t h = 0; h < 2; ++h) {
-        const uint32_t b = s0 + h * kFB;
-        if (b >= w1) break;
-        const uint32_t e = min(b + kFB, n);
-        const uint32_t fe = first_bit_from(bits, h * kFB), fx = first_bit_from(bits, e - s0);
-        const uint64_t g = cd.bitword_begin + b / kFB;
-        spec_g[g] = bits[h] & (e - b < 32 ? (1u << (e - b)) - 1u : 0xFFFFFFFFu);
-        entry_g[g] = fe != kNone ? s0 + fe : tail;
-        exit_g[g] = fx != kNone ? s0 + fx : tail;
+    const SpecOut o = narrow ? spec_walk<true>(st, p, n, s0, eps) : spec_walk<false>(GlobalKeys<KT>{K}, p, n, s0, eps);
+    const uint64_t g = cd.bitword_begin + s0 / kFB;
+    const uint32_t e0 = min(s0 + kFB, n);
+    spec_g[g] = o.m0 & (e0 - s0 < 32 ? (1u << (e0 - s0)) - 1u : 0xFFFFFFFFu);
+    entry_g[g] = o.ent;
+    exit_g[g] = o.mid;
+    if (s0 + kFB < w1) {
+        const uint32_t e1 = min(s0 + 2 * kFB, n);
+        spec_g[g + 1] = o.m1 & (e1 - s0 - kFB < 32 ? (1u << (e1 - s0 - kFB)) - 1u : 0xFFFFFFFFu);
+        entry_g[g + 1] = o.mid;
+        exit_g[g + 1] = o.ex;
     }
 }
 
@@ -372,8 +410,8 @@ spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, c
 // blocks takes the whole run at once).  Elsewhere the warp walks one segment
 // itself (32 keys per step, or 256 while the cone does not move) and looks
 // again.  Output: the chunk's anchor bitmap and segment count.  Every segment
-// longer than kShortMax keys is found by such a walk (the speculative walks
-// stop kFCap keys past their span), and the walk ends with the segment's
+// longer than kShortMax keys is found by such a walk (a speculative walk stops
+// inside any segment longer than that), and the walk ends with the segment's
 // cone: its slope and end are recorded at the anchor's block (at most one such
 // segment starts in a block).
 template <typename KT>
@@ -405,17 +443,18 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
         if (k != knext) pm = 0;
         for (uint32_t q = knext + lane; q < k; q += 32) T[q] = 0;
         knext = k;
-        const uint32_t m0 = __ldg(spec_g + gb + k);
+        // the walks of blocks k .. k+31 (one load round per step)
+        const uint32_t kb = k + lane;
+        const bool valid = kb < nblk;
+        uint32_t m = 0, ex = kNone, ent = kNone;
+        if (valid) {
+            m = __ldg(spec_g + gb + kb);
+            ex = __ldg(exit_g + gb + kb);
+            ent = __ldg(entry_g + gb + kb);
+        }
+        const uint32_t m0 = __shfl_sync(0xFFFFFFFFu, m, 0);
         if ((m0 >> (x - b)) & 1u) {
             // x is on block k's walk: exact from x on; extend over consistent blocks
-            const uint32_t kb = k + lane;
-            const bool valid = kb < nblk;
-            uint32_t m = 0, ex = kNone, ent = kNone;
-            if (valid) {
-                m = __ldg(spec_g + gb + kb);
-                ex = __ldg(exit_g + gb + kb);
-                ent = __ldg(entry_g + gb + kb);
-            }
             if (lane == 0) m = pm | (m & (0xFFFFFFFFu << (x - b)));
             const uint32_t exp = __shfl_up_sync(0xFFFFFFFFu, ex, 1);
             const bool cons = valid && (lane == 0 || (ent == exp && exp != kNone));
@@ -518,7 +557,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
                  uint32_t* __restrict__ bitoff, uint16_t* __restrict__ start, uint8_t* __restrict__ width,
                  LongItem* __restrict__ items, uint32_t* __restrict__ nitems, uint32_t items_cap,
                  Piece* __restrict__ pieces, uint32_t* __restrict__ npieces, uint32_t pieces_cap,
-                 uint32_t* __restrict__ status) {
+                 ulonglong2* __restrict__ cones, uint32_t* __restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr uint32_t kWords = kWinKeys / kFB;
     __shared__ uint32_t s_T[kWords + 4];
@@ -556,9 +595,9 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     const uint32_t pre = block_excl_scan<uint32_t>(__popc(word), AddOp(), 0u, s_warp, nullptr);
     uint64_t j = csb[wd.chunk] + s_base + pre;
     const uint64_t* __restrict__ magic = g_magic;
-    for (uint32_t rest = word; rest; rest &= rest - 1, ++j) {
-        const uint32_t a = w0 + tid * kFB + (uint32_t)(__ffs(rest) - 1);
-        // next anchor among the kShortMax = 96 keys after a (bit t: key a + 1 + t)
+    // the next anchor among the kShortMax = 96 keys after a (bit t: key a + 1 + t), n if the chunk ends
+    // first, kNone if neither
+    auto next_anchor = [&](uint32_t a) -> uint32_t {
         const uint32_t q = a + 1 - w0, qi = q >> 5, sh = q & 31u;
         const uint64_t lo64 = ((uint64_t)s_T[qi + 1] << 32) | s_T[qi];
         const uint64_t hi64 = ((uint64_t)s_T[qi + 3] << 32) | s_T[qi + 2];
@@ -571,49 +610,123 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
         } else if (left < 96) {
             nhi &= (1u << (left - 64)) - 1u;
         }
-        uint32_t b;
-        if (nlo) b = a + 1 + (uint32_t)(__ffsll((long long)nlo) - 1);
-        else if (nhi) b = a + 65 + (uint32_t)(__ffs(nhi) - 1);
-        else if (left < kShortMax) b = n;
-        else b = kNone;
-        const uint64_t ka = st(a);
-        icpt[j] = (KT)ka;
-        start[j] = (uint16_t)a;
-        if (b != kNone) {
-            int64_t M = 0;
-            uint32_t zmax = 0;
-            if (b - a >= 2) {
-                Frac c;
-                {
-                    const uint64_t D = st(a + 1) - ka;
-                    c.X = (int64_t)D - eps;
-                    c.E = 1;
-                    c.Y = D + (uint64_t)eps + 1;
-                    c.F = 1;
-                }
-                for (uint32_t i = a + 2; i < b; ++i) {
-                    const uint64_t D = st(i) - ka;
-                    const uint32_t d = i - a;
-                    const int64_t xl = (int64_t)D - eps;
-                    const uint64_t yh = D + (uint64_t)eps + 1;
-                    if (frac_gt(xl, d, c.X, c.E)) { c.X = xl; c.E = d; }
-                    if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { c.Y = yh; c.F = d; }
-                }
-                M = frac_slope(c, magic);
-                for (uint32_t i = a + 1; i < b; ++i)
-                    zmax = max(zmax, zigzag32((int64_t)(st(i) - ka) - line_at(M, i - a)));
-            }
-            slope[j] = M;
-            width[j] = (uint8_t)(32u - __clz(zmax));
-        } else {
-            const LongInfo li = longinfo[cd.bitword_begin + (a >> 5)];
-            slope[j] = 0;
-            width[j] = 0;
-            if (li.end <= a + kShortMax || li.end > n) {  // no walk recorded it: cannot happen
-                atomicOr(status, kStInternal);
+        if (nlo) return a + 1 + (uint32_t)(__ffsll((long long)nlo) - 1);
+        if (nhi) return a + 65 + (uint32_t)(__ffs(nhi) - 1);
+        return left < kShortMax ? n : kNone;
+    };
+    auto is_anchor = [&](uint32_t i) { return (s_T[(i - w0) >> 5] >> ((i - w0) & 31u)) & 1u; };
+    // The thread's segments are those whose anchor lies in its block: every
+    // one up to the last anchor a_last is short (it ends at the next anchor);
+    // the one at a_last is short iff the next anchor is within 96 keys.  Keys
+    // [a_first, end) are therefore whole short segments, walked as one flat
+    // loop twice: the cone and slope, then the widths.
+    uint32_t a_first = 0, a_last = 0, e_last = kNone, end = 0;
+    if (word) {
+        const uint32_t b0 = w0 + tid * kFB;
+        a_first = b0 + (uint32_t)(__ffs(word) - 1);
+        a_last = b0 + 31u - (uint32_t)__clz(word);
+        e_last = next_anchor(a_last);
+        end = e_last != kNone ? e_last : a_last;
+    }
+    const uint64_t range = end > a_first + 1 ? st(end - 1) - st(a_first) : 0;
+    const bool narrow = __all_sync(0xFFFFFFFFu, range + (uint64_t)eps + 1 < (1ull << 31));
+    const uint64_t j_first = j;
+    if (end > a_first) {
+        // pass 1: cones (the anchors are known, so every key only narrows its
+        // segment's cone); a closed cone goes to scratch, its slope is taken
+        // in pass S, so that no lane waits on another lane's divisions here
+        uint32_t a = a_first;
+        uint64_t ka = st(a);
+        Frac c = frac_open();
+        Frac32 c32 = frac32_open();
+        auto close = [&](uint32_t e) {
+            Frac f = c;
+            if (narrow) f = Frac{(int64_t)c32.X, c32.E, (uint64_t)c32.Y, c32.F};
+            // short segment: E, F <= 95 and |X|, Y < 2^38, packed in 16 bytes; E = 0 marks one key
+            const uint32_t E = e - a >= 2 ? f.E : 0u;
+            cones[j] = make_ulonglong2(((uint64_t)f.X & ((1ull << 48) - 1)) | ((uint64_t)E << 48) |
+                                           ((uint64_t)f.F << 56),
+                                       f.Y);
+            icpt[j] = (KT)ka;
+            start[j] = (uint16_t)a;
+        };
+        for (uint32_t i = a_first + 1; i < end; ++i) {
+            const uint64_t Ki = st(i);
+            if (is_anchor(i)) {
+                close(i);
+                ++j;
+                a = i;
+                ka = Ki;
+                c = frac_open();
+                c32 = frac32_open();
                 continue;
             }
-            const uint32_t q = atomicAdd(&s_nlong, 1u);  // at most one per 65 keys: fits
+            const uint32_t d = i - a;
+            if (narrow) {
+                const uint32_t D = (uint32_t)(Ki - ka);
+                const int32_t xl = (int32_t)D - (int32_t)eps;
+                const uint32_t yh = D + (uint32_t)eps + 1u;
+                if ((int64_t)xl * c32.E > (int64_t)c32.X * d) { c32.X = xl; c32.E = d; }
+                if ((uint64_t)yh * c32.F < (uint64_t)c32.Y * d) { c32.Y = yh; c32.F = d; }
+            } else {
+                const uint64_t D = Ki - ka;
+                const int64_t xl = (int64_t)D - eps;
+                const uint64_t yh = D + (uint64_t)eps + 1;
+                if (frac_gt(xl, d, c.X, c.E)) { c.X = xl; c.E = d; }
+                if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { c.Y = yh; c.F = d; }
+            }
+        }
+        close(end);
+        const uint64_t j_end = j + 1;
+        // pass S: the slope of every segment from its cone (floor midpoint, 0 for one key)
+        for (uint64_t q = j_first; q < j_end; ++q) {
+            const ulonglong2 cc = cones[q];
+            const uint32_t E = (uint32_t)(cc.x >> 48) & 0xFFu;
+            int64_t M = 0;
+            if (E) {
+                Frac f;
+                f.X = (int64_t)(cc.x << 16) >> 16;  // sign-extend the 48-bit numerator
+                f.E = E;
+                f.F = (uint32_t)(cc.x >> 56);
+                f.Y = cc.y;
+                M = frac_slope(f, magic);
+            }
+            slope[q] = M;
+        }
+        // pass 2: widths, from the slopes just written (plain loads: this thread wrote them)
+        j = j_first;
+        a = a_first;
+        ka = st(a);
+        int64_t M = slope[j];
+        uint32_t zmax = 0;
+        for (uint32_t i = a_first + 1; i < end; ++i) {
+            const uint64_t Ki = st(i);
+            if (is_anchor(i)) {
+                width[j] = (uint8_t)(32u - __clz(zmax));
+                ++j;
+                a = i;
+                ka = Ki;
+                M = slope[j];
+                zmax = 0;
+                continue;
+            }
+            zmax = max(zmax, zigzag32((int64_t)(Ki - ka) - line_at(M, i - a)));
+        }
+        width[j] = (uint8_t)(32u - __clz(zmax));
+        ++j;
+    }
+    if (word && e_last == kNone) {
+        // the segment at a_last is longer than 96 keys: its slope came from the chain's walk
+        const uint32_t a = a_last;
+        icpt[j] = (KT)st(a);
+        start[j] = (uint16_t)a;
+        const LongInfo li = longinfo[cd.bitword_begin + (a >> 5)];
+        slope[j] = 0;
+        width[j] = 0;
+        if (li.end <= a + kShortMax || li.end > n) {  // no walk recorded it: cannot happen
+            atomicOr(status, kStInternal);
+        } else {
+            const uint32_t q = atomicAdd(&s_nlong, 1u);  // at most one per 97 keys: fits
             if (q < kLongPerWin) s_long[q] = WinLong{j, li.M, a, li.end - a};
         }
     }
@@ -921,6 +1034,7 @@ struct FitScratch {
     LongItem* items;
     Piece* pieces;
     uint32_t* counters;  // [0] long items, [1] pieces
+    ulonglong2* cones;   // stage 1: the cone of every short segment [L]
     uint32_t items_cap, pieces_cap;
 };
 
@@ -934,7 +1048,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
     const Layout& lay = col->lay;
     if (stage == 0) {
         static bool attr[2] = {false, false};
-        const size_t smem = sizeof(KT) * kSpecSlots;
+        const size_t smem = sizeof(uint32_t) * kSpecSlots;
         if (!attr[sizeof(KT) == 8]) {
             int rc = cuda_status(
                 cudaFuncSetAttribute(spec_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -970,7 +1084,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
             keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
             (int64_t*)(blob + lay.slope), (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start),
             (uint8_t*)(blob + lay.width), fs.items, fs.counters, fs.items_cap, fs.pieces, fs.counters + 1,
-            fs.pieces_cap, status);
+            fs.pieces_cap, fs.cones, status);
     }
     {
         KTime kt("model_long", st);
@@ -1052,9 +1166,11 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     fs.pieces_cap = (uint32_t)pieces_cap;
     uint64_t total = 0;
     uint32_t h_status = 0;
+    fs.cones = nullptr;
     auto fail = [&](int code) {
         cudaStreamSynchronize(st);
         cudaFreeAsync(scratch, st);
+        if (fs.cones) cudaFreeAsync(fs.cones, st);
         return code;
     };
 
@@ -1102,6 +1218,11 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     col->lay = lay;
     rc = cuda_status(cudaMemcpyAsync(col->blob + lay.csb, csb_tmp, (C + 1) * 8, cudaMemcpyDeviceToDevice, st));
     if (rc) return fail(rc);
+    // the cones of the short segments between the fit's two passes (16 bytes per segment)
+    if (cudaMallocAsync((void**)&fs.cones, 16 * std::max<uint64_t>(L, 1), st) != cudaSuccess) {
+        fs.cones = nullptr;
+        return fail(LC_ERR_NOMEM);
+    }
 
     // stage 1: model, widths, payload
     if (kb == 4)
@@ -1121,6 +1242,7 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     col->W = total;
     col->lay = make_layout(kb, C, L, col->W, col->NL, col->list_mode != 0);
     cudaFreeAsync(scratch, st);
+    cudaFreeAsync(fs.cones, st);
     return LC_OK;
 }
 
