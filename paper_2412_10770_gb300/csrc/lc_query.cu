@@ -314,30 +314,6 @@ decode_ranges_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64
                      v.max_tile_segs);
 }
 
-// Key t of the segment whose record is r (Fig. 2: floor(f_j(i)) + Delta[i]).
-__device__ __forceinline__ uint64_t rec_key(const ColView& v, const SegRec& r, uint32_t t) {
-    if (t == 0) return r.icpt;
-    const uint32_t w = (uint32_t)(r.kstart_w >> 56);
-    const int64_t line = line_at(r.slope, t);
-    if (w == 0) return r.icpt + (uint64_t)line;
-    const uint64_t pos = (r.bit1_n & kBitMask) + (uint64_t)w * (t - 1);
-    const uint64_t wi = pos >> 5;  // < 2W: the residual's bits lie inside the payload
-    const uint32_t lo = __ldg(v.pay32 + wi);
-    const uint32_t hi = wi + 1 < 2 * v.W ? __ldg(v.pay32 + wi + 1) : 0u;
-    return r.icpt + (uint64_t)(line + (int64_t)unzigzag32(extract_bits(lo, hi, (uint32_t)(pos & 31u), w)));
-}
-
-__device__ __forceinline__ SegRec load_rec(const SegRec* p) {
-    const ulonglong2* q = (const ulonglong2*)p;
-    const ulonglong2 a = __ldg(q), b = __ldg(q + 1);
-    SegRec r;
-    r.icpt = a.x;
-    r.slope = (int64_t)a.y;
-    r.kstart_w = b.x;
-    r.bit1_n = b.y;
-    return r;
-}
-
 constexpr uint64_t kKeyMask = (1ull << 56) - 1;
 
 // L2 eviction priorities for the random lookups: directories that many queries
@@ -357,11 +333,6 @@ __device__ __forceinline__ uint64_t policy_stream() {
 __device__ __forceinline__ ulonglong2 ld2_hint(const void* ptr, uint64_t pol) {
     ulonglong2 r;
     asm("ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;" : "=l"(r.x), "=l"(r.y) : "l"(ptr), "l"(pol));
-    return r;
-}
-__device__ __forceinline__ uint2 ld2x32_hint(const void* ptr, uint64_t pol) {
-    uint2 r;
-    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(r.x), "=r"(r.y) : "l"(ptr), "l"(pol));
     return r;
 }
 __device__ __forceinline__ uint64_t ld64_hint(const void* ptr, uint64_t pol) {
