@@ -412,6 +412,9 @@ def main():
             "segments": {g: sizes[g][1] for g in gens},
             "clocks": clocks, "gpu_launches": launches}
 
+    # the quantile and segments-only rows (Sec. III-C), timed apart from the step
+    line["analytics"] = measure_analytics(args, cols, lc, torch, stream, out_dec, out_acc, peak)
+
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         e2e = run_e2e(args, cols, lc, torch, stream)
@@ -435,6 +438,43 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def measure_analytics(args, cols, lc, torch, stream, out_dec, out_acc, peak):
+    """Per column, after the timed steps: the segments-only decode of every key
+    and m quantile queries (exact and from the segments alone) with q = 2^32
+    and k uniform in [0, q].  Mean of 3 runs each, CUDA events."""
+    N, m = args.n, args.queries
+    res = {}
+    for g, host, dev in cols:
+        col = lc.lc_compress(dev["keys"], eps=args.eps, chunk_log2=16, stream=stream)
+        L = col.info["segments"]
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(11)
+        q = 1 << 32
+        ks = torch.randint(0, q + 1, (m,), generator=gen, device="cuda", dtype=torch.int64).view(torch.uint64)
+        row = {}
+        for name, fn, units, alg in (
+                ("decode_approx", lambda: lc.lc_decode_approx(col, 0, N, out_dec, stream=stream), N,
+                 8 * N + N / 4 + 32 * L),
+                ("quantile", lambda: lc.lc_quantile(col, ks, q, True, out_acc, stream=stream), m, m * (8 + 8 + 64)),
+                ("quantile_approx", lambda: lc.lc_quantile(col, ks, q, False, out_acc, stream=stream), m,
+                 m * (8 + 8 + 32))):
+            fn()
+            torch.cuda.synchronize()
+            ms = 0.0
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b) / 3
+            row[name] = {"ms": ms, "units_per_s": units / (ms / 1e3), "alg_gbs": alg / (ms / 1e3) / 1e9,
+                         "hbm_frac": alg / (ms / 1e3) / 1e9 / peak}
+        res[g] = row
+        col.free()
+    return res
 
 
 def run_batch(args):

@@ -178,6 +178,23 @@ int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* o
 int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t* out_dev,
                    void* stream);
 
+/* Quantiles (Sec. III-C, Table 2): out[r] = the k[r]-th q-quantile of the
+ * column, the key at index floor(N k / q) (the last key for k = q; the index
+ * is computed exactly).  exact = 1: f(i) + Delta[i], the key itself (rank
+ * access).  exact = 0: floor(f(i)) from the segments alone, without reading
+ * any residual (approximate query processing; within eps of the key, Def. 2).
+ * k_dev: m uint64 values (device), 0 <= k <= q; a k > q yields 0 and sets
+ * LC_ERR_OUT_OF_RANGE in the status word.  out_dev: m keys (device).  q >= 1.
+ * Single columns only (LC_ERR_UNSUPPORTED in list mode).  Asynchronous. */
+int lc_quantile(const lc_column* col, const uint64_t* k_dev, uint64_t m, uint64_t q, int exact, void* out_dev,
+                void* stream);
+
+/* Segments-only decode (Sec. III-C approximate query processing): out_dev
+ * receives floor(f(i)) for i in [begin, begin + count), each within eps of
+ * K[i] (Def. 2); the residual array is not read.  Layout and errors as
+ * lc_decode.  Asynchronous. */
+int lc_decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream);
+
 /* Scalar conveniences (synchronous, legacy default stream). */
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key);
 int lc_lower_bound1(const lc_column* col, uint64_t v, uint64_t* pos);

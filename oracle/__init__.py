@@ -68,6 +68,8 @@ def bind(path: str) -> ctypes.CDLL:
     lib.lco_decode.argtypes = [p, u64, p]
     lib.lco_access.argtypes = [p, u64, p, u64, p]
     lib.lco_lower_bound.argtypes = [p, u64, p, u64, p]
+    lib.lco_predict.argtypes = [p, u64, p, u64, p]
+    lib.lco_predict.restype = ctypes.c_int
     lib.lco_free.argtypes = [p]
     lib.lco_for_compress.argtypes = [p, u64, ctypes.c_int, pp, pu64]
     lib.lco_for_decode.argtypes = [p, u64, p]
@@ -156,6 +158,21 @@ def access(blob: bytes, idx) -> np.ndarray:
     out = np.empty(ix.size, dtype=_dtype(inf["key_bytes"]))
     _check(_L().lco_access(blob, len(blob), ix.ctypes.data, ix.size, out.ctypes.data))
     return out
+
+
+def predict(blob: bytes, idx) -> np.ndarray:
+    """floor(f(i)) for every i in idx: the model alone, without residuals."""
+    inf = info(blob)
+    ix = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.empty(ix.size, dtype=_dtype(inf["key_bytes"]))
+    _check(_L().lco_predict(blob, len(blob), ix.ctypes.data, ix.size, out.ctypes.data))
+    return out
+
+
+def quantile_index(n: int, k: int, q: int) -> int:
+    """Index of the k-th q-quantile (Sec. III-C): floor(n k / q), the last key
+    for k = q (exact integer arithmetic)."""
+    return min(n * k // q, n - 1)
 
 
 def lower_bound(blob: bytes, values) -> np.ndarray:

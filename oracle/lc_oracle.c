@@ -554,6 +554,37 @@ int lco_access(const uint8_t* blob, uint64_t len, const uint64_t* idx, uint64_t 
     return LCO_OK;
 }
 
+/* floor(f(i)) for every i in idx: the segments alone, no residual (Sec. III-C
+ * approximate query processing; within eps of K[i] by Def. 2).  The segment
+ * of i is found exactly as in lco_access. */
+int lco_predict(const uint8_t* blob, uint64_t len, const uint64_t* idx, uint64_t m, void* out)
+{
+    oview v;
+    int rc = parse(blob, len, &v);
+    if (rc) return rc;
+    if (m && (!idx || !out)) return LCO_ERR_INVALID_ARG;
+    for (uint64_t q = 0; q < m; q++) {
+        uint64_t i = idx[q];
+        if (i >= v.N) return LCO_ERR_OUT_OF_RANGE;
+        uint64_t lo = 0, hi = v.C;
+        while (hi - lo > 1) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (U64(v.ckb, mid) <= i) lo = mid; else hi = mid;
+        }
+        uint64_t c = lo, local = i - U64(v.ckb, c);
+        uint64_t a = U64(v.csb, c), b = U64(v.csb, c + 1);
+        while (b - a > 1) {
+            uint64_t mid = a + (b - a) / 2;
+            if (get_le(v.start + 2 * mid, 2) <= local) a = mid; else b = mid;
+        }
+        uint64_t t = local - get_le(v.start + 2 * a, 2);
+        int64_t M = (int64_t)get_le(v.slope + 8 * a, 8);
+        i128 pred = (i128)icpt_of(&v, a) + (i128)(t ? line_offset(M, t) : 0);
+        put_le((uint8_t*)out + (uint64_t)v.kb * q, (uint64_t)pred, v.kb);
+    }
+    return LCO_OK;
+}
+
 int lco_lower_bound(const uint8_t* blob, uint64_t len, const void* vals, uint64_t m, uint64_t* out)
 {
     oview v;

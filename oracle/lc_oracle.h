@@ -102,6 +102,9 @@ int lco_access(const uint8_t* blob, uint64_t len, const uint64_t* idx, uint64_t 
  * v holds m values of key_bytes bytes. */
 int lco_lower_bound(const uint8_t* blob, uint64_t len, const void* v, uint64_t m, uint64_t* out);
 
+/* floor(f(idx[q])) from the segments alone (no residual), key_bytes each. */
+int lco_predict(const uint8_t* blob, uint64_t len, const uint64_t* idx, uint64_t m, void* out);
+
 void lco_free(void* p);
 
 /* The frame-of-reference delta bit-packing baseline ("FOR1", blocks of 128

@@ -488,6 +488,20 @@ int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t
     return lower_bound(col, v_dev, m, out_dev, (cudaStream_t)stream);
 }
 
+int lc_quantile(const lc_column* col, const uint64_t* k_dev, uint64_t m, uint64_t q, int exact, void* out_dev,
+                void* stream) {
+    if (!col || q == 0 || (m && (!k_dev || !out_dev))) return LC_ERR_INVALID_ARG;
+    if (col->list_mode) return LC_ERR_UNSUPPORTED;
+    if (col->N == 0) return m ? LC_ERR_OUT_OF_RANGE : LC_OK;
+    return quantile(col, k_dev, m, q, exact ? 1 : 0, out_dev, (cudaStream_t)stream);
+}
+
+int lc_decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream) {
+    if (!col || (count && !out_dev)) return LC_ERR_INVALID_ARG;
+    if (begin > col->N || count > col->N - begin) return LC_ERR_OUT_OF_RANGE;
+    return decode_approx(col, begin, count, out_dev, (cudaStream_t)stream);
+}
+
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key) {
     if (!col || !key) return LC_ERR_INVALID_ARG;
     if (i >= col->N) return LC_ERR_OUT_OF_RANGE;

@@ -174,6 +174,8 @@ int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uin
                           const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st);
 int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
+int quantile(const lc_column* col, const uint64_t* ks, uint64_t m, uint64_t q, int exact, void* out, cudaStream_t st);
+int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);
 
 // Serving: one batch of requests over several columns (lc_query.cu).
 int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, uint32_t nqreq, uint64_t nq,

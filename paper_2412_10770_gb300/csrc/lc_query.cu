@@ -446,6 +446,64 @@ __global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* _
         out[q] = lower_bound_one<KT>(v, (uint64_t)vals[q], keep, stream);
 }
 
+// ------------------------------------------------------------------ quantiles and segments-only (approximate) keys
+
+// floor(f_j(i)) of key i from the segments alone (Def. 2: within eps of K[i]):
+// the rank word gives the segment, its record the anchored line; no residual
+// is read.
+__device__ __forceinline__ uint64_t predict_one(const ColView& v, uint64_t i, uint64_t keep, uint64_t stream) {
+    const ulonglong2 rw = ld2_hint(v.rank + (i >> 6), keep);
+    const uint64_t j = rw.y + __popcll(rw.x & (~0ull >> (63u - (uint32_t)(i & 63u)))) - 1;
+    const SegRec r = load_rec_hint(v.recs + j, stream);
+    return r.icpt + (uint64_t)line_at(r.slope, (uint32_t)(i - (r.kstart_w & kKeyMask)));
+}
+
+// Index of the k-th q-quantile (Sec. III-C): floor(N k / q), the last key for
+// k = q.  Exact for every k <= q (128-bit product).
+__device__ __forceinline__ uint64_t quantile_index(uint64_t N, uint64_t k, uint64_t q) {
+    const unsigned __int128 t = (unsigned __int128)N * k / q;
+    return t >= N ? N - 1 : (uint64_t)t;
+}
+
+// out[r] = the ks[r]-th q-quantile: K[floor(N k/q)] (exact = 1, Sec. III-C)
+// or floor(f(floor(N k/q))) from the segments only (exact = 0, the
+// approximate answer within eps).  k > q is out of range (0 and a status bit).
+template <typename KT>
+__global__ void quantile_kernel(ColView v, const uint64_t* __restrict__ ks, uint64_t m, uint64_t q, int exact,
+                                KT* __restrict__ out) {
+    const uint64_t keep = policy_keep(), stream = policy_stream();
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m; r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ks[r];
+        if (k > q) {
+            atomicOr(v.status, kStOutOfRange);
+            out[r] = 0;
+            continue;
+        }
+        const uint64_t i = quantile_index(v.N, k, q);
+        out[r] = (KT)(exact ? access_one(v, i, keep, stream) : predict_one(v, i, keep, stream));
+    }
+}
+
+// Segments-only decode of keys [begin, begin + count): out[g - begin] =
+// floor(f(g)), within eps of K[g] (Sec. III-C, approximate query processing
+// without the residuals).  Four consecutive keys per thread share one rank
+// word and usually one record.
+template <typename KT>
+__global__ void __launch_bounds__(256) decode_approx_kernel(ColView v, uint64_t begin, uint64_t count,
+                                                            KT* __restrict__ out) {
+    const uint64_t keep = policy_keep(), stream = policy_stream();
+    const uint64_t groups = (count + 3) / 4;
+    for (uint64_t gq = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gq < groups;
+         gq += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t o0 = 4 * gq;
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint64_t o = o0 + u;
+            if (o < count) out[o] = (KT)predict_one(v, begin + o, keep, stream);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ serving: multi-column batches
 
 // Access and lower_bound requests of one batch, over any of the server's
@@ -905,6 +963,34 @@ int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* ou
             lower_bound_kernel<uint32_t><<<grid, 256, 0, st>>>(v, (const uint32_t*)vals, m, out);
         else
             lower_bound_kernel<uint64_t><<<grid, 256, 0, st>>>(v, (const uint64_t*)vals, m, out);
+    }
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+int quantile(const lc_column* col, const uint64_t* ks, uint64_t m, uint64_t q, int exact, void* out, cudaStream_t st) {
+    if (m == 0) return LC_OK;
+    const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
+    {
+        KTime kt(exact ? "quantile" : "quantile_approx", st);
+        if (col->key_bytes == 4)
+            quantile_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, ks, m, q, exact, (uint32_t*)out);
+        else
+            quantile_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, ks, m, q, exact, (uint64_t*)out);
+    }
+    note_launch();
+    return cuda_status(cudaGetLastError());
+}
+
+int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st) {
+    if (count == 0) return LC_OK;
+    const unsigned grid = (unsigned)std::min<uint64_t>((count / 4 + 256) / 256, (uint64_t)sm_count() * 16);
+    {
+        KTime kt("decode_approx", st);
+        if (col->key_bytes == 4)
+            decode_approx_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, begin, count, (uint32_t*)out);
+        else
+            decode_approx_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, begin, count, (uint64_t*)out);
     }
     note_launch();
     return cuda_status(cudaGetLastError());

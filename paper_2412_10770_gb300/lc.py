@@ -35,7 +35,8 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free", "lc_server_create", "lc_server_submit",
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
-           "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free")
+           "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
+           "lc_quantile", "lc_decode_approx")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -139,6 +140,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_for_size": ([p, pu64], i32),
         "lc_for_serialize": ([p, p, u64, pu64], i32),
         "lc_for_free": ([p], None),
+        "lc_quantile": ([p, p, u64, u64, i32, p, p], i32),
+        "lc_decode_approx": ([p, u64, u64, p, p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -342,6 +345,31 @@ def lc_info(col: Column) -> dict:
     inf = _Info()
     _check(load().lc_info(col.handle, ctypes.byref(inf)), "lc_info")
     return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+
+def lc_quantile(col: Column, ks: torch.Tensor, q: int, exact: bool = True, out=None, stream=None) -> torch.Tensor:
+    """The ks[r]-th q-quantiles (exact keys, or floor(f) from the segments alone)."""
+    lib = load()
+    _dev(ks, "ks")
+    if out is None:
+        out = torch.empty(ks.numel(), dtype=col.dtype, device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_quantile(col.handle, ks.data_ptr(), ks.numel(), int(q), 1 if exact else 0, out.data_ptr(),
+                           _stream(stream)), "lc_quantile")
+    return out
+
+
+def lc_decode_approx(col: Column, begin: int = 0, count: int | None = None, out=None, stream=None) -> torch.Tensor:
+    """floor(f(i)) for i in [begin, begin + count): the segments alone, within eps of the keys."""
+    lib = load()
+    if count is None:
+        count = col.n - begin
+    if out is None:
+        out = torch.empty(count, dtype=col.dtype, device="cuda")
+    _dev(out, "out")
+    _check(lib.lc_decode_approx(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream)),
+           "lc_decode_approx")
+    return out
 
 
 def lc_serialize(col: Column) -> bytes:

@@ -109,6 +109,18 @@ def reconstruct(p: dict) -> list:
     return keys
 
 
+def predictions(p: dict) -> list:
+    """floor(f(i)) of every key from the segments alone, in exact Python
+    integers reduced to the key width: icpt_j + floor(M_j t / 2^32)."""
+    mod = 1 << (8 * p["key_bytes"])
+    out = []
+    for j, (c, s, n) in enumerate(segments(p)):
+        icpt = int(p["seg_icpt"][j])
+        M = int(p["seg_slope"][j])
+        out.extend((icpt + ((M * t) >> 32)) % mod for t in range(n))
+    return out
+
+
 def closed_form_size(p: dict) -> int:
     """Sec. II-A size(K^c) = size(f) + residual bits, restated for this format:
     header + chunk directory + per-segment model + packed residual words, with W
