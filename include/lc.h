@@ -195,6 +195,24 @@ int lc_quantile(const lc_column* col, const uint64_t* k_dev, uint64_t m, uint64_
  * lc_decode.  Asynchronous. */
 int lc_decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream);
 
+/* Posting-list AND / OR (Sec. III-A, Fig. 4): the sorted values present in
+ * both lists (lc_intersect) or in either (lc_union), each value once.  A list
+ * is list la of column a (a list-mode column) or, for la < 0, the whole of a
+ * single column; likewise lb of b.  Both sides must have the same key_bytes.
+ * The intersection looks every key of the shorter list up in the longer one
+ * through the longer list's segment intercepts: each segment's key range is
+ * known from its intercept and the next one, so only the one segment that
+ * can hold the key is decoded (segment-level pruning in place of skip
+ * pointers).  The union merges both decoded lists.
+ *   out_dev: cap keys of key_bytes (device).  *count receives the result's
+ *   length; if it exceeds cap, LC_ERR_INVALID_ARG is returned and nothing is
+ *   written.  LC_ERR_OUT_OF_RANGE for a list index past the column's lists,
+ *   LC_ERR_INVALID_ARG for la/lb < 0 on a list-mode column.  Synchronous. */
+int lc_intersect(const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out_dev, uint64_t cap,
+                 uint64_t* count, void* stream);
+int lc_union(const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out_dev, uint64_t cap,
+             uint64_t* count, void* stream);
+
 /* Scalar conveniences (synchronous, legacy default stream). */
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key);
 int lc_lower_bound1(const lc_column* col, uint64_t v, uint64_t* pos);

@@ -502,6 +502,18 @@ int lc_decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void*
     return decode_approx(col, begin, count, out_dev, (cudaStream_t)stream);
 }
 
+int lc_intersect(const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out_dev, uint64_t cap,
+                 uint64_t* count, void* stream) {
+    if (!a || !b || !count) return LC_ERR_INVALID_ARG;
+    return set_op(true, a, la, b, lb, out_dev, cap, count, (cudaStream_t)stream);
+}
+
+int lc_union(const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out_dev, uint64_t cap,
+             uint64_t* count, void* stream) {
+    if (!a || !b || !count) return LC_ERR_INVALID_ARG;
+    return set_op(false, a, la, b, lb, out_dev, cap, count, (cudaStream_t)stream);
+}
+
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key) {
     if (!col || !key) return LC_ERR_INVALID_ARG;
     if (i >= col->N) return LC_ERR_OUT_OF_RANGE;

@@ -176,6 +176,8 @@ int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cud
 int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
 int quantile(const lc_column* col, const uint64_t* ks, uint64_t m, uint64_t q, int exact, void* out, cudaStream_t st);
 int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);
+int set_op(bool is_and, const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out, uint64_t cap,
+           uint64_t* count, cudaStream_t st);
 
 // Serving: one batch of requests over several columns (lc_query.cu).
 int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, uint32_t nqreq, uint64_t nq,

@@ -402,6 +402,8 @@ __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint6
 // (s = slope / 2^32, dx = x - intercept).  A binary search inside the bracket
 // finishes.  Dependent loads: one table entry pair, the intercept run, one
 // 32-byte record, the payload words of the bracket.
+__device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uint64_t x, uint64_t j, uint64_t stream);
+
 template <typename KT>
 __device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x, uint64_t keep, uint64_t stream) {
     if (v.L == 0 || x <= v.kmin) return 0;
@@ -416,6 +418,13 @@ __device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x
         else hi = mid;
     }
     const uint64_t j = lo ? lo - 1 : 0;  // lo >= 1 for sorted keys: icpt[0] = kmin < x
+    return lower_bound_in_segment(v, x, j, stream);
+}
+
+// The first key index of segment j or after it whose key is >= x, given
+// that segment j's intercept is < x: its line brackets the answer (see
+// lower_bound_one), a binary search inside the bracket finishes.
+__device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uint64_t x, uint64_t j, uint64_t stream) {
     const SegRec r = load_rec_hint(v.recs + j, stream);
     const uint64_t ks = r.kstart_w & kKeyMask;
     const uint32_t n = (uint32_t)(r.bit1_n >> 48) + 1u;
@@ -501,6 +510,103 @@ __global__ void __launch_bounds__(256) decode_approx_kernel(ColView v, uint64_t 
             const uint64_t o = o0 + u;
             if (o < count) out[o] = (KT)predict_one(v, begin + o, keep, stream);
         }
+    }
+}
+
+// ------------------------------------------------------------------ posting-list AND / OR (Sec. III-A, Fig. 4)
+//
+// AND: every key x of the shorter list S is looked up in the longer list L by
+// a binary search over L's segment intercepts (each segment's key range
+// starts at its intercept and ends before the next one, so only the one
+// segment that can hold x is touched: segment-level pruning, Fig. 4b) and its
+// line bracket; x is kept iff that key equals x (and x is not a repeat of the
+// key before it in S).  OR: a merge-path merge of both decoded lists, keeping
+// each value once.  Both compact their flags with an exclusive scan.
+
+// The first index in [k0, k1) of list L (segments [s0, s1)) whose key is >= x,
+// or k1.
+template <typename KT>
+__device__ __forceinline__ uint64_t lower_bound_range(const ColView& v, uint64_t x, uint64_t s0, uint64_t s1,
+                                                      uint64_t k0, uint64_t k1, uint64_t keep, uint64_t stream) {
+    uint64_t lo = s0, hi = s1;  // count of the range's intercepts < x
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const uint64_t k = sizeof(KT) == 8 ? ld64_hint((const uint64_t*)v.icpt + mid, keep)
+                                           : (uint64_t)ld32_hint((const uint32_t*)v.icpt + mid, keep);
+        if (k < x) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo == s0) return k0;  // x <= the first key
+    return min(lower_bound_in_segment(v, x, lo - 1, stream), k1);
+}
+
+template <typename KT>
+__global__ void and_flags_kernel(ColView v, const KT* __restrict__ S, uint64_t nS, uint64_t s0, uint64_t s1, uint64_t k0,
+                                 uint64_t k1, uint32_t* __restrict__ flag) {
+    const uint64_t keep = policy_keep(), stream = policy_stream();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nS; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = (uint64_t)S[i];
+        uint32_t f = 0;
+        if (i == 0 || (uint64_t)S[i - 1] != x) {
+            const uint64_t p = lower_bound_range<KT>(v, x, s0, s1, k0, k1, keep, stream);
+            f = p < k1 && access_one(v, p, keep, stream) == x;
+        }
+        flag[i] = f;
+    }
+}
+
+template <typename KT>
+__global__ void scatter_flagged_kernel(const KT* __restrict__ S, uint64_t n, const uint32_t* __restrict__ flag,
+                                       const uint64_t* __restrict__ off, KT* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        if (flag[i]) out[off[i]] = S[i];
+}
+
+constexpr uint32_t kMergeItems = 8;  // merged positions per thread
+
+// Merge path: the number of A elements among the first d of merge(A, B)
+// (ties: A first).
+template <typename KT>
+__device__ __forceinline__ uint64_t merge_split(const KT* A, uint64_t nA, const KT* B, uint64_t nB, uint64_t d) {
+    uint64_t lo = d > nB ? d - nB : 0, hi = min(d, nA);
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d - mid - 1]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Thread t merges positions [8t, 8t + 8): pass 0 counts the values that
+// differ from the merged value before them, pass 1 writes them at off[t].
+template <typename KT>
+__global__ void or_merge_kernel(const KT* __restrict__ A, uint64_t nA, const KT* __restrict__ B, uint64_t nB, int pass,
+                                uint32_t* __restrict__ cnt, const uint64_t* __restrict__ off, KT* __restrict__ out) {
+    const uint64_t total = nA + nB, nt = (total + kMergeItems - 1) / kMergeItems;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < nt; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t d0 = t * kMergeItems, d1 = min(d0 + kMergeItems, total);
+        uint64_t i = merge_split(A, nA, B, nB, d0), j = d0 - i;
+        bool has_prev = d0 > 0;
+        KT prev = 0;
+        if (has_prev) {  // merged[d0 - 1]: the larger of the last A and B elements taken
+            if (i == 0) prev = B[j - 1];
+            else if (j == 0) prev = A[i - 1];
+            else prev = max(A[i - 1], B[j - 1]);
+        }
+        uint64_t o = pass ? off[t] : 0;
+        uint32_t c = 0;
+        for (uint64_t d = d0; d < d1; ++d) {
+            KT x;
+            if (j >= nB || (i < nA && A[i] <= B[j])) x = A[i++];
+            else x = B[j++];
+            if (!has_prev || x != prev) {
+                if (pass) out[o++] = x;
+                ++c;
+            }
+            prev = x;
+            has_prev = true;
+        }
+        if (!pass) cnt[t] = c;
     }
 }
 
@@ -994,6 +1100,95 @@ int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* ou
     }
     note_launch();
     return cuda_status(cudaGetLastError());
+}
+
+// Key and segment ranges of list l of a column (l < 0: the whole single column).
+struct ListRange {
+    uint64_t k0, k1, s0, s1;
+};
+
+static int list_range(const lc_column* col, int64_t l, cudaStream_t st, ListRange* r) {
+    if (l < 0) {
+        if (col->list_mode) return LC_ERR_INVALID_ARG;
+        *r = ListRange{0, col->N, 0, col->L};
+        return LC_OK;
+    }
+    if (!col->list_mode || (uint64_t)l >= col->NL) return LC_ERR_OUT_OF_RANGE;
+    uint64_t kb[2], cb[2], sb[2];
+    int rc = cuda_status(cudaMemcpyAsync(kb, col->blob + col->lay.lkb + 8 * l, 16, cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(cb, col->blob + col->lay.lcb + 8 * l, 16, cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(sb, col->blob + col->lay.csb + 8 * cb[0], 8, cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(sb + 1, col->blob + col->lay.csb + 8 * cb[1], 8, cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    *r = ListRange{kb[0], kb[1], sb[0], sb[1]};
+    return LC_OK;
+}
+
+template <typename KT>
+static int setop_t(bool is_and, const lc_column* a, const ListRange& ra, const lc_column* b, const ListRange& rb,
+                   KT* out, uint64_t cap, uint64_t* count, cudaStream_t st) {
+    const uint64_t nA = ra.k1 - ra.k0, nB = rb.k1 - rb.k0;
+    // AND looks the shorter list up in the longer one
+    const bool swap = is_and && nA > nB;
+    const lc_column* cs = swap ? b : a;
+    const lc_column* cl = swap ? a : b;
+    const ListRange& rs = swap ? rb : ra;
+    const ListRange& rl = swap ? ra : rb;
+    const uint64_t n1 = rs.k1 - rs.k0, n2 = is_and ? 0 : rl.k1 - rl.k0;
+    const uint64_t nflags = is_and ? n1 : (n1 + n2 + kMergeItems - 1) / kMergeItems;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t tmp_b = scan_tmp_bytes(nflags);
+    const size_t o_s = 0, o_l = al(sizeof(KT) * n1), o_f = o_l + al(sizeof(KT) * n2), o_off = o_f + al(4 * nflags),
+                 o_tmp = o_off + al(8 * (nflags + 1));
+    uint8_t* p = nullptr;
+    if (cudaMallocAsync((void**)&p, o_tmp + tmp_b + 16, st) != cudaSuccess) return LC_ERR_NOMEM;
+    KT* S = (KT*)(p + o_s);
+    KT* Lk = (KT*)(p + o_l);
+    uint32_t* flag = (uint32_t*)(p + o_f);
+    uint64_t* off = (uint64_t*)(p + o_off);
+    int rc = decode_range(cs, rs.k0, n1, S, st);
+    if (!rc && !is_and) rc = decode_range(cl, rl.k0, n2, Lk, st);
+    const unsigned grid = (unsigned)std::min<uint64_t>((std::max<uint64_t>(nflags, 1) + 255) / 256, (uint64_t)sm_count() * 16);
+    if (!rc && nflags) {
+        KTime kt(is_and ? "and_probe" : "or_merge", st);
+        if (is_and)
+            and_flags_kernel<KT><<<grid, 256, 0, st>>>(cl->view, S, n1, rl.s0, rl.s1, rl.k0, rl.k1, flag);
+        else
+            or_merge_kernel<KT><<<grid, 256, 0, st>>>(S, n1, Lk, n2, 0, flag, nullptr, nullptr);
+        note_launch();
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (!rc) rc = scan_exclusive(flag, off, nflags, ScanOp::Identity, p + o_tmp, tmp_b, st);
+    uint64_t total = 0;
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(&total, off + nflags, 8, cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    if (!rc) {
+        *count = total;
+        if (total > cap || (total && !out)) rc = LC_ERR_INVALID_ARG;
+    }
+    if (!rc && total) {
+        KTime kt(is_and ? "and_scatter" : "or_merge", st);
+        if (is_and) scatter_flagged_kernel<KT><<<grid, 256, 0, st>>>(S, n1, flag, off, out);
+        else or_merge_kernel<KT><<<grid, 256, 0, st>>>(S, n1, Lk, n2, 1, nullptr, off, out);
+        note_launch();
+        rc = cuda_status(cudaGetLastError());
+    }
+    cudaFreeAsync(p, st);
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int set_op(bool is_and, const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out, uint64_t cap,
+           uint64_t* count, cudaStream_t st) {
+    if (a->key_bytes != b->key_bytes) return LC_ERR_INVALID_ARG;
+    ListRange ra, rb;
+    int rc = list_range(a, la, st, &ra);
+    if (!rc) rc = list_range(b, lb, st, &rb);
+    if (rc) return rc;
+    if (a->key_bytes == 4) return setop_t<uint32_t>(is_and, a, ra, b, rb, (uint32_t*)out, cap, count, st);
+    return setop_t<uint64_t>(is_and, a, ra, b, rb, (uint64_t*)out, cap, count, st);
 }
 
 // ------------------------------------------------------------------ multi-range decode without allocation

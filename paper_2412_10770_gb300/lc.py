@@ -36,7 +36,7 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
-           "lc_quantile", "lc_decode_approx")
+           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -142,6 +142,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_for_free": ([p], None),
         "lc_quantile": ([p, p, u64, u64, i32, p, p], i32),
         "lc_decode_approx": ([p, u64, u64, p, p], i32),
+        "lc_intersect": ([p, ctypes.c_int64, p, ctypes.c_int64, p, u64, pu64, p], i32),
+        "lc_union": ([p, ctypes.c_int64, p, ctypes.c_int64, p, u64, pu64, p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -370,6 +372,32 @@ def lc_decode_approx(col: Column, begin: int = 0, count: int | None = None, out=
     _check(lib.lc_decode_approx(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream)),
            "lc_decode_approx")
     return out
+
+
+def _set_op(name: str, a: Column, la: int, b: Column, lb: int, out, stream) -> torch.Tensor:
+    lib = load()
+    fn = getattr(lib, name)
+    cnt = ctypes.c_uint64()
+    if out is None:
+        # the result's length first (capacity 0), then the call that writes it
+        rc = fn(a.handle, int(la), b.handle, int(lb), None, 0, ctypes.byref(cnt), _stream(stream))
+        if rc not in (LC_OK, LC_ERR_INVALID_ARG) or (rc == LC_ERR_INVALID_ARG and cnt.value == 0):
+            _check(rc, name)
+        out = torch.empty(cnt.value, dtype=a.dtype, device="cuda")
+    _dev(out, "out")
+    _check(fn(a.handle, int(la), b.handle, int(lb), out.data_ptr() if out.numel() else None, out.numel(),
+              ctypes.byref(cnt), _stream(stream)), name)
+    return out[: cnt.value]
+
+
+def lc_intersect(a: Column, b: Column, la: int = -1, lb: int = -1, out=None, stream=None) -> torch.Tensor:
+    """Values in both lists (list la of a, lb of b; -1: the whole single column)."""
+    return _set_op("lc_intersect", a, la, b, lb, out, stream)
+
+
+def lc_union(a: Column, b: Column, la: int = -1, lb: int = -1, out=None, stream=None) -> torch.Tensor:
+    """Values in either list, each once."""
+    return _set_op("lc_union", a, la, b, lb, out, stream)
 
 
 def lc_serialize(col: Column) -> bytes:
