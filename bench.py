@@ -80,6 +80,38 @@ def dist_env():
     return world, rank, local
 
 
+def kernel_sources_sha256() -> str:
+    """Hash of the CUDA sources the kernels are built from (the traffic
+    profile below applies only to exactly these sources)."""
+    import glob
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_2412_10770_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.h")) +
+                    glob.glob(os.path.join(d, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` on the large-column workload, from the
+    committed ncu capture (profiles/traffic_large_column_eps63.json), or None
+    when the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_large_column_eps63.json")
+    try:
+        with open(path) as fh:
+            prof = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if prof.get("source_sha256") != kernel_sources_sha256():
+        return None
+    k = prof.get("kernels", {}).get(kernel)
+    return k["dram_bytes_per_launch"] if k else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -407,10 +439,17 @@ def main():
             "phases": phase_out, "kernels": kernels,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
-                         "ms_per_launch": kernels[dom]["ms_per_launch"], "traffic": None},
+                         "ms_per_launch": kernels[dom]["ms_per_launch"], "traffic": dram_traffic(dom)},
             "ratio": {g: blob_bytes[g] / (N * kb) for g in gens},
             "segments": {g: sizes[g][1] for g in gens},
             "clocks": clocks, "gpu_launches": launches}
+
+    # DRAM bytes actually moved by the dominant kernel (ncu capture of these
+    # sources): the traffic, and the DRAM throughput it implies at the live time
+    tr = line["roofline"]["traffic"]
+    if tr:
+        line["roofline"]["dram_gbs"] = tr / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
+        line["roofline"]["dram_frac"] = line["roofline"]["dram_gbs"] / peak
 
     # the quantile and segments-only rows (Sec. III-C), timed apart from the step
     line["analytics"] = measure_analytics(args, cols, lc, torch, stream, out_dec, out_acc, peak)
@@ -568,7 +607,39 @@ def run_batch(args):
             "batched_over_per_list": value / (skeys / tp),
             "ratio": size / (4 * N), "bits_per_id": 8 * size / N, "segments": segs,
             "tuning": table, "gen_s": t_gen, "tune_s": t_tune, "clocks": clocks, "gpu_launches": launches}
+    line["setops"] = measure_setops(args, ids, begin, eps, log2, lc, torch, stream)
     print(json.dumps(line), flush=True)
+
+
+def measure_setops(args, ids, begin, eps, log2, lc, torch, stream):
+    """AND / OR of list pairs on the batched column (Sec. III-A, Fig. 4): each
+    pair is one of the 1000 longest lists with a random list (the typical
+    short-vs-long AND of a search query).  Host-timed calls through the C ABI
+    (each returns its result length synchronously)."""
+    col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream)
+    lens = np.diff(begin.astype(np.int64))
+    rng = np.random.default_rng(5)
+    longest = np.argsort(lens)[-1000:]
+    P = 500
+    pairs = [(int(rng.choice(longest)), int(rng.integers(0, len(lens)))) for _ in range(P)]
+    cap = int(lens.max()) * 2 + 16
+    out = torch.empty(cap, dtype=torch.uint32, device="cuda")
+    res = {"pairs": P}
+    for name, fn in (("and", lc.lc_intersect), ("or", lc.lc_union)):
+        fn(col, col, pairs[0][0], pairs[0][1], out=out, stream=stream)
+        torch.cuda.synchronize()
+        keys = 0
+        t0 = time.perf_counter()
+        for la, lb in pairs:
+            fn(col, col, la, lb, out=out, stream=stream)
+            keys += int(lens[la] + lens[lb])
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        res[name] = {"us_per_pair": 1e6 * t / P, "input_keys_per_s": keys / t}
+    res["mean_long_list"] = float(np.mean([lens[a] for a, _ in pairs]))
+    res["mean_other_list"] = float(np.mean([lens[b] for _, b in pairs]))
+    col.free()
+    return res
 
 
 def run_sweep(args):
