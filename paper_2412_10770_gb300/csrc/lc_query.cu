@@ -340,6 +340,30 @@ __device__ __forceinline__ uint64_t ld64_hint(const void* ptr, uint64_t pol) {
     asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(ptr), "l"(pol));
     return r;
 }
+__device__ __forceinline__ void st64_hint(void* ptr, uint64_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(ptr), "l"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st32_hint(void* ptr, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(ptr), "r"(v), "l"(pol) : "memory");
+}
+// A query stream element (read once): L2 evict_first, so that streaming the
+// queries and results does not push the shared directories out of L2.
+template <typename T>
+__device__ __forceinline__ uint64_t ld_stream(const T* p, uint64_t pol) {
+    if (sizeof(T) == 8) {
+        uint64_t r;
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+        return r;
+    }
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ void st_stream(T* p, uint64_t v, uint64_t pol) {
+    if (sizeof(T) == 8) st64_hint(p, v, pol);
+    else st32_hint(p, (uint32_t)v, pol);
+}
 __device__ __forceinline__ uint32_t ld32_hint(const void* ptr, uint64_t pol) {
     uint32_t r;
     asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(ptr), "l"(pol));
@@ -383,13 +407,13 @@ template <typename KT>
 __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint64_t m, KT* __restrict__ out) {
     const uint64_t keep = policy_keep(), stream = policy_stream();
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i = idx[q];
+        const uint64_t i = ld_stream(idx + q, stream);
         if (i >= v.N) {
             atomicOr(v.status, kStOutOfRange);
             out[q] = 0;
             continue;
         }
-        out[q] = (KT)access_one(v, i, keep, stream);
+        st_stream(out + q, access_one(v, i, keep, stream), stream);
     }
 }
 
@@ -452,7 +476,7 @@ __global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* _
                                                           uint64_t* __restrict__ out) {
     const uint64_t keep = policy_keep(), stream = policy_stream();
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
-        out[q] = lower_bound_one<KT>(v, (uint64_t)vals[q], keep, stream);
+        st_stream(out + q, lower_bound_one<KT>(v, ld_stream(vals + q, stream), keep, stream), stream);
 }
 
 // ------------------------------------------------------------------ quantiles and segments-only (approximate) keys
