@@ -112,6 +112,29 @@ def dram_traffic(kernel: str):
     return k["dram_bytes_per_launch"] if k else None
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Weak scaling: every rank draws its own columns (seed offset by rank)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(pg, value: float, device: str) -> float:
+    """The job's time is the slowest rank's: an all-reduce MAX of one float
+    (NCCL on the GPUs, gloo in the CPU tests), then a barrier."""
+    if pg is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.barrier()
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, ms: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -290,7 +313,7 @@ def main():
     N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
     cols = []
     for g in gens:
-        seed = inputs.seed_for(2, 1 + GENS.index(g)) + 1000 * rank  # weak scaling: own data per rank
+        seed = rank_seed(inputs.seed_for(2, 1 + GENS.index(g)), rank)  # weak scaling: own data per rank
         k = gen_column(g, N, seed)
         idx = inputs.uniform_ranks(m, N, seed=seed + 1)
         vals = inputs.uniform_values(m, int(k[0]), int(k[-1]), seed=seed + 2)
@@ -370,13 +393,7 @@ def main():
     lc.lc_timing_enable(False)
     ktimes = lc.lc_timing_read()
     clocks = sampler.stop()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    if pg:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-        if pg:
-            pg.barrier()
+    ms = max_over_ranks(pg, t_start.elapsed_time(t_end) / args.steps, "cuda")
 
     # per-phase times (ms, summed over steps and columns)
     ph_ms = {p: 0.0 for p in phases}
@@ -431,7 +448,7 @@ def main():
             kernels[name]["hbm_frac"] = kernels[name]["alg_gbs"] / peak
     dom = max((k for k in kernels if k in kalg), key=lambda k: ktimes[k][1])
     achieved = kernels[dom]["alg_gbs"]
-    value = world * ncols * N / (ms / 1e3)
+    value = job_throughput(world, ncols * N, ms)
 
     line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -457,11 +474,8 @@ def main():
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         e2e = run_e2e(args, cols, lc, torch, stream)
-        if pg:
-            t = torch.tensor([e2e["ms"]], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e["ms"] = float(t.item())
-        line["e2e"] = {"value": world * ncols * N / (e2e["ms"] / 1e3), "unit": "keys/s",
+        e2e["ms"] = max_over_ranks(pg, e2e["ms"], "cuda")
+        line["e2e"] = {"value": job_throughput(world, ncols * N, e2e["ms"]), "unit": "keys/s",
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
