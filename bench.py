@@ -667,7 +667,7 @@ def run_sweep(args):
     import torch
 
     from paper_2412_10770_gb300 import build as lcbuild
-    from paper_2412_10770_gb300 import inputs, lc
+    from paper_2412_10770_gb300 import inputs, lc, tune
 
     lcbuild.build()
     lc.load()
@@ -696,13 +696,23 @@ def run_sweep(args):
     for gi, (g, kw) in enumerate(gens.items()):
         keys = inputs.column_device(g, N, seed=inputs.seed_for(5, 1 + gi), **kw)
         torch.cuda.synchronize()
-        codecs = [("for_bp128", None)] + [("lc", e) for e in eps_list]
+        codecs = [("for_bp128", None)] + [("lc", e) for e in eps_list] + [("lc_partitioned", None)]
+        chunk_costs = {}
         for name, eps in codecs:
             cms = dms = 0.0
             size = segs = None
+            if name == "lc_partitioned":
+                # eps per partition of whole chunks (Sec. IV-A): shortest path over the chunk costs just measured
+                pb, pe, pinfo = tune.partition_eps(keys, tuple(eps_list), chunk_costs=chunk_costs)
             for it in range(args.warmup + args.steps):
                 if name == "lc":
                     col, c_ms = timed(lambda: lc.lc_compress(keys, eps=eps, chunk_log2=16, stream=stream))
+                    _, d_ms = timed(lambda: lc.lc_decode(col, 0, N, out, stream=stream))
+                    size, segs = lc.lc_size(col), col.info["segments"]
+                    if it == 0:
+                        chunk_costs[eps] = lc.lc_chunk_bytes(col)
+                elif name == "lc_partitioned":
+                    col, c_ms = timed(lambda: lc.lc_compress_batch(keys, pb, pe, 16, stream=stream))
                     _, d_ms = timed(lambda: lc.lc_decode(col, 0, N, out, stream=stream))
                     size, segs = lc.lc_size(col), col.info["segments"]
                 else:
@@ -720,6 +730,9 @@ def run_sweep(args):
             tot_keys += 2 * N
             tot_ms += cms + dms
             alg = 8 * N + size
+            if name == "lc_partitioned":
+                eps = {"partitions": pinfo["partitions"], "eps_used": sorted(set(int(e) for e in pe)),
+                       "best_single_eps": pinfo["best_single_eps"]}
             rows.append({"generator": g, "codec": name, "eps": eps, "ratio": size / (8 * N),
                          "bits_per_key": 8 * size / N, "segments": segs,
                          "compress_ms": cms, "compress_keys_per_s": N / (cms / 1e3),
@@ -730,7 +743,7 @@ def run_sweep(args):
         del keys
         torch.cuda.empty_cache()
     clocks = sampler.stop()
-    lcrows = [r for r in rows if r["codec"] == "lc"]
+    lcrows = [r for r in rows if r["codec"].startswith("lc")]
     best = max(lcrows, key=lambda r: r["decode_hbm_frac"])
     line = {"metric": METRIC, "value": tot_keys / (tot_ms / 1e3), "unit": "keys/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,

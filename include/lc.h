@@ -213,6 +213,13 @@ int lc_intersect(const lc_column* a, int64_t la, const lc_column* b, int64_t lb,
 int lc_union(const lc_column* a, int64_t la, const lc_column* b, int64_t lb, void* out_dev, uint64_t cap,
              uint64_t* count, void* stream);
 
+/* Per-chunk cost of a column (Sec. II-A size of the model and residuals,
+ * restated per chunk): out_host[c] = segments_c (key_bytes + 15) + 8 words_c
+ * + 24, the bytes chunk c adds to K^c (its segments, payload words and chunk
+ * directory entries; alignment padding excluded).  cap >= C entries (host
+ * memory).  Used to choose eps per partition (Sec. IV-A).  Synchronous. */
+int lc_chunk_bytes(const lc_column* col, uint64_t* out_host, uint64_t cap);
+
 /* Scalar conveniences (synchronous, legacy default stream). */
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key);
 int lc_lower_bound1(const lc_column* col, uint64_t v, uint64_t* pos);

@@ -514,6 +514,20 @@ int lc_union(const lc_column* a, int64_t la, const lc_column* b, int64_t lb, voi
     return set_op(false, a, la, b, lb, out_dev, cap, count, (cudaStream_t)stream);
 }
 
+int lc_chunk_bytes(const lc_column* col, uint64_t* out_host, uint64_t cap) {
+    if (!col || (col->C && !out_host)) return LC_ERR_INVALID_ARG;
+    if (cap < col->C) return LC_ERR_INVALID_ARG;
+    if (col->C == 0) return LC_OK;
+    std::vector<uint64_t> csb(col->C + 1), cwb(col->C + 1);
+    int rc = cuda_status(cudaMemcpy(csb.data(), col->blob + col->lay.csb, 8 * (col->C + 1), cudaMemcpyDeviceToHost));
+    if (!rc) rc = cuda_status(cudaMemcpy(cwb.data(), col->blob + col->lay.cwb, 8 * (col->C + 1), cudaMemcpyDeviceToHost));
+    if (rc) return rc;
+    const uint64_t seg_bytes = (uint64_t)col->key_bytes + 8 + 4 + 2 + 1;  // icpt, slope, bitoff, start, width
+    for (uint64_t c = 0; c < col->C; ++c)
+        out_host[c] = (csb[c + 1] - csb[c]) * seg_bytes + 8 * (cwb[c + 1] - cwb[c]) + 24;  // + 3 directory entries
+    return LC_OK;
+}
+
 int lc_access1(const lc_column* col, uint64_t i, uint64_t* key) {
     if (!col || !key) return LC_ERR_INVALID_ARG;
     if (i >= col->N) return LC_ERR_OUT_OF_RANGE;

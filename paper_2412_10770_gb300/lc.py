@@ -36,7 +36,7 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
-           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union")
+           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -144,6 +144,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_decode_approx": ([p, u64, u64, p, p], i32),
         "lc_intersect": ([p, ctypes.c_int64, p, ctypes.c_int64, p, u64, pu64, p], i32),
         "lc_union": ([p, ctypes.c_int64, p, ctypes.c_int64, p, u64, pu64, p], i32),
+        "lc_chunk_bytes": ([p, p, u64], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -398,6 +399,14 @@ def lc_intersect(a: Column, b: Column, la: int = -1, lb: int = -1, out=None, str
 def lc_union(a: Column, b: Column, la: int = -1, lb: int = -1, out=None, stream=None) -> torch.Tensor:
     """Values in either list, each once."""
     return _set_op("lc_union", a, la, b, lb, out, stream)
+
+
+def lc_chunk_bytes(col: Column) -> np.ndarray:
+    """Bytes each chunk adds to K^c (segments, payload words, directory entries)."""
+    C = col.info["chunks"]
+    out = np.zeros(max(C, 1), dtype=np.uint64)
+    _check(load().lc_chunk_bytes(col.handle, out.ctypes.data, out.size), "lc_chunk_bytes")
+    return out[:C]
 
 
 def lc_serialize(col: Column) -> bytes:

@@ -105,3 +105,73 @@ def tune(ids: torch.Tensor, begin: np.ndarray, sample_lists: int = 24, sample_ke
     for t in table:
         t["bittuner_eps"] = math.sqrt(2 * math.log(2) * t["gap_var"] * C * (K + 2 * F)) if t["gap_var"] > 0 else 0.0
     return eps_of, log2_of, {"buckets": table, "bittuner_C": C, "K": K, "F": F}
+
+
+# ---------------------------------------------------------------- eps per partition (Sec. IV-A, Fig. 5)
+
+# Bytes one more partition adds: its list directory entries (key begin, chunk
+# begin, eps, chunk_log2).
+PART_OVERHEAD = 8 + 8 + 8 + 1
+
+
+def best_partition(costs: np.ndarray, switch: float = PART_OVERHEAD):
+    """The shortest path of the partition graph (Sec. IV-A, Fig. 5) at chunk
+    granularity.  costs[e, c] = bytes of chunk c compressed with candidate e.
+    Chunks are independent in the format, so a partition's cost is the sum of
+    its chunks' costs under its eps, plus `switch` per partition; the best
+    partitioning is a shortest path over the states (chunk, eps), solved by
+    dynamic programming in O(E C).  Returns (choice[c] = candidate index of
+    chunk c, total cost)."""
+    E, C = costs.shape
+    if C == 0:
+        return np.zeros(0, dtype=np.int64), 0.0
+    D = costs[:, 0].astype(np.float64) + switch
+    back = np.zeros((C, E), dtype=np.int64)
+    back[0] = np.arange(E)
+    idx = np.arange(E)
+    for c in range(1, C):
+        a = int(np.argmin(D))
+        new = D[a] + switch
+        stay = D <= new  # continuing the partition beats opening a new one
+        back[c] = np.where(stay, idx, a)
+        D = np.where(stay, D, new) + costs[:, c]
+    e = int(np.argmin(D))
+    total = float(D[e])
+    choice = np.empty(C, dtype=np.int64)
+    for c in range(C - 1, -1, -1):
+        choice[c] = e
+        e = int(back[c, e])
+    return choice, total
+
+
+def partition_eps(keys: torch.Tensor, eps_candidates=(0, 1, 3, 7, 15, 31, 63, 127, 255, 511, 1023), chunk_log2: int = 16,
+                  switch: float = PART_OVERHEAD, chunk_costs=None):
+    """eps per partition of one sorted column (Sec. IV-A): compress the column
+    once per candidate eps on the GPU, read every chunk's cost
+    (lc_chunk_bytes), take the shortest path of best_partition, and return
+    (part_begin uint64[P+1] key offsets, part_eps uint64[P], info).  The
+    partitions are whole chunks; lc_compress_batch(keys, part_begin,
+    part_eps, chunk_log2) stores them as one list-mode column.  chunk_costs:
+    an optional {eps: per-chunk bytes} already measured."""
+    n = keys.numel()
+    cs = 1 << chunk_log2
+    costs = []
+    for e in eps_candidates:
+        if chunk_costs is not None and e in chunk_costs:
+            costs.append(np.asarray(chunk_costs[e], dtype=np.float64))
+            continue
+        col = lc.lc_compress(keys, eps=int(e), chunk_log2=chunk_log2)
+        try:
+            costs.append(lc.lc_chunk_bytes(col).astype(np.float64))
+        finally:
+            col.free()
+    costs = np.stack(costs)
+    choice, total = best_partition(costs, switch)
+    C = costs.shape[1]
+    starts = [0] + [c for c in range(1, C) if choice[c] != choice[c - 1]]
+    part_begin = np.array([min(n, s * cs) for s in starts] + [n], dtype=np.uint64)
+    part_eps = np.array([eps_candidates[choice[s]] for s in starts], dtype=np.uint64)
+    single = costs.sum(axis=1)
+    info = {"partitions": len(starts), "dp_bytes": total, "best_single_eps": int(eps_candidates[int(np.argmin(single))]),
+            "best_single_bytes": float(single.min())}
+    return part_begin, part_eps, info

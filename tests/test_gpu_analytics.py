@@ -101,3 +101,40 @@ def test_full_size_column_segments_only():
     idx = np.array([oracle.quantile_index(n, int(k), 1000) for k in ks])
     assert np.array_equal(lc.lc_quantile(col, dev(ks), 1000).cpu().numpy(), keys[idx])
     col.free()
+
+
+def _mixed_column(seed: int) -> np.ndarray:
+    """Consecutive regimes of whole chunks from different generators (a column
+    whose best eps changes along the keys)."""
+    parts, base = [], np.uint64(0)
+    gens = [lambda n, s: inputs.uniform_gaps(n, s, dtype=np.uint64),
+            lambda n, s: inputs.clusters(n, s),
+            lambda n, s: inputs.lognormal_gaps(n, s, mu=3.0, sigma=2.0),
+            lambda n, s: inputs.piecewise_linear(n, s)]
+    for r in range(8):
+        k = gens[r % 4](3 * 65536, seed + r)
+        k = k - k[0] + base + np.uint64(1)
+        parts.append(k)
+        base = k[-1]
+    return np.concatenate(parts)
+
+
+def test_eps_per_partition_column():
+    """Sec. IV-A: eps chosen per partition of whole chunks by the shortest path
+    over measured chunk costs; stored as a list-mode column that equals the
+    oracle's bytes, decodes exactly and is no larger than the best single eps."""
+    from paper_2412_10770_gb300 import tune
+
+    keys = _mixed_column(5)
+    dk = dev(keys)
+    cands = (0, 1, 3, 15, 63, 255, 1023)
+    pb, pe, info = tune.partition_eps(dk, cands)
+    assert pb[0] == 0 and pb[-1] == keys.size and info["partitions"] >= 2
+    col = lc.lc_compress_batch(dk, pb, pe, 16)
+    blob = lc.lc_serialize(col)
+    assert blob == oracle.compress_lists(keys, pb, pe, np.full(pe.size, 16, np.uint8))
+    assert torch.equal(lc.lc_decode(col), dk)
+    single = lc.lc_compress(dk, eps=info["best_single_eps"])
+    assert lc.lc_size(col) <= lc.lc_size(single)
+    single.free()
+    col.free()
