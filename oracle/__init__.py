@@ -64,6 +64,8 @@ def bind(path: str) -> ctypes.CDLL:
     pu64 = ctypes.POINTER(ctypes.c_uint64)
     lib.lco_compress.argtypes = [p, u64, ctypes.c_int, u64, ctypes.c_int, pp, pu64]
     lib.lco_compress_lists.argtypes = [p, p, u64, ctypes.c_int, p, p, pp, pu64]
+    lib.lco_compress_jump.argtypes = [p, u64, ctypes.c_int, u64, ctypes.c_int, pp, pu64]
+    lib.lco_compress_jump.restype = ctypes.c_int
     lib.lco_info.argtypes = [p, u64, pu64, ctypes.POINTER(ctypes.c_int), pu64, pu64, pu64]
     lib.lco_decode.argtypes = [p, u64, p]
     lib.lco_access.argtypes = [p, u64, p, u64, p]
@@ -114,6 +116,16 @@ def compress(keys, eps: int, chunk_log2: int = 16) -> bytes:
     blob, n = ctypes.c_void_p(), ctypes.c_uint64()
     _check(_L().lco_compress(a.ctypes.data, a.size, a.itemsize, int(eps), int(chunk_log2),
                              ctypes.byref(blob), ctypes.byref(n)))
+    return _take_blob(blob, n.value)
+
+
+def compress_jump(keys, eps: int, chunk_log2: int = 16) -> bytes:
+    """K^c of one sorted column with the jump fit (fewest segments among greedy
+    prefixes, see lc_oracle.h)."""
+    a = _keys_array(keys)
+    blob, n = ctypes.c_void_p(), ctypes.c_uint64()
+    _check(_L().lco_compress_jump(a.ctypes.data, a.size, a.itemsize, int(eps), int(chunk_log2),
+                                  ctypes.byref(blob), ctypes.byref(n)))
     return _take_blob(blob, n.value)
 
 

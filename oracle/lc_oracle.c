@@ -131,16 +131,27 @@ static int close_segment(const uint64_t* K, uint64_t s, uint64_t n, i128 LO, i12
     return segvec_push(out, g);
 }
 
+/* The integer Q32 slopes key i admits in the segment anchored at s:
+ * [lo, hi] with D - eps <= floor(M d / 2^32) <= D + eps (Def. 2),
+ * d = i - s, D = K[i] - K[s]. */
+static void key_bounds(const uint64_t* K, uint64_t s, uint64_t i, uint64_t eps, i128* lo_out, i128* hi_out)
+{
+    i128 d = (i128)(i - s);
+    i128 D = (i128)(K[i] - K[s]);
+    i128 lo = ceil_div((D - (i128)eps) * TWO32, d);
+    i128 hi = floor_div((D + (i128)eps + 1) * TWO32 - 1, d);
+    *lo_out = lo;
+    *hi_out = hi;
+}
+
 /* Greedy shrinking-cone eps-PLA over the keys K[b, e) of one chunk. */
 static int fit_chunk(const uint64_t* K, uint64_t b, uint64_t e, uint64_t eps, segvec* out)
 {
     uint64_t s = b;
     i128 LO = INT64_MIN, HI = INT64_MAX;
     for (uint64_t i = b + 1; i < e; i++) {
-        i128 d = (i128)(i - s);
-        i128 D = (i128)(K[i] - K[s]);
-        i128 lo = ceil_div((D - (i128)eps) * TWO32, d);
-        i128 hi = floor_div((D + (i128)eps + 1) * TWO32 - 1, d);
+        i128 lo, hi;
+        key_bounds(K, s, i, eps, &lo, &hi);
         i128 nlo = LO > lo ? LO : lo;
         i128 nhi = HI < hi ? HI : hi;
         if (nlo <= nhi) {
@@ -157,9 +168,100 @@ static int fit_chunk(const uint64_t* K, uint64_t b, uint64_t e, uint64_t eps, se
     return close_segment(K, s, e - s, LO, HI, eps, out);
 }
 
+/* The integer cone [LO, HI] of the keys K[s+1, s+n) anchored at s: the
+ * intersection of every key's admissible Q32 slopes (Def. 2). */
+static void cone_of(const uint64_t* K, uint64_t s, uint64_t n, uint64_t eps, i128* LO_out, i128* HI_out)
+{
+    i128 LO = INT64_MIN, HI = INT64_MAX;
+    for (uint64_t i = s + 1; i < s + n; i++) {
+        i128 lo, hi;
+        key_bounds(K, s, i, eps, &lo, &hi);
+        if (lo > LO) LO = lo;
+        if (hi < HI) HI = hi;
+    }
+    *LO_out = LO;
+    *HI_out = HI;
+}
+
+/* The greedy's next anchor from p inside the chunk [b, e): the first key that
+ * empties the cone anchored at p, or e. */
+static uint64_t greedy_next(const uint64_t* K, uint64_t p, uint64_t e, uint64_t eps)
+{
+    i128 LO = INT64_MIN, HI = INT64_MAX;
+    for (uint64_t i = p + 1; i < e; i++) {
+        i128 lo, hi;
+        key_bounds(K, p, i, eps, &lo, &hi);
+        if (lo > LO) LO = lo;
+        if (hi < HI) HI = hi;
+        if (LO > HI) return i;
+    }
+    return e;
+}
+
+#define JUMP_H 96u            /* segments of at most this many keys take part in the jump */
+#define JUMP_LONG UINT64_MAX  /* the greedy segment from p has more than JUMP_H keys */
+
+/* The "jump" fit of one chunk, aiming at Sec. II-A's objective (the fewest
+ * segments, which O'Rourke's algorithm reaches for free lines) within anchored
+ * segments that are greedy prefixes.  r(p) = the greedy's next anchor from p
+ * when that segment has at most JUMP_H keys, else JUMP_LONG.  From the anchor
+ * a, the segment ends at the position in (a, r(a)] whose own r reaches
+ * farthest (JUMP_LONG counts as farthest; ties: the first such position): the
+ * jump-game choice, optimal when every segment is short.  A segment from an
+ * anchor with r(a) = JUMP_LONG is the greedy's long segment.  The chunk keeps
+ * this segmentation only if it has fewer segments than the greedy's. */
+static int fit_chunk_jump(const uint64_t* K, uint64_t b, uint64_t e, uint64_t eps, segvec* out)
+{
+    const uint64_t n = e - b;
+    uint64_t* r = (uint64_t*)malloc((n ? n : 1) * sizeof(uint64_t));
+    if (!r) return LCO_ERR_NOMEM;
+    for (uint64_t p = b; p < e; p++) {
+        uint64_t nx = greedy_next(K, p, e, eps);
+        r[p - b] = nx - p <= JUMP_H ? nx : JUMP_LONG;
+    }
+    int rc = LCO_OK;
+    /* the jump segmentation into its own list first: the chunk keeps it only
+     * if it has fewer segments than the greedy's (ties: the greedy) */
+    segvec jump = {0, 0, 0};
+    uint64_t a = b;
+    while (a < e && !rc) {
+        uint64_t nx;
+        if (r[a - b] == JUMP_LONG) {
+            nx = greedy_next(K, a, e, eps);
+        } else if (r[a - b] == e) {
+            nx = e;
+        } else {
+            uint64_t best = a + 1, bk = r[a + 1 - b];
+            for (uint64_t q = a + 2; q <= r[a - b]; q++)
+                if (r[q - b] > bk) {
+                    bk = r[q - b];
+                    best = q;
+                }
+            nx = best;
+        }
+        i128 LO, HI;
+        cone_of(K, a, nx - a, eps, &LO, &HI);
+        rc = close_segment(K, a, nx - a, LO, HI, eps, &jump);
+        a = nx;
+    }
+    free(r);
+    if (!rc) {
+        const uint64_t n0 = out->n;
+        rc = fit_chunk(K, b, e, eps, out);
+        if (!rc && jump.n < out->n - n0) {
+            out->n = n0;
+            for (uint64_t j = 0; j < jump.n && !rc; j++) rc = segvec_push(out, jump.v[j]);
+        }
+    }
+    free(jump.v);
+    return rc;
+}
+
 typedef struct {
     uint64_t key_begin, key_end, eps;
 } ochunk;
+
+static int g_fit_jump = 0; /* encode(): 0 the greedy fit, 1 the jump fit */
 
 /* Shared back end of both entry points: chunks -> segments -> bytes. */
 static int encode(const uint64_t* K, uint64_t N, int kb, const ochunk* ch, uint64_t C,
@@ -179,7 +281,8 @@ static int encode(const uint64_t* K, uint64_t N, int kb, const ochunk* ch, uint6
     /* 1. fit every chunk, then lay out its residual bits */
     for (uint64_t c = 0; c < C; c++) {
         csb[c] = segs.n;
-        rc = fit_chunk(K, ch[c].key_begin, ch[c].key_end, ch[c].eps, &segs);
+        rc = g_fit_jump ? fit_chunk_jump(K, ch[c].key_begin, ch[c].key_end, ch[c].eps, &segs)
+                        : fit_chunk(K, ch[c].key_begin, ch[c].key_end, ch[c].eps, &segs);
         if (rc) goto done;
         uint64_t bits = 0;
         for (uint64_t j = csb[c]; j < segs.n; j++) {
@@ -312,6 +415,15 @@ int lco_compress(const void* keys, uint64_t n, int key_bytes, uint64_t eps, int 
                     NULL, 0, blob, len);
     free(ch);
     free(K);
+    return rc;
+}
+
+int lco_compress_jump(const void* keys, uint64_t n, int key_bytes, uint64_t eps, int chunk_log2,
+                      uint8_t** blob, uint64_t* len)
+{
+    g_fit_jump = 1;
+    int rc = lco_compress(keys, n, key_bytes, eps, chunk_log2, blob, len);
+    g_fit_jump = 0;
     return rc;
 }
 

@@ -81,6 +81,18 @@ enum {
 int lco_compress(const void* keys, uint64_t n, int key_bytes, uint64_t eps,
                  int chunk_log2, uint8_t** blob, uint64_t* len);
 
+/* The same with the "jump" fit in place of the greedy (fewest anchored
+ * segments among greedy prefixes; optimal when no segment exceeds 96 keys,
+ * Sec. II-A's objective): from anchor a, with r(p) = the greedy's next anchor
+ * from p if that segment has <= 96 keys (else "long"), the next anchor is the
+ * position in (a, r(a)] whose r reaches farthest (long = farthest; ties: the
+ * first); an anchor whose own segment is long takes the greedy segment.  A
+ * chunk keeps this segmentation only if it has fewer segments than the
+ * greedy's (ties: the greedy).  Slopes, widths and bytes follow as for the
+ * greedy.  Not thread-safe. */
+int lco_compress_jump(const void* keys, uint64_t n, int key_bytes, uint64_t eps,
+                      int chunk_log2, uint8_t** blob, uint64_t* len);
+
 /* Compress nlists sorted lists stored back to back in keys.  list_begin has
  * nlists+1 entries (list l is keys[list_begin[l], list_begin[l+1])), eps and
  * chunk_log2 one entry per list. */

@@ -36,6 +36,12 @@ MUTANTS = {
     "chunks_do_not_restart": ("ch[c].key_end = (c + 1) * cs < n ? (c + 1) * cs : n;",
                               "ch[c].key_end = n;"),
 }
+# mistakes planted in the jump fit (fewest segments)
+MUTANTS.update({
+    "jump_takes_the_greedy_anchor": ("            nx = best;\n", "            nx = r[a - b];\n"),
+    "jump_picks_the_nearest_reach": ("                if (r[q - b] > bk) {", "                if (r[q - b] < bk) {"),
+})
+JUMP_MUTANTS = {"jump_takes_the_greedy_anchor", "jump_picks_the_nearest_reach"}
 # mistakes planted in the FOR-delta bp128 baseline's reference (for_bp128.c)
 FOR_MUTANTS = {
     "for_first_gap_not_zero": ("if (i == 0 || k >= n) return 0;", "if (k == 0 || k >= n) return 0;"),
@@ -57,6 +63,13 @@ def _pin_suite():
         blob = oracle.compress(keys, eps, 8)
         assert np.array_equal(oracle.decode(blob), keys)
         check_invariants(keys, eps, blob)
+
+
+def _jump_pin_suite():
+    from test_jump_pins import _jump_cases, test_jump_reaches_the_anchored_optimum_on_short_segments
+
+    for case in range(len(_jump_cases())):
+        test_jump_reaches_the_anchored_optimum_on_short_segments(case)
 
 
 def _for_pin_suite():
@@ -82,7 +95,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
     if name in MUTANTS:
         old, new = MUTANTS[name]
         assert lc_src.count(old) == 1, f"mutation site for {name} not found exactly once"
-        lc_src, suite = lc_src.replace(old, new), _pin_suite
+        lc_src, suite = lc_src.replace(old, new), (_jump_pin_suite if name in JUMP_MUTANTS else _pin_suite)
     else:
         old, new = FOR_MUTANTS[name]
         assert for_src.count(old) == 1, f"mutation site for {name} not found exactly once"
