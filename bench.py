@@ -696,7 +696,8 @@ def run_sweep(args):
     for gi, (g, kw) in enumerate(gens.items()):
         keys = inputs.column_device(g, N, seed=inputs.seed_for(5, 1 + gi), **kw)
         torch.cuda.synchronize()
-        codecs = [("for_bp128", None)] + [("lc", e) for e in eps_list] + [("lc_partitioned", None)]
+        codecs = ([("for_bp128", None)] + [("lc", e) for e in eps_list] + [("lc_partitioned", None)] +
+                  [("lc_jump", e) for e in eps_list])
         chunk_costs = {}
         for name, eps in codecs:
             cms = dms = 0.0
@@ -711,6 +712,10 @@ def run_sweep(args):
                     size, segs = lc.lc_size(col), col.info["segments"]
                     if it == 0:
                         chunk_costs[eps] = lc.lc_chunk_bytes(col)
+                elif name == "lc_jump":
+                    col, c_ms = timed(lambda: lc.lc_compress_jump(keys, eps=eps, chunk_log2=16, stream=stream))
+                    _, d_ms = timed(lambda: lc.lc_decode(col, 0, N, out, stream=stream))
+                    size, segs = lc.lc_size(col), col.info["segments"]
                 elif name == "lc_partitioned":
                     col, c_ms = timed(lambda: lc.lc_compress_batch(keys, pb, pe, 16, stream=stream))
                     _, d_ms = timed(lambda: lc.lc_decode(col, 0, N, out, stream=stream))

@@ -101,6 +101,22 @@ typedef struct {
 int lc_compress(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params,
                 void* stream, lc_column** out);
 
+/* lc_compress with the "jump" fit in place of the greedy, aiming at Sec.
+ * II-A's objective of the fewest segments (the one O'Rourke's algorithm
+ * reaches for free lines).  Every feasible anchored segment is a prefix of the
+ * greedy one from its anchor, so with r(p) = the greedy's next anchor from p
+ * (taken up to 96 keys; "long" beyond), the segment from anchor a ends at the
+ * position in (a, r(a)] whose own r reaches farthest (long counts as
+ * farthest; ties: the first position): the fewest segments whenever no
+ * segment exceeds 96 keys.  An anchor whose greedy segment is long keeps that
+ * segment, and a chunk keeps the jump segmentation only if it has fewer
+ * segments than the greedy's, so a column never has more.  Slopes, widths and
+ * the byte format are those of lc_compress; every query works unchanged.
+ * Same arguments, errors and synchronisation as lc_compress; costs one more
+ * walk of up to 96 keys per key. */
+int lc_compress_jump(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params,
+                     void* stream, lc_column** out);
+
 /* K^c of many sorted lists stored back to back (inverted-index posting lists,
  * Sec. III-A).  ids_dev: all keys, device memory.  list_begin: nlists+1
  * non-decreasing offsets (host memory), list l is ids[list_begin[l],

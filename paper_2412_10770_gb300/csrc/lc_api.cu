@@ -278,8 +278,21 @@ void lc_free(lc_column* col) {
     delete col;
 }
 
+static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
+                           lc_column** out, bool jump);
+
 int lc_compress(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
                 lc_column** out) {
+    return compress_column(keys_dev, n, key_bytes, params, stream, out, false);
+}
+
+int lc_compress_jump(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
+                     lc_column** out) {
+    return compress_column(keys_dev, n, key_bytes, params, stream, out, true);
+}
+
+static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
+                           lc_column** out, bool jump) {
     if (!out || (n && !keys_dev)) return LC_ERR_INVALID_ARG;
     *out = nullptr;
     if (key_bytes != 4 && key_bytes != 8) return LC_ERR_INVALID_ARG;
@@ -317,7 +330,7 @@ int lc_compress(const void* keys_dev, uint64_t n, int key_bytes, const lc_params
             ch[c].pad = 0;
             bound += bound_words(ch[c].n, eps);
         }
-        rc = compress_impl(keys_dev, key_bytes, ch.data(), col->C, col->C * (cs / 32), bound, st, col);
+        rc = compress_impl(keys_dev, key_bytes, ch.data(), col->C, col->C * (cs / 32), bound, st, col, jump);
     }
     if (!rc) rc = finish_column(col, st, nullptr, nullptr, nullptr, nullptr);
     if (rc) { lc_free(col); return rc; }

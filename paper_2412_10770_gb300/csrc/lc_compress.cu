@@ -490,6 +490,154 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
     if (lane == 0) counts[c] = total;
 }
 
+// ------------------------------------------------------------------ the jump fit (fewest segments)
+//
+// Sec. II-A fits with the fewest segments.  Every feasible anchored segment is
+// a prefix of the greedy one from its anchor, so the fewest segments follow
+// from each position's greedy reach r(p) by the jump-game choice: from anchor
+// a, end the segment at the position in (a, r(a)] whose own reach is
+// farthest.  Reaches are taken up to kShortMax keys (r(p) "long" beyond; a
+// long reach counts as farthest, ties go to the first position), a long
+// segment is walked as by the greedy, and a chunk keeps the jump segmentation
+// only if it has fewer segments than the greedy's.
+
+// reach_kernel: one CTA per 8192-key window, keys [w0, w1 + 96] staged as
+// 32-bit offsets; r_off[p] = r(p) - p in 1..96, or 0 when the greedy segment
+// from p is longer than 96 keys.  One thread per position.
+template <typename KT>
+__global__ void __launch_bounds__(kShortThreads)
+reach_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
+             uint8_t* __restrict__ roff) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const WinDesc wd = wins[blockIdx.x];
+    const ChunkDesc cd = chunks[wd.chunk];
+    const KT* __restrict__ K = keys + cd.key_begin;
+    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
+    const int64_t eps = cd.eps;
+    const uint32_t top = min(n, w1 + kShortMax + 1);
+    uint32_t* s = (uint32_t*)smem;
+    const uint64_t kbase = (uint64_t)__ldg(K + w0);
+#pragma unroll 4
+    for (uint32_t q = threadIdx.x; q < top - w0; q += kShortThreads)
+        s[q + (q >> 5)] = (uint32_t)((uint64_t)__ldg(K + w0 + q) - kbase);
+    __syncthreads();
+    const Staged<uint32_t> st{s, w0};
+    const uint32_t iters = (w1 - w0 + kShortThreads - 1) / kShortThreads;  // the same for every thread
+    for (uint32_t it = 0; it < iters; ++it) {
+        const uint32_t p = w0 + threadIdx.x + it * kShortThreads;
+        const bool active = p < w1;
+        const uint32_t lim = active ? min(n, p + kShortMax + 1) : p + 1;
+        const uint64_t span = active ? (uint64_t)__ldg(K + lim - 1) - (uint64_t)__ldg(K + p) : 0;
+        const bool narrow = __all_sync(0xFFFFFFFFu, span + (uint64_t)eps + 1 < (1ull << 31));
+        if (!active) continue;
+        uint32_t i = p + 1;
+        if (narrow) {
+            const uint32_t kx = (uint32_t)st(p);
+            int32_t X = INT32_MIN;
+            uint32_t E = 1u, Y = 0x7FFFFFFFu, F = 1u;
+            const int32_t e32 = (int32_t)eps;
+            for (; i < lim; ++i) {
+                const uint32_t D = (uint32_t)st(i) - kx, d = i - p;
+                const int32_t xl = (int32_t)D - e32;
+                const uint32_t yh = D + (uint32_t)e32 + 1u;
+                if ((int64_t)xl * E > (int64_t)X * d) { X = xl; E = d; }
+                if ((uint64_t)yh * F < (uint64_t)Y * d) { Y = yh; F = d; }
+                if (X >= 0 && (uint64_t)(uint32_t)X * F >= (uint64_t)Y * E) break;
+            }
+        } else {
+            const uint64_t kx = (uint64_t)__ldg(K + p);
+            Frac c = frac_open();
+            for (; i < lim; ++i)
+                if (!frac_step((uint64_t)__ldg(K + i) - kx, i - p, eps, c)) break;
+        }
+        // i: the first key that empties the cone, or lim (the chunk's end, or 97 keys on)
+        roff[cd.key_begin + p] = (uint8_t)(i - p <= kShortMax ? i - p : 0u);
+    }
+}
+
+// jump_kernel: one warp per chunk; the reaches of 256 positions at a time sit
+// in the lanes (8 bytes each).  Writes the jump segmentation's anchor bits and
+// long-segment records to scratch, then replaces the greedy's for the chunk
+// when it has fewer segments.
+template <typename KT>
+__global__ void __launch_bounds__(kChainThreads, 6)
+jump_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, uint64_t C,
+            const uint8_t* __restrict__ roff, uint32_t* __restrict__ tbits, uint32_t* __restrict__ counts,
+            LongInfo* __restrict__ longinfo, uint32_t* __restrict__ jbits, LongInfo* __restrict__ jlong) {
+    const uint64_t c = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= C) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const ChunkDesc cd = chunks[c];
+    const KT* __restrict__ K = keys + cd.key_begin;
+    const uint8_t* __restrict__ R = roff + cd.key_begin;
+    const uint32_t n = cd.n, nblk = (n + kFB - 1) / kFB;
+    const int64_t eps = cd.eps;
+    const uint64_t gb = cd.bitword_begin;
+    uint32_t* __restrict__ J = jbits + gb;
+    const uint64_t* __restrict__ magic = g_magic;
+    for (uint32_t q = lane; q < nblk; q += 32) J[q] = 0;
+    __syncwarp();
+    auto load_win = [&](uint32_t base) {
+        uint64_t v = 0;
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) {
+            const uint32_t q = base + 8 * lane + u;
+            v |= (uint64_t)(q < n ? R[q] : 0) << (8 * u);
+        }
+        return v;
+    };
+    uint32_t base = 0;
+    uint64_t win = load_win(0);
+    uint32_t a = 0, cnt = 0;
+    while (a < n) {
+        ++cnt;
+        if (lane == 0) J[a >> 5] |= 1u << (a & 31u);
+        if (a + kShortMax >= base + 256) {  // the window must hold positions a .. a + 96
+            base = a;
+            win = load_win(base);
+        }
+        const uint32_t oa = a - base;
+        const uint32_t ra = (uint32_t)(__shfl_sync(0xFFFFFFFFu, win, oa >> 3) >> (8 * (oa & 7u))) & 0xFFu;
+        uint32_t nx;
+        if (ra == 0) {  // the greedy segment from a is long: walk it
+            Frac f;
+            nx = warp_walk(K, a, n, eps, lane, &f);
+            if (lane == 0) jlong[gb + (a >> 5)] = LongInfo{frac_slope(f, magic), nx, 0u};
+        } else if (a + ra >= n) {
+            nx = n;
+        } else {
+            // the candidate in (a, a + ra] that reaches farthest (long: farthest; ties: the first)
+            const uint32_t hi = a + ra;
+            uint32_t bv = 0, bq = 0xFFFFFFFFu;
+#pragma unroll
+            for (uint32_t u = 0; u < 8; ++u) {
+                const uint32_t q = base + 8 * lane + u;
+                if (q > a && q <= hi) {
+                    const uint32_t r = (uint32_t)(win >> (8 * u)) & 0xFFu;
+                    const uint32_t v = r ? q + r : 0xFFFFFFFFu;
+                    if (v > bv) {
+                        bv = v;
+                        bq = q;
+                    }
+                }
+            }
+            const uint32_t mv = __reduce_max_sync(0xFFFFFFFFu, bv);
+            nx = __reduce_min_sync(0xFFFFFFFFu, bv == mv ? bq : 0xFFFFFFFFu);
+        }
+        a = nx;
+    }
+    __syncwarp();
+    const bool better = cnt < __ldg(counts + c);
+    if (better) {
+        uint32_t* __restrict__ T = tbits + gb;
+        for (uint32_t q = lane; q < nblk; q += 32) {
+            T[q] = J[q];
+            longinfo[gb + q] = jlong[gb + q];  // read only at long anchors, which the jump recorded
+        }
+        if (lane == 0) counts[c] = cnt;
+    }
+}
+
 // ------------------------------------------------------------------ block scans
 
 template <typename T, typename Op>
@@ -1019,6 +1167,11 @@ static int ensure_magic(int dev) {
     return LC_OK;
 }
 
+// Keys covered by the chunk table (the reach array is indexed like the keys).
+static uint64_t nkeys_total_of(const ChunkDesc* ch, uint64_t C) {
+    return C ? ch[C - 1].key_begin + ch[C - 1].n : 0;
+}
+
 static int device_sms() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -1035,6 +1188,9 @@ struct FitScratch {
     Piece* pieces;
     uint32_t* counters;  // [0] long items, [1] pieces
     ulonglong2* cones;   // stage 1: the cone of every short segment [L]
+    uint8_t* roff;       // jump fit: reach of every key [N] (nullptr: greedy only)
+    uint32_t* jbits;     // jump fit: anchor bits [bitwords]
+    LongInfo* jlong;     // jump fit: long-segment records [bitwords]
     uint32_t items_cap, pieces_cap;
 };
 
@@ -1068,6 +1224,28 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         note_launch(2);
         int rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
+        if (fs.roff) {
+            static bool attr_r[2] = {false, false};
+            const size_t rsm = sizeof(uint32_t) * kShortSlots;
+            if (!attr_r[sizeof(KT) == 8]) {
+                rc = cuda_status(cudaFuncSetAttribute(reach_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)rsm));
+                if (rc) return rc;
+                attr_r[sizeof(KT) == 8] = true;
+            }
+            {
+                KTime kt("jump_reach", st);
+                reach_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, rsm, st>>>(keys, chunks_d, fs.wins, fs.roff);
+            }
+            {
+                KTime kt("jump_chain", st);
+                jump_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0,
+                                  st>>>(keys, chunks_d, C, fs.roff, tbits, counts, fs.longinfo, fs.jbits, fs.jlong);
+            }
+            note_launch(2);
+            rc = cuda_status(cudaGetLastError());
+            if (rc) return rc;
+        }
         return scan_exclusive(counts, csb, C, ScanOp::Identity, tmp, tmp_bytes, st);
     }
     {
@@ -1114,7 +1292,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
 }
 
 int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
-                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col) {
+                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump) {
     int rc = ensure_magic(col->device);
     if (rc) return rc;
     // windows of the speculation kernel
@@ -1167,12 +1345,28 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     uint64_t total = 0;
     uint32_t h_status = 0;
     fs.cones = nullptr;
+    fs.roff = nullptr;
+    fs.jbits = nullptr;
+    fs.jlong = nullptr;
+    uint8_t* jscratch = nullptr;
     auto fail = [&](int code) {
         cudaStreamSynchronize(st);
         cudaFreeAsync(scratch, st);
         if (fs.cones) cudaFreeAsync(fs.cones, st);
+        if (jscratch) cudaFreeAsync(jscratch, st);
         return code;
     };
+    if (jump) {
+        // reach per key, anchor bits and long-segment records of the jump segmentation
+        const uint64_t o_bits = al(nkeys_total_of(chunks_h, C)), o_long = o_bits + al(4 * bitwords);
+        if (cudaMallocAsync((void**)&jscratch, o_long + sizeof(LongInfo) * bitwords + 256, st) != cudaSuccess) {
+            jscratch = nullptr;
+            return fail(LC_ERR_NOMEM);
+        }
+        fs.roff = jscratch;
+        fs.jbits = (uint32_t*)(jscratch + o_bits);
+        fs.jlong = (LongInfo*)(jscratch + o_long);
+    }
 
     rc = cuda_status(cudaMemcpyAsync(scratch + off_wins, wins.data(), nwins * sizeof(WinDesc), cudaMemcpyHostToDevice, st));
     if (rc) return fail(rc);
@@ -1243,6 +1437,7 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     col->lay = make_layout(kb, C, L, col->W, col->NL, col->list_mode != 0);
     cudaFreeAsync(scratch, st);
     cudaFreeAsync(fs.cones, st);
+    if (jscratch) cudaFreeAsync(jscratch, st);
     return LC_OK;
 }
 

@@ -160,7 +160,7 @@ namespace lcx {
 // directory, chunk_key_begin) and the padding bytes; sets col->L, col->W and
 // col->lay.  Synchronizes `st`.
 int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
-                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col);
+                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump = false);
 // Upload the host-built prefix of the blob and zero its padding bytes.
 int finish_blob(lc_column* col, const uint8_t* prefix_h, uint64_t prefix_len, cudaStream_t st);
 

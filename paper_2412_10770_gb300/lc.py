@@ -36,7 +36,7 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
-           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes")
+           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes", "lc_compress_jump")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -145,6 +145,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_intersect": ([p, ctypes.c_int64, p, ctypes.c_int64, p, u64, pu64, p], i32),
         "lc_union": ([p, ctypes.c_int64, p, ctypes.c_int64, p, u64, pu64, p], i32),
         "lc_chunk_bytes": ([p, p, u64], i32),
+        "lc_compress_jump": ([p, u64, i32, ctypes.POINTER(_Params), p, pp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -235,6 +236,18 @@ def lc_compress(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, stream=N
     prm = _Params(int(eps), int(chunk_log2))
     _check(lib.lc_compress(keys.data_ptr(), keys.numel(), kb, ctypes.byref(prm), _stream(stream),
                            ctypes.byref(h)), "lc_compress")
+    return Column(h.value)
+
+
+def lc_compress_jump(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, stream=None) -> Column:
+    """lc_compress with the jump fit (fewest segments; never more than the greedy's)."""
+    lib = load()
+    _dev(keys, "keys")
+    kb = _key_bytes(keys)
+    h = ctypes.c_void_p()
+    prm = _Params(int(eps), int(chunk_log2))
+    _check(lib.lc_compress_jump(keys.data_ptr(), keys.numel(), kb, ctypes.byref(prm), _stream(stream),
+                                ctypes.byref(h)), "lc_compress_jump")
     return Column(h.value)
 
 
