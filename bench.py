@@ -24,6 +24,7 @@ method) on a bounded sample of the same workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -803,7 +804,8 @@ def _pcts(lat):
 
 def _run_server_open_loop(lc, srv, reqs, arrivals):
     """Submit request i at time arrivals[i] (seconds from start); returns
-    latencies (completion - intended arrival, seconds) and the makespan."""
+    latencies (completion - intended arrival, seconds), the makespan and the
+    largest delay of a submission behind its arrival time."""
     import threading
 
     n = len(reqs)
@@ -816,6 +818,7 @@ def _run_server_open_loop(lc, srv, reqs, arrivals):
                 done[c["user"]] = (time.perf_counter(), c)
 
     th = threading.Thread(target=drainer)
+    gc.disable()  # a collection pause in this load generator would read as server latency
     th.start()
     t0 = time.perf_counter()
     for i, q in enumerate(reqs):
@@ -824,19 +827,22 @@ def _run_server_open_loop(lc, srv, reqs, arrivals):
         submit_at[i] = time.perf_counter()
         srv.submit(q[0], q[1], q[2], q[3], 0 if q[4] is None else q[4].ctypes.data, q[5].data_ptr(), user=i)
     th.join()
+    gc.enable()
+    lag = float(np.max(submit_at - (t0 + np.asarray(arrivals))))
     # completion = submission (taken here) + the server's own submit-to-completion time
     fin = [submit_at[i] + 1e-6 * done[i][1]["latency_us"] for i in range(n)]
     t_end = max(fin)
     lat = [fin[i] - (t0 + arrivals[i]) for i in range(n)]
     bad = [done[i][1]["status"] for i in range(n) if done[i][1]["status"] != 0]
     assert not bad, f"failed requests: {bad[:5]}"
-    return lat, t_end - t0
+    return lat, t_end - t0, lag
 
 
 def _run_plain_open_loop(lc, cols, reqs, arrivals, stream):
     """The plain path: one request at a time, synchronously, in arrival order."""
     n = len(reqs)
     lat = []
+    gc.disable()
     t0 = time.perf_counter()
     for i, q in enumerate(reqs):
         while time.perf_counter() - t0 < arrivals[i]:
@@ -845,7 +851,9 @@ def _run_plain_open_loop(lc, cols, reqs, arrivals, stream):
                              stream=stream)
         assert c["status"] == 0
         lat.append(time.perf_counter() - (t0 + arrivals[i]))
-    return lat, time.perf_counter() - t0
+    span = time.perf_counter() - t0
+    gc.enable()
+    return lat, span
 
 
 def run_serve(args):
@@ -880,8 +888,8 @@ def run_serve(args):
     budget = int(args.budget_gb * (1 << 30))
     srv = lc.lc_server_create(cols, budget, slots=args.slots)
     # closed loop: everything at once -> the server's saturation throughput
-    lat, span = _run_server_open_loop(lc, srv, reqs[:200], np.zeros(200))  # warm-up
-    lat, span = _run_server_open_loop(lc, srv, reqs, np.zeros(len(reqs)))
+    _run_server_open_loop(lc, srv, reqs, np.zeros(len(reqs)))  # warm-up: grows the staging buffers and the pool
+    lat, span, _ = _run_server_open_loop(lc, srv, reqs, np.zeros(len(reqs)))
     x_srv = len(reqs) / span
     lat_p, span_p = _run_plain_open_loop(lc, cols, reqs[:600], np.zeros(600), stream)
     x_plain = 600 / span_p
@@ -892,11 +900,12 @@ def run_serve(args):
         n = int(min(len(reqs), max(200, rate * 2.0)))
         arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
         arr -= arr[0]
-        ls, ss = _run_server_open_loop(lc, srv, reqs[:n], arr)
+        ls, ss, lag = _run_server_open_loop(lc, srv, reqs[:n], arr)
         s50, s99 = _pcts(ls)
         row = {"rate_frac_of_server_saturation": f, "rate_req_per_s": rate, "requests": n,
                "server": {"p50_ms": 1e3 * s50, "p99_ms": 1e3 * s99, "req_per_s": n / ss,
-                          "keys_per_s": keys_per_req[:n].sum() / ss}}
+                          "keys_per_s": keys_per_req[:n].sum() / ss,
+                          "client_max_submit_lag_ms": 1e3 * lag}}
         if rate <= 3 * x_plain:  # the plain path falls behind without bound above its own capacity
             lp, sp = _run_plain_open_loop(lc, cols, reqs[:n], arr, stream)
             p50, p99 = _pcts(lp)

@@ -279,13 +279,17 @@ typedef struct {
     uint64_t peak_hbm_bytes;    /* most device memory held by batches at once (<= budget) */
     uint32_t peak_inflight;     /* most batches on the device at once */
     uint32_t slots;
+    double launch_us_max;     /* longest host time spent packing and launching one batch */
+    double launch_us_total;   /* host time spent packing and launching, all batches */
+    uint64_t staging_regrows; /* page-locked staging buffers grown (each synchronises the device) */
 } lc_server_stats_t;
 
 typedef struct lc_server lc_server;
 
 /* cols: ncols single-mode or list-mode columns of one key width, all on the
  * current device; they must outlive the server.  hbm_budget: bytes of device
- * memory the server may hold for request inputs and outputs.  slots: streams
+ * memory the server may hold for request inputs and outputs; memory a batch
+ * frees stays reserved in the server's own pool until lc_server_destroy.  slots: streams
  * (batches in flight), 1..64. */
 int lc_server_create(lc_column* const* cols, int ncols, uint64_t hbm_budget, int slots, lc_server** out);
 /* Queue one request (thread-safe, non-blocking).  The input and output

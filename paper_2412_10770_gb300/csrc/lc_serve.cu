@@ -72,6 +72,9 @@ struct lc_server {
     uint64_t next_ticket = 1;
     uint64_t submitted = 0, completed = 0, batches = 0;
     uint32_t inflight = 0, peak_inflight = 0;
+    cudaMemPool_t pool = nullptr;  // the batches' device memory; never trimmed while the server lives
+    double launch_us_max = 0, launch_us_total = 0;
+    uint64_t staging_regrows = 0;
 };
 
 namespace lcx {
@@ -161,16 +164,20 @@ int launch_batch(lc_server* s, Slot& sl) {
     const size_t total = o_dec + dec_bytes;
     const size_t stage_in = o_out;  // bytes copied in
     const size_t need_h = o_out + 8 * nq;
-    if (sl.h_cap < need_h) {
+    if (sl.h_cap < need_h) {  // grow by doubling: page-locking is slow and synchronises the device
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
-        sl.h_cap = std::max(need_h, (size_t)1 << 20);
+        size_t cap = std::max(sl.h_cap, (size_t)1 << 20);
+        while (cap < need_h) cap *= 2;
+        sl.h_cap = cap;
+        ++s->staging_regrows;
         if (cudaMallocHost((void**)&sl.h_stage, sl.h_cap) != cudaSuccess) {
             sl.h_stage = nullptr;
             sl.h_cap = 0;
             return LC_ERR_NOMEM;
         }
     }
-    if (cudaMallocAsync((void**)&sl.d_buf, std::max<size_t>(total, 256), sl.st) != cudaSuccess) return LC_ERR_NOMEM;
+    if (cudaMallocFromPoolAsync((void**)&sl.d_buf, std::max<size_t>(total, 256), s->pool, sl.st) != cudaSuccess)
+        return LC_ERR_NOMEM;
     const uint64_t dbase = (uint64_t)(uintptr_t)(sl.d_buf + o_dec);
     for (SrvReq& d : dr) d.out += dbase;
     uint8_t* h = sl.h_stage;
@@ -288,7 +295,14 @@ void scheduler(lc_server* s) {
             sl.charged = charge;
             sl.busy = true;
             active = true;
+            const auto tl = Clock::now();
             const int rc = launch_batch(s, sl);
+            const double us = std::chrono::duration<double, std::micro>(Clock::now() - tl).count();
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->launch_us_total += us;
+                s->launch_us_max = std::max(s->launch_us_max, us);
+            }
             if (rc) {
                 cudaStreamSynchronize(sl.st);
                 retire_batch(s, sl, rc);
@@ -336,6 +350,18 @@ int lc_server_create(lc_column* const* cols, int ncols, uint64_t hbm_budget, int
         if (s->d_views) cudaFree(s->d_views);
         delete s;
         return LC_ERR_NOMEM;
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    uint64_t keep = ~0ull;  // keep what the batches freed: re-mapping device memory costs milliseconds
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        cudaFree(s->d_views);
+        delete s;
+        return LC_ERR_CUDA;
     }
     s->slots.resize(slots);
     for (Slot& sl : s->slots) {
@@ -409,6 +435,9 @@ int lc_server_stats(lc_server* s, lc_server_stats_t* st) {
     st->peak_hbm_bytes = s->peak_used;
     st->peak_inflight = s->peak_inflight;
     st->slots = (uint32_t)s->slots.size();
+    st->launch_us_max = s->launch_us_max;
+    st->launch_us_total = s->launch_us_total;
+    st->staging_regrows = s->staging_regrows;
     return LC_OK;
 }
 
@@ -424,6 +453,7 @@ int lc_server_destroy(lc_server* s) {
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
     }
     if (s->d_views) cudaFree(s->d_views);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return LC_OK;
 }

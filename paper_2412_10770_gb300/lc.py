@@ -75,7 +75,9 @@ class _Completion(ctypes.Structure):
 
 class _ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
-                ("peak_hbm_bytes", ctypes.c_uint64), ("peak_inflight", ctypes.c_uint32), ("slots", ctypes.c_uint32)]
+                ("peak_hbm_bytes", ctypes.c_uint64), ("peak_inflight", ctypes.c_uint32), ("slots", ctypes.c_uint32),
+                ("launch_us_max", ctypes.c_double), ("launch_us_total", ctypes.c_double),
+                ("staging_regrows", ctypes.c_uint64)]
 
 
 _lib = None
