@@ -224,6 +224,36 @@ def oracle_sample_step(keys: np.ndarray, eps: int, nq: int, seed: int) -> float:
 CPU_SAMPLE_LOG2 = 23
 
 
+def _oracle_ready(_):
+    import oracle
+
+    oracle.compress(np.arange(4, dtype=np.uint64), 0, 16)  # loads the library
+    return os.getpid()
+
+
+def oracle_all_cores(samp, eps: int, nq: int):
+    """The same sample over every host core: each column cut into contiguous
+    pieces at 2^16-key chunk boundaries (chunks are independent, so the pieces
+    hold exactly the sample's chunks), one spawned process per core (the
+    parent holds a CUDA context, so no fork).  Returns (seconds, processes)."""
+    import multiprocessing as mp
+
+    P = os.cpu_count() or 1
+    pieces = []
+    for c in samp:
+        nch = -(-c.size // 65536)
+        per = -(-nch // P)
+        for a in range(0, nch, per):
+            pieces.append(np.ascontiguousarray(c[a * 65536:min(c.size, (a + per) * 65536)]))
+    work = [(p, eps, max(1, nq * p.size // samp[0].size), 5 + i) for i, p in enumerate(pieces)]
+    with mp.get_context("spawn").Pool(P) as pool:
+        pool.map(_oracle_ready, range(P))
+        t0 = time.perf_counter()
+        pool.starmap(oracle_sample_step, work)
+        wall = time.perf_counter() - t0
+    return wall, P
+
+
 def cpu_sample(args, full_cols=None):
     """Bounded sample of the workload: the first 2^23 keys of each generator's
     full-size column, with queries in the same proportion as the full workload."""
@@ -488,6 +518,10 @@ def main():
                                 "sample": f"first 2^{CPU_SAMPLE_LOG2} keys of each generator column, {nq} access + {nq} "
                                           f"lower_bound queries each; compress+decode+access+lower_bound",
                                 "seconds": t}
+        t_all, procs = oracle_all_cores(samp, args.eps, nq)
+        line["cpu_baseline_all_cores"] = {"value": n_s * len(samp) / t_all, "unit": "keys/s", "cores": procs,
+                                          "kind": "oracle", "sample": "the same sample, chunk-aligned pieces over "
+                                                                      "one process per core", "seconds": t_all}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
