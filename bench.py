@@ -71,6 +71,9 @@ def parse_args():
     ap.add_argument("--budget-gb", type=float, default=16.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--write-traffic", metavar="CSV",
+                    help="turn an ncu --csv capture of dram__bytes_read.sum, dram__bytes_write.sum and "
+                         "gpu__time_duration.sum over the large-column step into the traffic profile, then exit")
     return ap.parse_args()
 
 
@@ -111,6 +114,56 @@ def dram_traffic(kernel: str):
         return None
     k = prof.get("kernels", {}).get(kernel)
     return k["dram_bytes_per_launch"] if k else None
+
+
+# ncu kernel name -> the bench's name for it
+TRAFFIC_KERNELS = {"spec_kernel": "fit_spec", "chain_kernel": "fit_chain", "fit_short_kernel": "model_short",
+                   "long_width_kernel": "model_long", "pack_kernel": "pack", "decode_kernel": "decode",
+                   "decode_ranges_kernel": "decode_ranges", "access_kernel": "access",
+                   "lower_bound_kernel": "lower_bound", "decode_approx_kernel": "decode_approx",
+                   "quantile_kernel": "quantile (exact and approximate)"}
+TRAFFIC_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
+                 "nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3, "ns": 1e-6, "us": 1e-3,
+                 "ms": 1.0, "s": 1e3}
+
+
+def write_traffic(csv_path: str, command: str, out_path: str | None = None) -> dict:
+    """Per kernel of TRAFFIC_KERNELS: launches and mean DRAM bytes per launch
+    from an ncu --csv metrics log, stamped with the current source hash."""
+    import csv
+    import re
+
+    with open(csv_path, newline="") as fh:
+        rows = list(csv.reader(fh))
+    head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    hdr = rows[head]
+    acc = {}
+    for r in rows[head + 1:]:
+        d = dict(zip(hdr, r))
+        m = re.search(r"(\w+)(?:<[^(]*)?\(", d.get("Kernel Name", ""))
+        name = TRAFFIC_KERNELS.get(m.group(1)) if m else None
+        if name is None:
+            continue
+        v = float(d["Metric Value"].replace(",", "")) * TRAFFIC_UNITS[d["Metric Unit"]]
+        k = acc.setdefault(name, {"ids": set(), "rd": 0.0, "wr": 0.0, "ms": 0.0})
+        k["ids"].add(d["ID"])
+        k[{"dram__bytes_read.sum": "rd", "dram__bytes_write.sum": "wr", "gpu__time_duration.sum": "ms"}
+          [d["Metric Name"]]] += v
+    kernels = {}
+    for name, k in acc.items():
+        n = len(k["ids"])
+        kernels[name] = {"launches": n, "dram_read_bytes_per_launch": k["rd"] / n,
+                         "dram_write_bytes_per_launch": k["wr"] / n,
+                         "dram_bytes_per_launch": (k["rd"] + k["wr"]) / n, "ms_per_launch_under_ncu": k["ms"] / n}
+    prof = {"workload": "large single column: 3 x N=2e8 sorted uint64 keys (lognormal, piecewise, clusters), eps=63, "
+                        "one warm-up and one timed step, then the quantile and segments-only rows",
+            "command": command,
+            "one_pass_check": "the same three metrics on lower_bound_kernel of a 3e7-key column reported 1 pass",
+            "source_sha256": kernel_sources_sha256(), "kernels": kernels}
+    with open(out_path or os.path.join(ROOT, "profiles", "traffic_large_column_eps63.json"), "w") as fh:
+        json.dump(prof, fh, indent=1)
+        fh.write("\n")
+    return prof
 
 
 def rank_seed(seed: int, rank: int) -> int:
@@ -309,6 +362,13 @@ def workload_config(args):
 
 def main():
     args = parse_args()
+    if args.write_traffic:
+        cmd = ("python bench.py --steps 1 --warmup 1 --no-e2e --no-cpu-baseline > gpurun_out/p3_full.log 2>&1 && "
+               "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
+               "--csv --log-file gpurun_out/p3_traffic_full.csv python bench.py --steps 1 --warmup 1 --no-e2e "
+               "--no-cpu-baseline; python bench.py --write-traffic gpurun_out/p3_traffic_full.csv")
+        write_traffic(args.write_traffic, cmd)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
