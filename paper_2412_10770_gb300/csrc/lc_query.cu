@@ -192,7 +192,8 @@ __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd
 }
 
 // The pipeline over work items w = blockIdx.x, blockIdx.x + gridDim.x, ...
-// < total; src(w, &view, &tile, &lo, &hi, &out) describes item w.
+// < total; src(w, &view, &tile, &lo, &hi, &out) describes item w and is
+// called by all 32 lanes of warp 0 together.
 template <typename KT, typename Src>
 __device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint32_t ms) {
     __shared__ __align__(8) uint64_t s_bar[2];
@@ -208,26 +209,30 @@ __device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint
     const ColView* vv;
     uint64_t t, lo, hi;
     void* o;
-    if (threadIdx.x == 0) {
+    // warp 0 describes the items (src is warp-collective), thread 0 issues
+    if (threadIdx.x < 32) {
         src(w0, &vv, &t, &lo, &hi, &o);
-        dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, 0), &s_bar[0], &s_item[0]);
+        if (threadIdx.x == 0) dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, 0), &s_bar[0], &s_item[0]);
     }
     uint32_t k = 0;
     for (uint64_t w = w0; w < total; w += gridDim.x, ++k) {
         const uint32_t s = k & 1u;
         const uint64_t wn = w + gridDim.x;
-        if (threadIdx.x == 0 && wn < total) {
+        if (threadIdx.x < 32 && wn < total) {
             src(wn, &vv, &t, &lo, &hi, &o);
-            dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, s ^ 1u), &s_bar[s ^ 1u], &s_item[s ^ 1u]);
+            if (threadIdx.x == 0)
+                dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, s ^ 1u), &s_bar[s ^ 1u], &s_item[s ^ 1u]);
         }
         const bool got = mbar_wait(&s_bar[s], (k >> 1) & 1u);
         if (__syncthreads_or(!got)) {
             // a copy never completed: record it, wait (bounded) for the other
             // stage's copies, and stop
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < 32) {
                 src(w, &vv, &t, &lo, &hi, &o);
-                atomicOr(vv->status, kStTimeout);
-                if (wn < total) mbar_wait(&s_bar[s ^ 1u], ((k + 1) >> 1) & 1u);
+                if (threadIdx.x == 0) {
+                    atomicOr(vv->status, kStTimeout);
+                    if (wn < total) mbar_wait(&s_bar[s ^ 1u], ((k + 1) >> 1) & 1u);
+                }
             }
             __syncthreads();
             return;
@@ -261,6 +266,25 @@ __global__ void __launch_bounds__(kDecThreads, 8) decode_kernel(ColView v, uint6
     dec_pipeline<KT>(nt, WholeSrc<KT>{&v, t0, begin, end, out}, smem, v.max_tile_segs);
 }
 
+// The last r in [0, n) with off[r] <= w, for non-decreasing off with
+// off[0] <= w, found by the 32 lanes of a warp together: each round probes 32
+// evenly spaced entries and keeps the span after the last one that is <= w,
+// so 16384 ranges take three rounds of loads instead of fourteen dependent
+// ones.  Call with all 32 lanes; every lane gets the result.
+__device__ __forceinline__ uint64_t warp_last_le(const uint64_t* __restrict__ off, uint64_t n, uint64_t w) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint64_t a = 0, b = n;  // the answer lies in [a, b)
+    while (b - a > 1) {
+        const uint64_t step = (b - a + 31) >> 5;
+        const uint64_t i = a + step * lane;
+        const bool ok = i < b && __ldg(off + i) <= w;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);  // a prefix of lanes; lane 0 (i = a) always
+        a += step * (31u - __clz(bal));
+        b = min(b, a + step);
+    }
+    return a;
+}
+
 // Work items of a multi-range decode: range r covers tiles
 // [first[r], first[r] + ntiles[r]).
 __global__ void range_tiles_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
@@ -290,12 +314,7 @@ struct RangesSrc {
     KT* out;
     __device__ void operator()(uint64_t w, const ColView** vv, uint64_t* t, uint64_t* lo, uint64_t* hi,
                                void** o) const {
-        uint64_t a = 0, b = m - 1;  // last r with work_off[r] <= w
-        while (a < b) {
-            const uint64_t mid = (a + b + 1) >> 1;
-            if (work_off[mid] <= w) a = mid;
-            else b = mid - 1;
-        }
+        const uint64_t a = warp_last_le(work_off, m, w);  // the range that holds item w
         *vv = v;
         *t = first[a] + (w - work_off[a]);
         *lo = begin[a];
@@ -675,12 +694,7 @@ struct ServeSrc {
     uint32_t nreq;
     __device__ void operator()(uint64_t w, const ColView** vv, uint64_t* t, uint64_t* lo, uint64_t* hi,
                                void** o) const {
-        uint32_t a = 0, b = nreq - 1;
-        while (a < b) {
-            const uint32_t mid = (a + b + 1) >> 1;
-            if (work_off[mid] <= w) a = mid;
-            else b = mid - 1;
-        }
+        const uint64_t a = warp_last_le(work_off, nreq, w);  // the request that holds item w
         const SrvReq& rq = reqs[a];
         *vv = views + rq.col;
         *t = rq.first_tile + (w - work_off[a]);
@@ -998,6 +1012,15 @@ static uint64_t host_tile_of(const lc_column* col, uint64_t i) {
     return col->h_ctb[c] + ((i - col->h_ckb[c]) >> kTileLog);
 }
 
+// CTAs of a persistent decode launch: as many as fit on every SM at once.
+template <typename F>
+static unsigned dec_grid(F kernel, size_t smem) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kDecThreads, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+    return (unsigned)(sm_count() * occ);
+}
+
 template <typename KT>
 static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_t begin, uint64_t count, void* out,
                          cudaStream_t st) {
@@ -1041,16 +1064,17 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
     int rc = cuda_status(cudaGetLastError());
     if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, tmp_b, st);
     if (!rc) {
-        const unsigned grid = (unsigned)(sm_count() * 4);
         const size_t smem = dec_smem(col->view.max_tile_segs);
         if (col->key_bytes == 4) {
             if (!(rc = set_smem<uint32_t>())) {
+                const unsigned grid = dec_grid(decode_ranges_kernel<uint32_t>, smem);
                 KTime kt("decode_ranges", st);
                 decode_ranges_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(col->view, begin, count, out_off, m,
                                                                                first, work_off, (uint32_t*)out);
             }
         } else {
             if (!(rc = set_smem<uint64_t>())) {
+                const unsigned grid = dec_grid(decode_ranges_kernel<uint64_t>, smem);
                 KTime kt("decode_ranges", st);
                 decode_ranges_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(col->view, begin, count, out_off, m,
                                                                                first, work_off, (uint64_t*)out);
@@ -1282,15 +1306,15 @@ int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uin
     rc = cuda_status(cudaGetLastError());
     if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, kNoAllocScanBytes, st);
     if (rc) return rc;
-    const unsigned grid = (unsigned)(sm_count() * 4);
+    const size_t smem = dec_smem(col->view.max_tile_segs);
     if (col->key_bytes == 4) {
         if ((rc = set_smem<uint32_t>())) return rc;
-        decode_ranges_kernel<uint32_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off, m, first,
-                                                                           work_off, (uint32_t*)out);
+        decode_ranges_kernel<uint32_t><<<dec_grid(decode_ranges_kernel<uint32_t>, smem), kDecThreads, smem, st>>>(
+            col->view, begin, count, out_off, m, first, work_off, (uint32_t*)out);
     } else {
         if ((rc = set_smem<uint64_t>())) return rc;
-        decode_ranges_kernel<uint64_t><<<grid, kDecThreads, dec_smem(col->view.max_tile_segs), st>>>(col->view, begin, count, out_off, m, first,
-                                                                           work_off, (uint64_t*)out);
+        decode_ranges_kernel<uint64_t><<<dec_grid(decode_ranges_kernel<uint64_t>, smem), kDecThreads, smem, st>>>(
+            col->view, begin, count, out_off, m, first, work_off, (uint64_t*)out);
     }
     note_launch();
     return cuda_status(cudaGetLastError());
@@ -1313,7 +1337,6 @@ int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, u
     }
     if (nwork) {
         const size_t smem = dec_smem(max_tile_segs);
-        const unsigned grid = (unsigned)std::min<uint64_t>(nwork, (uint64_t)sm_count() * 4);
         if (key_bytes == 4) {
             static bool done = false;
             if (!done) {
@@ -1322,6 +1345,7 @@ int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, u
                     return rc;
                 done = true;
             }
+            const unsigned grid = (unsigned)std::min<uint64_t>(nwork, dec_grid(serve_decode_kernel<uint32_t>, smem));
             serve_decode_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(views_d, dreqs_d, ndreq, work_off_d,
                                                                           max_tile_segs);
         } else {
@@ -1332,6 +1356,7 @@ int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, u
                     return rc;
                 done = true;
             }
+            const unsigned grid = (unsigned)std::min<uint64_t>(nwork, dec_grid(serve_decode_kernel<uint64_t>, smem));
             serve_decode_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(views_d, dreqs_d, ndreq, work_off_d,
                                                                           max_tile_segs);
         }
