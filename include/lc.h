@@ -134,7 +134,8 @@ int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t 
  * K[i] = floor(f_j(i)) + Delta[i]) into out_dev (count keys of key_bytes
  * bytes, device memory).  The full column is (0, N); in list mode list l is
  * (list_begin[l], list_begin[l+1] - list_begin[l]).  Asynchronous.
- * LC_ERR_OUT_OF_RANGE if begin + count > N. */
+ * LC_ERR_OUT_OF_RANGE if begin + count > N; LC_ERR_INVALID_ARG if out_dev is
+ * not a multiple of key_bytes (here and in lc_decode_ranges*). */
 int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream);
 
 /* Several ranges in one launch: range r is keys [begin[r], begin[r] +

@@ -402,8 +402,13 @@ int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t 
     return LC_OK;
 }
 
+// Output keys are stored whole: the buffer must be aligned to the key width.
+static bool misaligned(const lc_column* col, const void* out) {
+    return ((uintptr_t)out % col->key_bytes) != 0;
+}
+
 int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_dev, void* stream) {
-    if (!col || (count && !out_dev)) return LC_ERR_INVALID_ARG;
+    if (!col || (count && !out_dev) || misaligned(col, out_dev)) return LC_ERR_INVALID_ARG;
     if (begin > col->N || count > col->N - begin) return LC_ERR_OUT_OF_RANGE;
     return decode_range(col, begin, count, out_dev, (cudaStream_t)stream);
 }
@@ -411,6 +416,7 @@ int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_de
 int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
                      const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream) {
     if (!col || (m && (!begin_dev || !count_dev || !out_off_dev || !out_dev))) return LC_ERR_INVALID_ARG;
+    if (misaligned(col, out_dev)) return LC_ERR_INVALID_ARG;
     if (col->N == 0) return LC_OK;
     return decode_ranges(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
 }
@@ -418,7 +424,7 @@ int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint
 int lc_decode_ranges_noalloc(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
                              const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream) {
     if (!col || (m && (!begin_dev || !count_dev || !out_off_dev || !out_dev))) return LC_ERR_INVALID_ARG;
-    if (m > LC_NOALLOC_MAX_RANGES) return LC_ERR_INVALID_ARG;
+    if (m > LC_NOALLOC_MAX_RANGES || misaligned(col, out_dev)) return LC_ERR_INVALID_ARG;
     if (col->N == 0) return LC_OK;
     return decode_ranges_noalloc(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
 }

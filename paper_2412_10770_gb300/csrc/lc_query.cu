@@ -165,19 +165,36 @@ __device__ void dec_issue(const ColView& v, uint64_t t, uint64_t lo_key, uint64_
     if (td.pwn) bulk_load(sd.pay, v.pay32 + td.pw0, td.pwn * 4u, bar);
 }
 
+// Two keys stored as one aligned vector.
+__device__ __forceinline__ void st_pair(uint64_t* p, uint64_t a, uint64_t b) {
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b);
+}
+__device__ __forceinline__ void st_pair(uint32_t* p, uint32_t a, uint32_t b) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(a, b);
+}
+
 // All threads: the wanted keys of the item in stage sd.  Everything inside a
 // tile is 32-bit: positions, segment offsets and payload bits relative to the
 // tile (the low 32 bits of the global values suffice because every difference
-// taken is below 2^32).  The anchor (t = 0) takes a zero-width field, so no
-// key branches; four keys per thread are in flight at once.
+// taken is below 2^32).
+//
+// A thread decodes two neighbouring keys p, p + 1 at once, starting where
+// &out[p] is aligned to the pair: one rank word and one record serve both
+// (key p + 1 only reads the next record when it starts a segment), their two
+// residuals sit next to each other in one 64-bit window of the payload, and
+// the pair goes out as one vector store.  An unpaired first or last key is
+// decoded alone.  An anchor (t = 0) has no residual: its field is taken as 0.
 template <typename KT>
 __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd) {
     const uint32_t p0 = (uint32_t)(d.lo - d.kbeg), p1 = (uint32_t)(d.hi - d.kbeg);
     KT* __restrict__ out = (KT*)d.out + (d.lo - d.lo_key) - p0;  // out[p]: key kbeg + p
     const uint32_t kb32 = (uint32_t)d.kbeg, koff = kb32 & 63u;
     const uint32_t j0 = (uint32_t)d.j0, pb0 = (uint32_t)d.pbit0, nsm1 = d.ns - 1;
-#pragma unroll 4
-    for (uint32_t p = p0 + threadIdx.x; p < p1; p += kDecThreads) {
+    // pairs start at p = e (mod 2): there out + p is a multiple of 2 sizeof(KT)
+    const uint32_t e = (uint32_t)(((uintptr_t)out / sizeof(KT)) & 1u);
+    const uint32_t pa = p0 + ((p0 ^ e) & 1u);
+    const uint32_t np = p1 > pa ? (p1 - pa) >> 1 : 0u;
+    auto one = [&](uint32_t p) {
         const uint32_t g = kb32 + p;
         const RankWord rw = sd.rank[(koff + p) >> 6];
         const uint32_t jr = (uint32_t)rw.before - j0 + (uint32_t)__popcll(rw.bits << (63u - (g & 63u))) - 1u;
@@ -188,6 +205,35 @@ __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd
         const uint32_t q = min(lb >> 5, kPayWords - 2);
         const uint32_t z = extract_bits(sd.pay[q], sd.pay[q + 1], lb & 31u, t ? w : 0u);
         out[p] = (KT)(r.icpt + (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(z)));
+    };
+    if (threadIdx.x == kDecThreads - 1 && pa > p0 && p0 < p1) one(p0);
+    if (threadIdx.x == kDecThreads - 2 && p1 > pa && ((p1 - pa) & 1u)) one(p1 - 1);
+#pragma unroll 2
+    for (uint32_t i = threadIdx.x; i < np; i += kDecThreads) {
+        const uint32_t p = pa + 2 * i;
+        const uint32_t g = kb32 + p, x = koff + p, x1 = x + 1;
+        const RankWord rw = sd.rank[x >> 6];
+        const uint32_t jr = (uint32_t)rw.before - j0 + (uint32_t)__popcll(rw.bits << (63u - (x & 63u))) - 1u;
+        const uint64_t bits1 = (x1 & 63u) ? rw.bits : sd.rank[x1 >> 6].bits;  // the rank word of key p + 1
+        const bool starts1 = (bits1 >> (x1 & 63u)) & 1u;                     // key p + 1 opens a segment
+        const SegRec r = sd.rec[min(jr, nsm1)];
+        const uint32_t t = g - (uint32_t)r.kstart_w;
+        const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+        // the window starts at residual t (t >= 1), or at residual 1 for an anchor
+        const uint32_t lb = (uint32_t)r.bit1_n - pb0 + w * (t ? t - 1u : 0u);
+        const uint32_t q = min(lb >> 5, kPayWords - 3);
+        const uint32_t sh = lb & 31u;
+        const uint32_t a0 = sd.pay[q], a1 = sd.pay[q + 1], a2 = sd.pay[q + 2];
+        const uint64_t win = ((uint64_t)__funnelshift_r(a1, a2, sh) << 32) | __funnelshift_r(a0, a1, sh);
+        const uint64_t mask = (1ull << w) - 1ull;
+        const uint32_t za = (uint32_t)(win & mask), zb = (uint32_t)((win >> w) & mask);
+        const KT v0 = (KT)(r.icpt + (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(t ? za : 0u)));
+        KT v1;
+        if (starts1)
+            v1 = (KT)sd.rec[min(jr + 1u, nsm1)].icpt;
+        else
+            v1 = (KT)(r.icpt + (uint64_t)(line_at(r.slope, t + 1u) + (int64_t)unzigzag32(t ? zb : za)));
+        st_pair(out + p, v0, v1);
     }
 }
 

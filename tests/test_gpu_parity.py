@@ -206,6 +206,40 @@ def test_decode_ranges_many_windows():
     col.free()
 
 
+@pytest.mark.parametrize("dt", [np.uint32, np.uint64])
+def test_decode_into_every_output_alignment(dt):
+    # keys are decoded two at a time into vector stores aligned to the pair:
+    # an output that starts one key in shifts every pair, and odd begins and
+    # counts leave a lone first and last key; a pointer that is not a multiple
+    # of the key width is refused
+    n = 70001
+    keys = inputs.lognormal_gaps(n, seed=33, dtype=dt)
+    col = lc.lc_compress(dev(keys), eps=7)
+    buf = torch.zeros(n + 2, dtype=col.dtype, device="cuda")
+    for shift in (0, 1):
+        for b, c in ((0, n), (1, n - 1), (3, 5000), (2048, 2049), (4095, 1), (0, 2), (n - 3, 3)):
+            buf.zero_()
+            lc.lc_decode(col, b, c, out=buf[shift:shift + c])
+            got = host(buf)
+            assert np.array_equal(got[shift:shift + c], keys[b:b + c])
+            assert not got[:shift].any() and not got[shift + c:].any()
+    m = 64
+    rng = np.random.default_rng(5)
+    cnt = rng.integers(0, 3000, size=m).astype(np.uint64)
+    beg = np.array([rng.integers(0, n - c + 1) for c in cnt], dtype=np.uint64)
+    off = (np.concatenate([[0], np.cumsum(cnt)[:-1]]) + np.arange(m)).astype(np.uint64)  # odd gaps between ranges
+    out = torch.zeros(int(off[-1] + cnt[-1]) + 1, dtype=col.dtype, device="cuda")
+    lc.lc_decode_ranges(col, dev(beg), dev(cnt), dev(off), out)
+    got = host(out)
+    for b, c, o in zip(beg, cnt, off):
+        assert np.array_equal(got[int(o):int(o) + int(c)], keys[int(b):int(b) + int(c)])
+    raw = torch.zeros(8 * (n + 2), dtype=torch.uint8, device="cuda")
+    rc = lc.load().lc_decode(col.handle, 0, 10, raw.data_ptr() + 1, None)
+    assert rc == lc.LC_ERR_INVALID_ARG
+    assert lc.lc_status(col) == lc.LC_OK
+    col.free()
+
+
 def test_unsorted_input_and_out_of_range_queries():
     keys = inputs.uniform_gaps(10000, seed=2, dtype=np.uint64)
     bad = keys.copy()
