@@ -18,7 +18,7 @@
 namespace lcx {
 namespace {
 
-constexpr int kDecThreads = 256;
+constexpr int kDecThreads = 128;
 constexpr uint32_t kMaxSegsPerTile = kTile + 1;
 constexpr uint32_t kRankPerTile = kTile / 64 + 1;  // rank words a tile's keys can touch
 constexpr uint32_t kPayWords = kTile + 16;          // payload words a tile can need (32-bit)
@@ -208,7 +208,7 @@ __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd
     };
     if (threadIdx.x == kDecThreads - 1 && pa > p0 && p0 < p1) one(p0);
     if (threadIdx.x == kDecThreads - 2 && p1 > pa && ((p1 - pa) & 1u)) one(p1 - 1);
-#pragma unroll 2
+#pragma unroll 4
     for (uint32_t i = threadIdx.x; i < np; i += kDecThreads) {
         const uint32_t p = pa + 2 * i;
         const uint32_t g = kb32 + p, x = koff + p, x1 = x + 1;
@@ -306,7 +306,7 @@ struct WholeSrc {
 
 // Persistent: tiles t0 .. t0 + nt - 1, keys [begin, end) into out[g - begin].
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads, 8) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
+__global__ void __launch_bounds__(kDecThreads, 12) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
                                                              uint64_t end, KT* __restrict__ out) {
     extern __shared__ __align__(16) uint8_t smem[];
     dec_pipeline<KT>(nt, WholeSrc<KT>{&v, t0, begin, end, out}, smem, v.max_tile_segs);
@@ -370,7 +370,7 @@ struct RangesSrc {
 };
 
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads, 8)
+__global__ void __launch_bounds__(kDecThreads, 12)
 decode_ranges_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
                      const uint64_t* __restrict__ out_off, uint64_t m, const uint64_t* __restrict__ first,
                      const uint64_t* __restrict__ work_off, KT* __restrict__ out) {
@@ -751,7 +751,7 @@ struct ServeSrc {
 };
 
 template <typename KT>
-__global__ void __launch_bounds__(kDecThreads, 8)
+__global__ void __launch_bounds__(kDecThreads, 12)
 serve_decode_kernel(const ColView* __restrict__ views, const SrvReq* __restrict__ reqs, uint32_t nreq,
                     const uint64_t* __restrict__ work_off, uint32_t smem_segs) {
     extern __shared__ __align__(16) uint8_t smem[];
