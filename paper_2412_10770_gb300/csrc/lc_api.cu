@@ -71,6 +71,116 @@ int cuda_status(cudaError_t e) {
     return LC_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ small transfers without copy engines
+
+namespace {
+
+constexpr size_t kStageCap = 8u << 20;  // per host thread and device
+constexpr int kStageDevices = 64;
+
+struct StageArena {
+    uint8_t* h = nullptr;  // page-locked, mapped
+    uint8_t* d = nullptr;  // its device address
+    size_t off = 0;        // bytes in use since the last stage_sync
+};
+thread_local StageArena t_stage[kStageDevices];
+
+__global__ void stage_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void stage_copy1(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+int stage_arena(StageArena** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kStageDevices) return LC_ERR_INTERNAL;
+    StageArena& a = t_stage[dev];
+    if (!a.h) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, kStageCap, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+            return LC_ERR_NOMEM;
+        void* d = nullptr;
+        if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaFreeHost(h);
+            return LC_ERR_CUDA;
+        }
+        a.h = (uint8_t*)h;
+        a.d = (uint8_t*)d;
+        a.off = 0;
+    }
+    *out = &a;
+    return LC_OK;
+}
+
+// A region of `bytes` (16-byte aligned); when the arena is full, waits for st
+// (every region in use belongs to a transfer ordered on st before this one).
+int stage_reserve(size_t bytes, cudaStream_t st, StageArena** arena, size_t* off) {
+    if (bytes > kStageCap) return LC_ERR_UNSUPPORTED;
+    StageArena* a = nullptr;
+    int rc = stage_arena(&a);
+    if (rc) return rc;
+    if (a->off + bytes > kStageCap) {
+        rc = cuda_status(cudaStreamSynchronize(st));
+        if (rc) return rc;
+        a->off = 0;
+    }
+    *arena = a;
+    *off = a->off;
+    a->off = (a->off + bytes + 15) & ~(size_t)15;
+    return LC_OK;
+}
+
+int stage_copy(const uint8_t* src, uint8_t* dst, size_t bytes, cudaStream_t st) {
+    const bool v16 = ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
+    const size_t n16 = v16 ? bytes / 16 : 0, tail = bytes - 16 * n16;
+    if (n16) {
+        stage_copy16<<<(unsigned)std::min<size_t>((n16 + 255) / 256, 1024), 256, 0, st>>>((const uint4*)src,
+                                                                                           (uint4*)dst, n16);
+        note_launch();
+    }
+    if (tail) {
+        stage_copy1<<<(unsigned)std::min<size_t>((tail + 255) / 256, 1024), 256, 0, st>>>(src + 16 * n16,
+                                                                                           dst + 16 * n16, tail);
+        note_launch();
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+int stage_h2d(void* dst_dev, const void* src_host, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return LC_OK;
+    if (bytes > kStageCap / 8)  // large enough to be worth a copy engine
+        return cuda_status(cudaMemcpyAsync(dst_dev, src_host, bytes, cudaMemcpyHostToDevice, st));
+    StageArena* a = nullptr;
+    size_t off = 0;
+    int rc = stage_reserve(bytes, st, &a, &off);
+    if (rc) return rc;
+    std::memcpy(a->h + off, src_host, bytes);
+    return stage_copy(a->d + off, (uint8_t*)dst_dev, bytes, st);
+}
+
+int stage_d2h(const void* src_dev, size_t bytes, cudaStream_t st, const void** host_out) {
+    StageArena* a = nullptr;
+    size_t off = 0;
+    int rc = stage_reserve(std::max<size_t>(bytes, 1), st, &a, &off);
+    if (rc) return rc;
+    *host_out = a->h + off;
+    return bytes ? stage_copy((const uint8_t*)src_dev, a->d + off, bytes, st) : LC_OK;
+}
+
+int stage_sync(cudaStream_t st) {
+    const int rc = cuda_status(cudaStreamSynchronize(st));
+    StageArena* a = nullptr;
+    if (!rc && stage_arena(&a) == LC_OK) a->off = 0;
+    return rc;
+}
+
 static uint64_t pad16(uint64_t x) { return (x + 15) & ~(uint64_t)15; }
 
 Layout make_layout(int kb, uint64_t C, uint64_t L, uint64_t W, uint64_t NL, bool list_mode) {

@@ -1368,9 +1368,9 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
         fs.jlong = (LongInfo*)(jscratch + o_long);
     }
 
-    rc = cuda_status(cudaMemcpyAsync(scratch + off_wins, wins.data(), nwins * sizeof(WinDesc), cudaMemcpyHostToDevice, st));
+    rc = stage_h2d(scratch + off_wins, wins.data(), nwins * sizeof(WinDesc), st);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaMemcpyAsync(chunks_d, chunks_h, C * sizeof(ChunkDesc), cudaMemcpyHostToDevice, st));
+    rc = stage_h2d(chunks_d, chunks_h, C * sizeof(ChunkDesc), st);
     if (rc) return fail(rc);
     rc = cuda_status(cudaMemsetAsync(status, 0, 4, st));
     if (rc) return fail(rc);
@@ -1390,12 +1390,15 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
         rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 0);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaMemcpyAsync(&total, csb_tmp + C, 8, cudaMemcpyDeviceToHost, st));
+    const void *p_total = nullptr, *p_status = nullptr;
+    rc = stage_d2h(csb_tmp + C, 8, st, &p_total);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st));
+    rc = stage_d2h(status, 4, st, &p_status);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaStreamSynchronize(st));
+    rc = stage_sync(st);
     if (rc) return fail(rc);
+    std::memcpy(&total, p_total, 8);
+    std::memcpy(&h_status, p_status, 4);
     if (h_status & kStUnsorted) return fail(LC_ERR_UNSORTED);
     const uint64_t L = total;
     HTime ht1("fit_stage1");
@@ -1426,12 +1429,14 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
         rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 1);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaMemcpyAsync(&total, col->blob + lay.cwb + 8 * C, 8, cudaMemcpyDeviceToHost, st));
+    rc = stage_d2h(col->blob + lay.cwb + 8 * C, 8, st, &p_total);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st));
+    rc = stage_d2h(status, 4, st, &p_status);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaStreamSynchronize(st));
+    rc = stage_sync(st);
     if (rc) return fail(rc);
+    std::memcpy(&total, p_total, 8);
+    std::memcpy(&h_status, p_status, 4);
     if (total > payload_bound_words || (h_status & kStInternal)) return fail(LC_ERR_INTERNAL);
     col->W = total;
     col->lay = make_layout(kb, C, L, col->W, col->NL, col->list_mode != 0);
@@ -1453,7 +1458,7 @@ __global__ void zero_pads(uint8_t* __restrict__ p, PadRanges pr) {
 }  // namespace
 
 int finish_blob(lc_column* col, const uint8_t* prefix_h, uint64_t prefix_len, cudaStream_t st) {
-    int rc = cuda_status(cudaMemcpyAsync(col->blob, prefix_h, prefix_len, cudaMemcpyHostToDevice, st));
+    int rc = stage_h2d(col->blob, prefix_h, prefix_len, st);
     if (rc) return rc;
     const Layout& F = col->lay;
     const uint64_t C = col->C, L = col->L;

@@ -195,6 +195,19 @@ size_t scan_tmp_bytes(uint64_t n);
 
 int cuda_status(cudaError_t e);
 
+// Small host <-> device transfers (descriptors, headers, counts) made by
+// kernels on page-locked mapped host memory instead of by the copy engines,
+// so that they never queue behind a caller's large copies on other streams.
+// The staging memory is per host thread and device; a region stays in use
+// until the stream is synchronised with stage_sync.
+//   stage_h2d: bytes from src_host to dst_dev, ordered on st (above 1 MB by
+//              an ordinary copy).  src_host may be reused on return.
+//   stage_d2h: bytes from src_dev; *host_out points at them once stage_sync(st)
+//              has returned.
+int stage_h2d(void* dst_dev, const void* src_host, size_t bytes, cudaStream_t st);
+int stage_d2h(const void* src_dev, size_t bytes, cudaStream_t st, const void** host_out);
+int stage_sync(cudaStream_t st);
+
 // Count of kernel launches issued by the library in this process.
 void note_launch(uint32_t k = 1);
 

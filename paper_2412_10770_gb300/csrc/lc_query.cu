@@ -9,6 +9,7 @@
 // rank (popcount) on that map: no search per key.  Keys are written with
 // consecutive threads on consecutive keys (coalesced).
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -926,7 +927,7 @@ int build_derived(lc_column* col, cudaStream_t st) {
     col->chunk_tile_begin = (uint64_t*)p;
     col->tiles = (TileDesc*)(p + 8 * (C + 1));
     col->status = (uint32_t*)(p + 8 * (C + 1) + sizeof(TileDesc) * (col->ntiles + 1));
-    int rc = cuda_status(cudaMemcpyAsync(col->chunk_tile_begin, ctb.data(), 8 * (C + 1), cudaMemcpyHostToDevice, st));
+    int rc = stage_h2d(col->chunk_tile_begin, ctb.data(), 8 * (C + 1), st);
     if (rc) return rc;
     rc = cuda_status(cudaMemsetAsync(col->status, 0, 4, st));
     if (rc) return rc;
@@ -1014,10 +1015,12 @@ int build_derived(lc_column* col, cudaStream_t st) {
         ends_kernel<<<1, 32, 0, st>>>(v, ends);
         note_launch();
         uint64_t h[3] = {0, 0, 0};
-        rc = cuda_status(cudaMemcpyAsync(h, col->status, 24, cudaMemcpyDeviceToHost, st));
+        const void* ph = nullptr;
+        rc = stage_d2h(col->status, 24, st, &ph);
         if (rc) return rc;
-        rc = cuda_status(cudaStreamSynchronize(st));
+        rc = stage_sync(st);
         if (rc) return rc;
+        std::memcpy(h, ph, 24);
         v.max_tile_segs = std::max<uint32_t>((uint32_t)(h[0] >> 32), 1);
         v.kmin = h[1];
         v.kmax = h[2];
