@@ -664,10 +664,13 @@ def run_batch(args):
     launches0 = lc.lc_launch_count()
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
     sampler.start()
+    lc.lc_timing_read()  # drop anything recorded before the timed region
     for _ in range(args.steps):
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
+        lc.lc_timing_enable(True)  # per-kernel times of the compress (not of the graph's capture)
         col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream)
+        lc.lc_timing_enable(False)
         b.record(stream)
         graph, _ = lc.lc_graph_decode(col, 0, N, out, stream=stream)
         torch.cuda.synchronize()
@@ -683,6 +686,8 @@ def run_batch(args):
     clocks = sampler.stop()
     launches = lc.lc_launch_count() - launches0
     K = args.steps
+    compress_kernels = {name: {"launches_per_step": nl / K, "ms_per_step": tms / K}
+                        for name, (nl, tms) in sorted(lc.lc_timing_read().items(), key=lambda x: -x[1][1])}
     # one call per list, on a random sample of lists
     rng = np.random.default_rng(7)
     sample = rng.choice(len(begin) - 1, size=min(args.per_list_sample, len(begin) - 1), replace=False)
@@ -710,7 +715,8 @@ def run_batch(args):
             "batched": {"compress_keys_per_s": N / (ms_c / 1e3), "decode_keys_per_s": N / (ms_d / 1e3),
                         "compress_ms": ms_c, "decode_ms": ms_d,
                         "decode_alg_gbs": alg_d / (ms_d / 1e3) / 1e9, "decode_hbm_frac": alg_d / (ms_d / 1e3) / 1e9 / peak,
-                        "compress_alg_gbs": (4 * N + size) / (ms_c / 1e3) / 1e9},
+                        "compress_alg_gbs": (4 * N + size) / (ms_c / 1e3) / 1e9,
+                        "compress_kernels": compress_kernels},
             "per_list": {"lists_sampled": int(sample.size), "keys": int(skeys),
                          "keys_per_s": skeys / tp, "note": "one lc_compress + lc_decode per list, host-timed"},
             "batched_over_per_list": value / (skeys / tp),

@@ -711,7 +711,15 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     __shared__ uint32_t s_T[kWords + 4];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_base, s_nlong, s_item0, s_piece0;
-    __shared__ WinLong s_long[kLongPerWin];
+    // the passes' prefix pieces, then (after a barrier) the window's long segments
+    __shared__ union {
+        struct {
+            ulonglong2 pc[kShortThreads];  // partial cones (pass 1), then largest residuals (pass 2)
+            uint32_t pa[kShortThreads];    // their segment's anchor (kNone: none)
+        } pieces;
+        WinLong lng[kLongPerWin];
+    } s_u;
+    WinLong* const s_long = s_u.lng;
     const WinDesc wd = wins[blockIdx.x];
     const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
@@ -763,106 +771,191 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
         return left < kShortMax ? n : kNone;
     };
     auto is_anchor = [&](uint32_t i) { return (s_T[(i - w0) >> 5] >> ((i - w0) & 31u)) & 1u; };
-    // The thread's segments are those whose anchor lies in its block: every
-    // one up to the last anchor a_last is short (it ends at the next anchor);
-    // the one at a_last is short iff the next anchor is within 96 keys.  Keys
-    // [a_first, end) are therefore whole short segments, walked as one flat
-    // loop twice: the cone and slope, then the widths.
-    uint32_t a_first = 0, a_last = 0, e_last = kNone, end = 0;
+    // Work is split by keys, not by segments: thread t takes the keys of its
+    // 32-key block b (b0 <= i < b1) whatever segment they belong to, so every
+    // thread walks about 32 keys.  Its segments are those whose anchor lies in
+    // b: all but the last end inside b (the next anchor is in b); the last
+    // ends at e_last = next_anchor(a_last) and is short iff that is within 96
+    // keys.  The keys of b before its first anchor (the prefix piece) belong
+    // to the segment P of the last anchor aP before b0; when P is short and
+    // starts in this window, the thread narrows P's cone over them and leaves
+    // the partial cone in shared memory, where P's owner merges it (the cone
+    // is a max of lower and a min of upper fractions over the keys, so pieces
+    // merge exactly).  Keys past the window (at most 95, of the window's last
+    // segment) are walked by that segment's owner.
+    const uint32_t b0 = w0 + tid * kFB, b1 = min(b0 + kFB, w1);
+    const bool has_block = tid < nw;
+    uint32_t a_first = 0, a_last = 0, e_last = kNone;
     if (word) {
-        const uint32_t b0 = w0 + tid * kFB;
         a_first = b0 + (uint32_t)(__ffs(word) - 1);
         a_last = b0 + 31u - (uint32_t)__clz(word);
         e_last = next_anchor(a_last);
-        end = e_last != kNone ? e_last : a_last;
     }
-    const uint64_t range = end > a_first + 1 ? st(end - 1) - st(a_first) : 0;
+    uint32_t aP = kNone;  // P's anchor, or kNone: no prefix piece to walk
+    if (has_block && !(word & 1u)) {
+        for (uint32_t back = 1; back <= 3 && back <= tid && aP == kNone; ++back) {
+            const uint32_t wb = s_T[tid - back];
+            if (wb) aP = w0 + (tid - back) * kFB + 31u - (uint32_t)__clz(wb);
+        }
+        if (aP != kNone && next_anchor(aP) == kNone) aP = kNone;  // P is long: its own walk
+    }
+    const bool tail = word && e_last != kNone && e_last > b1;  // the last segment runs past the block
+    const uint32_t pend = word ? a_first : b1;                  // end of the prefix piece
+    const uint32_t lo = aP != kNone ? aP : (word ? a_first : b1);
+    // the block's keys to walk: up to a long last segment's anchor, else to b1
+    const uint32_t wend = word && e_last == kNone ? a_last + 1 : (has_block ? b1 : lo);
+    const uint32_t wstart = aP != kNone ? b0 : lo + 1;  // first key walked
+    const uint32_t hi = tail ? e_last : wend;            // past the last key any piece of this thread's cones holds
+    const uint64_t range = hi > lo + 1 ? st(hi - 1) - st(lo) : 0;
     const bool narrow = __all_sync(0xFFFFFFFFu, range + (uint64_t)eps + 1 < (1ull << 31));
     const uint64_t j_first = j;
-    if (end > a_first) {
-        // pass 1: cones (the anchors are known, so every key only narrows its
-        // segment's cone); a closed cone goes to scratch, its slope is taken
-        // in pass S, so that no lane waits on another lane's divisions here
-        uint32_t a = a_first;
-        uint64_t ka = st(a);
-        Frac c = frac_open();
-        Frac32 c32 = frac32_open();
-        auto close = [&](uint32_t e) {
-            Frac f = c;
-            if (narrow) f = Frac{(int64_t)c32.X, c32.E, (uint64_t)c32.Y, c32.F};
-            // short segment: E, F <= 95 and |X|, Y < 2^38, packed in 16 bytes; E = 0 marks one key
-            const uint32_t E = e - a >= 2 ? f.E : 0u;
-            cones[j] = make_ulonglong2(((uint64_t)f.X & ((1ull << 48) - 1)) | ((uint64_t)E << 48) |
-                                           ((uint64_t)f.F << 56),
-                                       f.Y);
-            icpt[j] = (KT)ka;
-            start[j] = (uint16_t)a;
-        };
-        for (uint32_t i = a_first + 1; i < end; ++i) {
+    const uint32_t nown = __popc(word);                           // segments owned, the last maybe long
+    const uint32_t nshort = nown - (word && e_last == kNone ? 1u : 0u);
+    ulonglong2* const s_pc = s_u.pieces.pc;
+    uint32_t* const s_pa = s_u.pieces.pa;
+    uint32_t* const s_pz = (uint32_t*)s_u.pieces.pc;  // reused once pass 1's merges are done
+
+    // cone state of the piece being walked
+    Frac c = frac_open();
+    Frac32 c32 = frac32_open();
+    auto cone_key = [&](uint64_t Ki, uint64_t ka, uint32_t d) {
+        if (narrow) {
+            const uint32_t D = (uint32_t)(Ki - ka);
+            const int32_t xl = (int32_t)D - (int32_t)eps;
+            const uint32_t yh = D + (uint32_t)eps + 1u;
+            if ((int64_t)xl * c32.E > (int64_t)c32.X * d) { c32.X = xl; c32.E = d; }
+            if ((uint64_t)yh * c32.F < (uint64_t)c32.Y * d) { c32.Y = yh; c32.F = d; }
+        } else {
+            const uint64_t D = Ki - ka;
+            const int64_t xl = (int64_t)D - eps;
+            const uint64_t yh = D + (uint64_t)eps + 1;
+            if (frac_gt(xl, d, c.X, c.E)) { c.X = xl; c.E = d; }
+            if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { c.Y = yh; c.F = d; }
+        }
+    };
+    // a cone packed in 16 bytes: E, F <= 95 and |X|, Y < 2^47; E = 0 marks one key
+    auto pack = [&](uint32_t nkeys) {
+        Frac f = c;
+        if (narrow) f = Frac{(int64_t)c32.X, c32.E, (uint64_t)c32.Y, c32.F};
+        const uint32_t E = nkeys >= 2 ? f.E : 0u;
+        return make_ulonglong2(((uint64_t)f.X & ((1ull << 48) - 1)) | ((uint64_t)E << 48) | ((uint64_t)f.F << 56),
+                               f.Y);
+    };
+    auto reset = [&]() {
+        c = frac_open();
+        c32 = frac32_open();
+    };
+
+    // pass 1: cones.  A closed cone goes to scratch; its slope is taken in
+    // pass S, so that no lane waits on another lane's divisions here.
+    s_pa[tid] = kNone;
+    {
+        uint32_t a = lo;
+        uint64_t ka = lo < hi ? st(lo) : 0;
+        for (uint32_t i = wstart; i < wend; ++i) {
             const uint64_t Ki = st(i);
             if (is_anchor(i)) {
-                close(i);
-                ++j;
+                if (a == aP && i == pend) {  // the prefix piece ends at the block's first anchor
+                    s_pc[tid] = pack(2);
+                    s_pa[tid] = aP;
+                } else {
+                    cones[j] = pack(i - a);
+                    icpt[j] = (KT)ka;
+                    start[j] = (uint16_t)a;
+                    ++j;
+                }
                 a = i;
                 ka = Ki;
-                c = frac_open();
-                c32 = frac32_open();
+                reset();
                 continue;
             }
-            const uint32_t d = i - a;
-            if (narrow) {
-                const uint32_t D = (uint32_t)(Ki - ka);
-                const int32_t xl = (int32_t)D - (int32_t)eps;
-                const uint32_t yh = D + (uint32_t)eps + 1u;
-                if ((int64_t)xl * c32.E > (int64_t)c32.X * d) { c32.X = xl; c32.E = d; }
-                if ((uint64_t)yh * c32.F < (uint64_t)c32.Y * d) { c32.Y = yh; c32.F = d; }
-            } else {
-                const uint64_t D = Ki - ka;
-                const int64_t xl = (int64_t)D - eps;
-                const uint64_t yh = D + (uint64_t)eps + 1;
-                if (frac_gt(xl, d, c.X, c.E)) { c.X = xl; c.E = d; }
-                if (yh * (uint64_t)c.F < c.Y * (uint64_t)d) { c.Y = yh; c.F = d; }
-            }
+            cone_key(Ki, ka, i - a);
         }
-        close(end);
-        const uint64_t j_end = j + 1;
-        // pass S: the slope of every segment from its cone (floor midpoint, 0 for one key)
-        for (uint64_t q = j_first; q < j_end; ++q) {
-            const ulonglong2 cc = cones[q];
-            const uint32_t E = (uint32_t)(cc.x >> 48) & 0xFFu;
-            int64_t M = 0;
-            if (E) {
-                Frac f;
-                f.X = (int64_t)(cc.x << 16) >> 16;  // sign-extend the 48-bit numerator
-                f.E = E;
-                f.F = (uint32_t)(cc.x >> 56);
-                f.Y = cc.y;
-                M = frac_slope(f, magic);
-            }
-            slope[q] = M;
+        if (aP != kNone && !word) {  // the whole block is prefix piece
+            s_pc[tid] = pack(2);
+            s_pa[tid] = aP;
+        } else if (word && e_last != kNone && !tail) {  // the last segment ends at b1
+            cones[j] = pack(e_last - a);
+            icpt[j] = (KT)ka;
+            start[j] = (uint16_t)a;
         }
-        // pass 2: widths, from the slopes just written (plain loads: this thread wrote them)
+        __syncthreads();
+        if (tail) {
+            // merge the following blocks' prefix pieces of this segment, then
+            // walk its keys past the window
+            for (uint32_t u = tid + 1; u < min(tid + 4u, nw) && s_pa[u] == a_last; ++u) {
+                const ulonglong2 p = s_pc[u];
+                const int64_t X = (int64_t)(p.x << 16) >> 16;
+                const uint32_t E = (uint32_t)(p.x >> 48) & 0xFFu, F = (uint32_t)(p.x >> 56);
+                if (narrow) {
+                    if (X * (int64_t)c32.E > (int64_t)c32.X * (int64_t)E) { c32.X = (int32_t)X; c32.E = E; }
+                    if (p.y * (uint64_t)c32.F < (uint64_t)c32.Y * F) { c32.Y = (uint32_t)p.y; c32.F = F; }
+                } else {
+                    if (frac_gt(X, E, c.X, c.E)) { c.X = X; c.E = E; }
+                    if (p.y * (uint64_t)c.F < c.Y * (uint64_t)F) { c.Y = p.y; c.F = F; }
+                }
+            }
+            for (uint32_t i = max(w1, wend); i < e_last; ++i) cone_key(st(i), ka, i - a);
+            cones[j] = pack(e_last - a);
+            icpt[j] = (KT)ka;
+            start[j] = (uint16_t)a;
+        }
+    }
+    // pass S: the slope of every owned short segment (floor midpoint, 0 for one key)
+    for (uint64_t q = j_first; q < j_first + nshort; ++q) {
+        const ulonglong2 cc = cones[q];
+        const uint32_t E = (uint32_t)(cc.x >> 48) & 0xFFu;
+        int64_t M = 0;
+        if (E) {
+            Frac f;
+            f.X = (int64_t)(cc.x << 16) >> 16;  // sign-extend the 48-bit numerator
+            f.E = E;
+            f.F = (uint32_t)(cc.x >> 56);
+            f.Y = cc.y;
+            M = frac_slope(f, magic);
+        }
+        slope[q] = M;
+    }
+    __syncthreads();  // P's slope, written by its owner, is read below
+    // pass 2: widths, walked the same way
+    {
         j = j_first;
-        a = a_first;
-        ka = st(a);
-        int64_t M = slope[j];
+        uint32_t a = lo;
+        uint64_t ka = lo < hi ? st(lo) : 0;
+        int64_t M = aP != kNone ? slope[j_first - 1] : (word ? slope[j_first] : 0);
         uint32_t zmax = 0;
-        for (uint32_t i = a_first + 1; i < end; ++i) {
+        for (uint32_t i = wstart; i < wend; ++i) {
             const uint64_t Ki = st(i);
             if (is_anchor(i)) {
-                width[j] = (uint8_t)(32u - __clz(zmax));
-                ++j;
+                if (a == aP && i == pend) {
+                    s_pz[tid] = zmax;
+                } else {
+                    width[j] = (uint8_t)(32u - __clz(zmax));
+                    ++j;
+                }
                 a = i;
                 ka = Ki;
-                M = slope[j];
+                M = j < j_first + nshort ? slope[j] : 0;
                 zmax = 0;
                 continue;
             }
             zmax = max(zmax, zigzag32((int64_t)(Ki - ka) - line_at(M, i - a)));
         }
-        width[j] = (uint8_t)(32u - __clz(zmax));
-        ++j;
+        if (aP != kNone && !word) {
+            s_pz[tid] = zmax;
+        } else if (word && e_last != kNone && !tail) {
+            width[j] = (uint8_t)(32u - __clz(zmax));
+        }
+        __syncthreads();
+        if (tail) {
+            for (uint32_t u = tid + 1; u < min(tid + 4u, nw) && s_pa[u] == a_last; ++u) zmax = max(zmax, s_pz[u]);
+            for (uint32_t i = max(w1, wend); i < e_last; ++i)
+                zmax = max(zmax, zigzag32((int64_t)(st(i) - ka) - line_at(M, i - a)));
+            width[j] = (uint8_t)(32u - __clz(zmax));
+        }
     }
+    j = j_first + nown - 1;  // the last owned segment (used below when it is long)
+    __syncthreads();         // the pieces' storage becomes the long-segment list
     if (word && e_last == kNone) {
         // the segment at a_last is longer than 96 keys: its slope came from the chain's walk
         const uint32_t a = a_last;
