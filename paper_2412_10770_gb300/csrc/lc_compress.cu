@@ -86,17 +86,129 @@ __device__ __forceinline__ Frac shfl_frac(const Frac& v, int src) {
     return f;
 }
 
+// The cone of frac_step with 32-bit numerators, for walks whose key range
+// (plus eps + 1) stays below 2^31: then every D - eps and D + eps + 1 fits in
+// an int32 and every cross product in 48 bits, and the int64 cap on the
+// slope (2^31 per key) can never be reached.  Same decisions as frac_step.
+struct Frac32 {
+    int32_t X;
+    uint32_t E;
+    uint32_t Y;
+    uint32_t F;
+};
+__device__ __forceinline__ Frac32 frac32_open() { return Frac32{INT32_MIN, 1u, 0x7FFFFFFFu, 1u}; }
+
 constexpr uint32_t kWalkLane = 8;                 // keys per lane in one step of the warp walk
 constexpr uint32_t kWalkStep = 32 * kWalkLane;    // 256 keys per step
 
+// The walk's cone arithmetic in two widths with the same decisions: 64-bit
+// (Frac) in general, 32-bit numerators (Frac32) for a step whose keys all lie
+// less than 2^31 - eps - 1 above the anchor, where every numerator fits an
+// int32 and every cross product 48 bits (and no key reaches the int64 cap).
+// The open cone is -2^31/1 .. 2^31/1 in both.
+struct WalkWide {
+    using F = Frac;
+    static __device__ __forceinline__ F open() { return frac_open(); }
+    static __device__ __forceinline__ F key(uint64_t Ki, uint32_t i, uint32_t x, uint64_t kx, uint32_t n, int64_t eps) {
+        return key_frac(Ki, i, x, kx, n, eps);
+    }
+    static __device__ __forceinline__ void meet(F& v, const F& o) { frac_meet(v, o); }
+    static __device__ __forceinline__ bool ok(const F& c) { return frac_ok(c); }
+    static __device__ __forceinline__ F shfl(const F& v, int src) { return shfl_frac(v, src); }
+    static __device__ __forceinline__ F shfl_up(const F& v, int off) {
+        F o;
+        o.X = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
+        o.E = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
+        o.Y = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
+        o.F = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
+        return o;
+    }
+    static __device__ __forceinline__ F from(const Frac& f) { return f; }
+    static __device__ __forceinline__ Frac wide(const F& f) { return f; }
+};
+struct WalkNarrow {
+    using F = Frac32;
+    static __device__ __forceinline__ F open() { return Frac32{INT32_MIN, 1u, 0x80000000u, 1u}; }
+    static __device__ __forceinline__ F key(uint64_t Ki, uint32_t i, uint32_t x, uint64_t kx, uint32_t n, int64_t eps) {
+        if (i >= n) return open();
+        const uint32_t D = (uint32_t)(Ki - kx), d = i - x;
+        return Frac32{(int32_t)D - (int32_t)eps, d, D + (uint32_t)eps + 1u, d};
+    }
+    static __device__ __forceinline__ void meet(F& v, const F& o) {
+        if ((int64_t)o.X * v.E > (int64_t)v.X * o.E) { v.X = o.X; v.E = o.E; }
+        if ((uint64_t)o.Y * v.F < (uint64_t)v.Y * o.F) { v.Y = o.Y; v.F = o.F; }
+    }
+    static __device__ __forceinline__ bool ok(const F& c) {
+        return c.X < 0 || (uint64_t)(uint32_t)c.X * c.F < (uint64_t)c.Y * c.E;
+    }
+    static __device__ __forceinline__ F shfl(const F& v, int src) {
+        return Frac32{__shfl_sync(0xFFFFFFFFu, v.X, src), __shfl_sync(0xFFFFFFFFu, v.E, src),
+                      __shfl_sync(0xFFFFFFFFu, v.Y, src), __shfl_sync(0xFFFFFFFFu, v.F, src)};
+    }
+    static __device__ __forceinline__ F shfl_up(const F& v, int off) {
+        return Frac32{__shfl_up_sync(0xFFFFFFFFu, v.X, off), __shfl_up_sync(0xFFFFFFFFu, v.E, off),
+                      __shfl_up_sync(0xFFFFFFFFu, v.Y, off), __shfl_up_sync(0xFFFFFFFFu, v.F, off)};
+    }
+    static __device__ __forceinline__ F from(const Frac& f) { return Frac32{(int32_t)f.X, f.E, (uint32_t)f.Y, f.F}; }
+    static __device__ __forceinline__ Frac wide(const F& f) {
+        return Frac{(int64_t)f.X, f.E, (uint64_t)f.Y, f.F};
+    }
+};
+
+// One step of the warp walk over keys p .. p + 255 (cur: lane l's keys
+// p + 8l .. p + 8l + 7): lane l intersects the slope intervals of its keys,
+// an inclusive scan over the lanes gives the cone after every lane's keys,
+// and the first lane whose cone is empty holds the next anchor, which that
+// lane finds key by key from the cone before it.  Returns true with the
+// anchor in *end and the segment's cone in *fin when the segment ends in
+// this step; else carries the cone on and returns false.
+template <typename W>
+__device__ __forceinline__ bool walk_step(const uint64_t (&cur)[kWalkLane], uint32_t p, uint32_t x, uint64_t kx,
+                                          uint32_t n, int64_t eps, uint32_t lane, Frac& carried, uint32_t* end,
+                                          Frac* fin) {
+    using F = typename W::F;
+    const F cone = W::from(carried);
+    const uint32_t i0 = p + kWalkLane * lane;
+    F v = W::open();
+#pragma unroll
+    for (uint32_t u = 0; u < kWalkLane; ++u) W::meet(v, W::key(cur[u], i0 + u, x, kx, n, eps));
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const F o = W::shfl_up(v, off);
+        if (lane >= (uint32_t)off) W::meet(v, o);
+    }
+    W::meet(v, cone);
+    const uint32_t badm = __ballot_sync(0xFFFFFFFFu, !W::ok(v));
+    if (badm) {
+        const int bl = __ffs(badm) - 1;
+        const F before = W::shfl(v, bl > 0 ? bl - 1 : 0);
+        F c = bl > 0 ? before : cone;
+        uint32_t brk = 0;
+        if (lane == (uint32_t)bl) {
+            brk = kWalkLane;
+#pragma unroll
+            for (uint32_t u = 0; u < kWalkLane; ++u) {
+                if (brk != kWalkLane) continue;
+                F t = c;
+                W::meet(t, W::key(cur[u], i0 + u, x, kx, n, eps));
+                if (!W::ok(t)) brk = u;
+                else c = t;
+            }
+        }
+        brk = __shfl_sync(0xFFFFFFFFu, brk, bl);
+        *fin = W::wide(W::shfl(c, bl));
+        *end = min(p + kWalkLane * (uint32_t)bl + brk, n);
+        return true;
+    }
+    carried = W::wide(W::shfl(v, 31));
+    return false;
+}
+
 // The greedy cone (Def. 2, shrinking-cone reading) with a whole warp, 256
-// keys per step: lane l intersects the slope intervals of keys p + 8l ..
-// p + 8l + 7, an inclusive scan over the lanes gives the cone after every
-// lane's keys, and the first lane whose cone is empty holds the next anchor,
-// which that lane finds key by key from the cone before it.  The keys of the
-// next step are loaded while this one computes.  Called with all 32 lanes
-// active and warp-uniform arguments.  *fin receives the cone of the
-// segment's keys (every lane).
+// keys per step (walk_step); the keys of the next step are loaded while this
+// one computes, and a step runs in 32-bit fractions when its keys allow.
+// Called with all 32 lanes active and warp-uniform arguments.  *fin
+// receives the cone of the segment's keys (every lane).
 template <typename KT>
 __device__ __forceinline__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t x, uint32_t n, int64_t eps, uint32_t lane,
                               Frac* fin) {
@@ -121,44 +233,17 @@ __device__ __forceinline__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t
             }
             if (pn + kWalkAhead < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(K + pn + kWalkAhead + 8 * lane));
         }
+        // the lane's largest key offset (keys are sorted: its last key in the chunk)
         const uint32_t i0 = p + kWalkLane * lane;
-        Frac v = frac_open();
+        uint64_t dmax = 0;
 #pragma unroll
-        for (uint32_t u = 0; u < kWalkLane; ++u) frac_meet(v, key_frac(cur[u], i0 + u, x, kx, n, eps));
-        // inclusive scan of the lanes' cones, then the carried cone
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            Frac o;
-            o.X = __shfl_up_sync(0xFFFFFFFFu, v.X, off);
-            o.E = __shfl_up_sync(0xFFFFFFFFu, v.E, off);
-            o.Y = __shfl_up_sync(0xFFFFFFFFu, v.Y, off);
-            o.F = __shfl_up_sync(0xFFFFFFFFu, v.F, off);
-            if (lane >= (uint32_t)off) frac_meet(v, o);
-        }
-        frac_meet(v, cone);
-        const uint32_t badm = __ballot_sync(0xFFFFFFFFu, !frac_ok(v));
-        if (badm) {
-            // lane bl holds the first key that empties the cone: find it from the cone before the lane
-            const int bl = __ffs(badm) - 1;
-            const Frac before = shfl_frac(v, bl > 0 ? bl - 1 : 0);
-            Frac c = bl > 0 ? before : cone;
-            uint32_t brk = 0;
-            if (lane == (uint32_t)bl) {
-                brk = kWalkLane;
-#pragma unroll
-                for (uint32_t u = 0; u < kWalkLane; ++u) {
-                    if (brk != kWalkLane) continue;
-                    Frac t = c;
-                    frac_meet(t, key_frac(cur[u], i0 + u, x, kx, n, eps));
-                    if (!frac_ok(t)) brk = u;
-                    else c = t;
-                }
-            }
-            brk = __shfl_sync(0xFFFFFFFFu, brk, bl);
-            *fin = shfl_frac(c, bl);
-            return min(p + kWalkLane * (uint32_t)bl + brk, n);
-        }
-        cone = shfl_frac(v, 31);
+        for (uint32_t u = 0; u < kWalkLane; ++u)
+            if (i0 + u < n) dmax = cur[u] - kx;
+        const bool narrow = __all_sync(0xFFFFFFFFu, dmax + (uint64_t)eps + 1 < (1ull << 31));
+        uint32_t end = 0;
+        if (narrow ? walk_step<WalkNarrow>(cur, p, x, kx, n, eps, lane, cone, &end, fin)
+                   : walk_step<WalkWide>(cur, p, x, kx, n, eps, lane, cone, &end, fin))
+            return end;
         p = pn;
     }
     *fin = cone;
@@ -232,17 +317,6 @@ struct Staged64 {
     }
 };
 
-// The cone of frac_step with 32-bit numerators, for walks whose key range
-// (plus eps + 1) stays below 2^31: then every D - eps and D + eps + 1 fits in
-// an int32 and every cross product in 48 bits, and the int64 cap on the
-// slope (2^31 per key) can never be reached.  Same decisions as frac_step.
-struct Frac32 {
-    int32_t X;
-    uint32_t E;
-    uint32_t Y;
-    uint32_t F;
-};
-__device__ __forceinline__ Frac32 frac32_open() { return Frac32{INT32_MIN, 1u, 0x7FFFFFFFu, 1u}; }
 
 // What one speculative walk leaves for its two blocks: its anchors in each
 // block, its first anchor at or after the span's start (entry of block 0), at
