@@ -1034,11 +1034,12 @@ def run_serve(args):
 def run_e2e(args, cols, lc, torch, stream):
     """The same step through the C ABI with inputs and results in pinned host
     memory: every step copies keys and queries in and decoded keys and query
-    results out.  The copies are pipelined the way a caller would do it: each
-    input travels in on one copy stream (keys first, then the windows and the
-    queries, the next column's while this one computes), each result travels
-    out on another as soon as the call that makes it is done, over two sets of
-    device buffers ordered by events."""
+    results out.  The copies are pipelined the way a streaming caller would do
+    it: each input travels in on one copy stream (keys first, then the windows
+    and the queries, the next column's while this one computes), each result
+    travels out on another as soon as the call that makes it is done, over two
+    sets of device buffers ordered by events, and the steps run back to back
+    (the timed region ends when the last step's results are on the host)."""
     N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
     pinned = []
     for g, host, dev in cols:
@@ -1062,14 +1063,17 @@ def run_e2e(args, cols, lc, torch, stream):
         e.record(s)
         return e
 
-    def step():
+    def run(steps):
+        """steps x C columns back to back: the copies of one step overlap the
+        compute and copies of the next; the columns are freed at the end."""
         in_ready = [None, None]   # per buffer set: one event per input group
         in_free = [None, None]    # the compute that last read the set's inputs
         out_free = [None, None]   # the copies that last read the set's outputs
         live = []
+        order = [c for _ in range(steps) for c in range(C)]
 
-        def copy_in(c):
-            b = c % 2
+        def copy_in(k):
+            b, c = k % 2, order[k]
             if in_free[b] is not None:
                 s_in.wait_event(in_free[b])
             evs = []
@@ -1087,10 +1091,10 @@ def run_e2e(args, cols, lc, torch, stream):
                     outs_h[nm].copy_(d_out[b][nm], non_blocking=True)
 
         copy_in(0)
-        for c in range(C):
-            b = c % 2
-            if c + 1 < C:
-                copy_in(c + 1)  # queued before this column's compress blocks the host
+        for k in range(len(order)):
+            b = k % 2
+            if k + 1 < len(order):
+                copy_in(k + 1)  # queued before this column's compress blocks the host
             if out_free[b] is not None:
                 stream.wait_event(out_free[b])
             di, do, ev = d_in[b], d_out[b], in_ready[b]
@@ -1114,11 +1118,10 @@ def run_e2e(args, cols, lc, torch, stream):
         for col in live:
             col.free()
 
-    step()
+    run(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
+    run(args.steps)
     torch.cuda.synchronize()
     return {"ms": 1e3 * (time.perf_counter() - t0) / args.steps, "h2d": h2d, "d2h": d2h}
 
