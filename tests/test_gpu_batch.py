@@ -88,3 +88,21 @@ def test_device_generator_lists_are_sorted_samples():
     for l in range(0, 2000, 7):
         x = h[int(begin[l]):int(begin[l + 1])].astype(np.int64)
         assert (np.diff(x) > 0).all() and x.min() >= 0 and x.max() < 5 * 10**7
+
+
+def test_many_short_lists_large_directories():
+    # 60000 lists of 16-40 ids: the batch's descriptors and header exceed the
+    # 1 MB above which the compressor's small-transfer staging hands them to
+    # an ordinary copy; the bytes must not change
+    rng = np.random.default_rng(11)
+    lens = rng.integers(16, 41, size=60000)
+    parts = [np.sort(rng.choice(1_000_000, size=int(k), replace=False)).astype(np.uint32) for k in lens]
+    ids = np.concatenate(parts)
+    begin = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    eps = np.where(lens < 28, 3, 15).astype(np.uint64)
+    log2 = np.full(len(lens), 16, dtype=np.uint8)
+    d = torch.from_numpy(ids).cuda()
+    col = lc.lc_compress_batch(d, begin, eps, log2)
+    assert lc.lc_serialize(col) == oracle.compress_lists(ids, begin, eps, log2)
+    assert torch.equal(lc.lc_decode_batch(col), d)
+    col.free()
