@@ -123,8 +123,10 @@ struct ColView {
     const SegRec* recs;                // [L]
     const RankWord* rank;              // [ceil(N / 64)]
     const uint64_t* rdx;               // radix table over the intercepts [B + 1]
+    const void* ioff;                  // [L] intercept - its bucket's first value, ioff_bytes each
     uint64_t kmin, kmax;               // first and last key
     uint32_t rdx_shift;                // bucket width 2^rdx_shift
+    uint32_t ioff_bytes;               // 2 or 4; 0: no offsets (buckets wider than 2^32), use icpt
     uint32_t max_tile_segs;            // most segments meeting one decode tile
     uint32_t key_bytes;
     uint32_t* status;

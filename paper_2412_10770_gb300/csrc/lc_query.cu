@@ -436,6 +436,12 @@ __device__ __forceinline__ uint32_t ld32_hint(const void* ptr, uint64_t pol) {
     return r;
 }
 
+__device__ __forceinline__ uint32_t ld16_hint(const void* ptr, uint64_t pol) {
+    uint16_t r;
+    asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(ptr), "l"(pol));
+    return r;
+}
+
 __device__ __forceinline__ SegRec load_rec_hint(const SegRec* p, uint64_t pol) {
     const ulonglong2 a = ld2_hint(p, pol), b = ld2_hint((const ulonglong2*)p + 1, pol);
     SegRec r;
@@ -500,12 +506,26 @@ __device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x
     if (x > v.kmax) return v.N;
     const uint64_t q = (x - v.kmin) >> v.rdx_shift;
     uint64_t lo = min(ld64_hint(v.rdx + q, keep), v.L), hi = min(ld64_hint(v.rdx + q + 1, keep), v.L);
-    while (lo < hi) {  // count of intercepts < x, within [rdx[q], rdx[q+1])
-        const uint64_t mid = (lo + hi) >> 1;
-        const uint64_t k = sizeof(KT) == 8 ? ld64_hint((const uint64_t*)v.icpt + mid, keep)
-                                           : (uint64_t)ld32_hint((const uint32_t*)v.icpt + mid, keep);
-        if (k < x) lo = mid + 1;
-        else hi = mid;
+    if (v.ioff_bytes) {
+        // count of intercepts < x within [rdx[q], rdx[q+1]): all of them lie in
+        // bucket q, so their offsets from the bucket's first value compare as
+        // the intercepts do, and the offsets array is a quarter of the size
+        const uint32_t xo = (uint32_t)((x - v.kmin) & ((1ull << v.rdx_shift) - 1));
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            const uint32_t k = v.ioff_bytes == 2 ? ld16_hint((const uint16_t*)v.ioff + mid, keep)
+                                                 : ld32_hint((const uint32_t*)v.ioff + mid, keep);
+            if (k < xo) lo = mid + 1;
+            else hi = mid;
+        }
+    } else {
+        while (lo < hi) {  // count of intercepts < x, within [rdx[q], rdx[q+1])
+            const uint64_t mid = (lo + hi) >> 1;
+            const uint64_t k = sizeof(KT) == 8 ? ld64_hint((const uint64_t*)v.icpt + mid, keep)
+                                               : (uint64_t)ld32_hint((const uint32_t*)v.icpt + mid, keep);
+            if (k < x) lo = mid + 1;
+            else hi = mid;
+        }
     }
     const uint64_t j = lo ? lo - 1 : 0;  // lo >= 1 for sorted keys: icpt[0] = kmin < x
     return lower_bound_in_segment(v, x, j, stream);
@@ -828,6 +848,14 @@ __global__ void radix_fine_kernel(ColView v, uint64_t* __restrict__ rdx, uint64_
     }
 }
 
+// ioff[j] = intercept j minus the first value of its radix bucket.
+template <typename KT, typename OT>
+__global__ void ioff_kernel(ColView v, OT* __restrict__ ioff) {
+    const uint64_t mask = (1ull << v.rdx_shift) - 1;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < v.L; j += (uint64_t)gridDim.x * blockDim.x)
+        ioff[j] = (OT)((ld_icpt<KT>(v.icpt, j) - v.kmin) & mask);
+}
+
 // ends[0] = first key, ends[1] = last key (N >= 1).
 __global__ void ends_kernel(ColView v, uint64_t* __restrict__ ends) {
     if (threadIdx.x == 0) {
@@ -941,7 +969,8 @@ int build_derived(lc_column* col, cudaStream_t st) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t off_rank = al(sizeof(SegRec) * L);
     const size_t off_rdx = al(off_rank + sizeof(RankWord) * nw);
-    const size_t bytes2 = al(off_rdx + (B ? 8 * (B + 1) : 0)) + 256;
+    const size_t off_ioff = al(off_rdx + (B ? 8 * (B + 1) : 0));
+    const size_t bytes2 = al(off_ioff + (B ? 4 * L : 0)) + 256;
     if (cudaMallocAsync((void**)&col->derived2, bytes2, st) != cudaSuccess) {
         col->derived2 = nullptr;
         return LC_ERR_NOMEM;
@@ -970,6 +999,8 @@ int build_derived(lc_column* col, cudaStream_t st) {
     v.recs = recs;
     v.rank = rank;
     v.rdx = B ? rdx : nullptr;
+    v.ioff = nullptr;
+    v.ioff_bytes = 0;
     v.kmin = v.kmax = 0;
     v.rdx_shift = 0;
     v.key_bytes = col->key_bytes;
@@ -1044,6 +1075,24 @@ int build_derived(lc_column* col, cudaStream_t st) {
         note_launch(2);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
+        // intercept offsets within their buckets, 16 or 32 bits when the buckets are that narrow
+        if (sh <= 32) {
+            uint8_t* ioff = col->derived2 + off_ioff;
+            const unsigned gi = (unsigned)std::min<uint64_t>((L + 255) / 256, 65535);
+            KTime kt("derived_radix", st);
+            if (sh <= 16) {
+                if (col->key_bytes == 4) ioff_kernel<uint32_t, uint16_t><<<gi, 256, 0, st>>>(v, (uint16_t*)ioff);
+                else ioff_kernel<uint64_t, uint16_t><<<gi, 256, 0, st>>>(v, (uint16_t*)ioff);
+            } else {
+                if (col->key_bytes == 4) ioff_kernel<uint32_t, uint32_t><<<gi, 256, 0, st>>>(v, (uint32_t*)ioff);
+                else ioff_kernel<uint64_t, uint32_t><<<gi, 256, 0, st>>>(v, (uint32_t*)ioff);
+            }
+            note_launch();
+            rc = cuda_status(cudaGetLastError());
+            if (rc) return rc;
+            v.ioff = ioff;
+            v.ioff_bytes = sh <= 16 ? 2 : 4;
+        }
         return cuda_status(cudaStreamSynchronize(st));
     }
     v.max_tile_segs = 1;
