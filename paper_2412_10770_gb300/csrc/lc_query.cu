@@ -136,6 +136,7 @@ __device__ __forceinline__ DecStage dec_stage_at(uint8_t* smem, uint32_t ms, uin
 // arrive, so that the waiting threads see it.  A tile that does not fit the
 // stage (cannot happen: ms bounds every tile) or holds no wanted key is marked
 // and its barrier completed without copies.
+template <bool Approx = false>
 __device__ void dec_issue(const ColView& v, uint64_t t, uint64_t lo_key, uint64_t hi_key, void* out, uint32_t ms,
                           const DecStage& sd, uint64_t* bar, DecItem* it) {
     const TileDesc td = v.tiles[t];
@@ -160,10 +161,11 @@ __device__ void dec_issue(const ColView& v, uint64_t t, uint64_t lo_key, uint64_
         mbar_expect(bar, 0);
         return;
     }
-    mbar_expect(bar, nr * 16u + ns * 32u + td.pwn * 4u);
+    const uint32_t pwn = Approx ? 0u : td.pwn;  // the segments-only decode reads no payload
+    mbar_expect(bar, nr * 16u + ns * 32u + pwn * 4u);
     bulk_load(sd.rank, v.rank + d.r0, nr * 16u, bar);
     bulk_load(sd.rec, v.recs + d.j0, ns * 32u, bar);
-    if (td.pwn) bulk_load(sd.pay, v.pay32 + td.pw0, td.pwn * 4u, bar);
+    if (pwn) bulk_load(sd.pay, v.pay32 + td.pw0, pwn * 4u, bar);
 }
 
 // Two keys stored as one aligned vector.
@@ -185,7 +187,7 @@ __device__ __forceinline__ void st_pair(uint32_t* p, uint32_t a, uint32_t b) {
 // residuals sit next to each other in one 64-bit window of the payload, and
 // the pair goes out as one vector store.  An unpaired first or last key is
 // decoded alone.  An anchor (t = 0) has no residual: its field is taken as 0.
-template <typename KT>
+template <typename KT, bool Approx = false>
 __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd) {
     const uint32_t p0 = (uint32_t)(d.lo - d.kbeg), p1 = (uint32_t)(d.hi - d.kbeg);
     KT* __restrict__ out = (KT*)d.out + (d.lo - d.lo_key) - p0;  // out[p]: key kbeg + p
@@ -204,7 +206,7 @@ __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd
         const uint32_t w = (uint32_t)(r.kstart_w >> 56);
         const uint32_t lb = (uint32_t)r.bit1_n - pb0 + w * (t - 1u);
         const uint32_t q = min(lb >> 5, kPayWords - 2);
-        const uint32_t z = extract_bits(sd.pay[q], sd.pay[q + 1], lb & 31u, t ? w : 0u);
+        const uint32_t z = Approx ? 0u : extract_bits(sd.pay[q], sd.pay[q + 1], lb & 31u, t ? w : 0u);
         out[p] = (KT)(r.icpt + (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(z)));
     };
     if (threadIdx.x == kDecThreads - 1 && pa > p0 && p0 < p1) one(p0);
@@ -224,10 +226,14 @@ __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd
         const uint32_t lb = (uint32_t)r.bit1_n - pb0 + w * (t ? t - 1u : 0u);
         const uint32_t q = min(lb >> 5, kPayWords - 3);
         const uint32_t sh = lb & 31u;
-        const uint32_t a0 = sd.pay[q], a1 = sd.pay[q + 1], a2 = sd.pay[q + 2];
-        const uint64_t win = ((uint64_t)__funnelshift_r(a1, a2, sh) << 32) | __funnelshift_r(a0, a1, sh);
-        const uint64_t mask = (1ull << w) - 1ull;
-        const uint32_t za = (uint32_t)(win & mask), zb = (uint32_t)((win >> w) & mask);
+        uint32_t za = 0, zb = 0;
+        if (!Approx) {
+            const uint32_t a0 = sd.pay[q], a1 = sd.pay[q + 1], a2 = sd.pay[q + 2];
+            const uint64_t win = ((uint64_t)__funnelshift_r(a1, a2, sh) << 32) | __funnelshift_r(a0, a1, sh);
+            const uint64_t mask = (1ull << w) - 1ull;
+            za = (uint32_t)(win & mask);
+            zb = (uint32_t)((win >> w) & mask);
+        }
         const KT v0 = (KT)(r.icpt + (uint64_t)(line_at(r.slope, t) + (int64_t)unzigzag32(t ? za : 0u)));
         KT v1;
         if (starts1)
@@ -241,7 +247,7 @@ __device__ __forceinline__ void dec_compute(const DecItem& d, const DecStage& sd
 // The pipeline over work items w = blockIdx.x, blockIdx.x + gridDim.x, ...
 // < total; src(w, &view, &tile, &lo, &hi, &out) describes item w and is
 // called by all 32 lanes of warp 0 together.
-template <typename KT, typename Src>
+template <typename KT, typename Src, bool Approx = false>
 __device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint32_t ms) {
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ DecItem s_item[2];
@@ -259,7 +265,8 @@ __device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint
     // warp 0 describes the items (src is warp-collective), thread 0 issues
     if (threadIdx.x < 32) {
         src(w0, &vv, &t, &lo, &hi, &o);
-        if (threadIdx.x == 0) dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, 0), &s_bar[0], &s_item[0]);
+        if (threadIdx.x == 0)
+            dec_issue<Approx>(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, 0), &s_bar[0], &s_item[0]);
     }
     uint32_t k = 0;
     for (uint64_t w = w0; w < total; w += gridDim.x, ++k) {
@@ -268,7 +275,8 @@ __device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint
         if (threadIdx.x < 32 && wn < total) {
             src(wn, &vv, &t, &lo, &hi, &o);
             if (threadIdx.x == 0)
-                dec_issue(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, s ^ 1u), &s_bar[s ^ 1u], &s_item[s ^ 1u]);
+                dec_issue<Approx>(*vv, t, lo, hi, o, ms, dec_stage_at(smem, ms, s ^ 1u), &s_bar[s ^ 1u],
+                                  &s_item[s ^ 1u]);
         }
         const bool got = mbar_wait(&s_bar[s], (k >> 1) & 1u);
         if (__syncthreads_or(!got)) {
@@ -285,7 +293,7 @@ __device__ void dec_pipeline(uint64_t total, const Src& src, uint8_t* smem, uint
             return;
         }
         const DecItem d = s_item[s];
-        if (d.ok) dec_compute<KT>(d, dec_stage_at(smem, ms, s));
+        if (d.ok) dec_compute<KT, Approx>(d, dec_stage_at(smem, ms, s));
         __syncthreads();  // stage s is free for item k + 2
     }
 }
@@ -330,6 +338,18 @@ __device__ __forceinline__ uint64_t warp_last_le(const uint64_t* __restrict__ of
         b = min(b, a + step);
     }
     return a;
+}
+
+// Segments-only decode (Sec. III-C, approximate query processing without the
+// residuals): the decode pipeline over tiles t0 .. t0 + nt - 1 with every
+// residual taken as 0, so out[g - begin] = floor(f(g)), within eps of K[g];
+// no payload is read.
+template <typename KT>
+__global__ void __launch_bounds__(kDecThreads, 12) decode_approx_kernel(ColView v, uint64_t t0, uint64_t nt,
+                                                                    uint64_t begin, uint64_t end,
+                                                                    KT* __restrict__ out) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    dec_pipeline<KT, WholeSrc<KT>, true>(nt, WholeSrc<KT>{&v, t0, begin, end, out}, smem, v.max_tile_segs);
 }
 
 // Work items of a multi-range decode: range r covers tiles
@@ -600,26 +620,6 @@ __global__ void quantile_kernel(ColView v, const uint64_t* __restrict__ ks, uint
         }
         const uint64_t i = quantile_index(v.N, k, q);
         out[r] = (KT)(exact ? access_one(v, i, keep, stream) : predict_one(v, i, keep, stream));
-    }
-}
-
-// Segments-only decode of keys [begin, begin + count): out[g - begin] =
-// floor(f(g)), within eps of K[g] (Sec. III-C, approximate query processing
-// without the residuals).  Four consecutive keys per thread share one rank
-// word and usually one record.
-template <typename KT>
-__global__ void __launch_bounds__(256) decode_approx_kernel(ColView v, uint64_t begin, uint64_t count,
-                                                            KT* __restrict__ out) {
-    const uint64_t keep = policy_keep(), stream = policy_stream();
-    const uint64_t groups = (count + 3) / 4;
-    for (uint64_t gq = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gq < groups;
-         gq += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t o0 = 4 * gq;
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) {
-            const uint64_t o = o0 + u;
-            if (o < count) out[o] = (KT)predict_one(v, begin + o, keep, stream);
-        }
     }
 }
 
@@ -1236,13 +1236,32 @@ int quantile(const lc_column* col, const uint64_t* ks, uint64_t m, uint64_t q, i
 
 int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st) {
     if (count == 0) return LC_OK;
-    const unsigned grid = (unsigned)std::min<uint64_t>((count / 4 + 256) / 256, (uint64_t)sm_count() * 16);
-    {
+    const uint64_t t0 = host_tile_of(col, begin), nt = host_tile_of(col, begin + count - 1) - t0 + 1;
+    const size_t smem = dec_smem(col->view.max_tile_segs);
+    if (col->key_bytes == 4) {
+        static bool attr = false;
+        if (!attr) {
+            int rc = cuda_status(cudaFuncSetAttribute(decode_approx_kernel<uint32_t>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem));
+            if (rc) return rc;
+            attr = true;
+        }
+        const unsigned grid = (unsigned)std::min<uint64_t>(nt, dec_grid(decode_approx_kernel<uint32_t>, smem));
         KTime kt("decode_approx", st);
-        if (col->key_bytes == 4)
-            decode_approx_kernel<uint32_t><<<grid, 256, 0, st>>>(col->view, begin, count, (uint32_t*)out);
-        else
-            decode_approx_kernel<uint64_t><<<grid, 256, 0, st>>>(col->view, begin, count, (uint64_t*)out);
+        decode_approx_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count,
+                                                                        (uint32_t*)out);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            int rc = cuda_status(cudaFuncSetAttribute(decode_approx_kernel<uint64_t>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem));
+            if (rc) return rc;
+            attr = true;
+        }
+        const unsigned grid = (unsigned)std::min<uint64_t>(nt, dec_grid(decode_approx_kernel<uint64_t>, smem));
+        KTime kt("decode_approx", st);
+        decode_approx_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count,
+                                                                        (uint64_t*)out);
     }
     note_launch();
     return cuda_status(cudaGetLastError());
