@@ -448,7 +448,7 @@ def main():
             mark()
             lc.lc_lower_bound(col, dev["vals"], out_lb, stream=stream)
             mark()
-            col.free()
+            col.free_async(stream)  # in stream order: the host runs on into the next column
             if ev is not None:
                 ev.append((g, marks))
 

@@ -357,7 +357,12 @@ int lc_deserialize(const void* host, uint64_t len, void* stream, lc_column** out
  * (LC_OK or the first LC_ERR_* recorded by a kernel).  Synchronous. */
 int lc_status(const lc_column* col, void* stream);
 
+/* Release the column.  lc_free first waits for the whole device;
+ * lc_free_async releases the device memory in the order of `stream` instead,
+ * so the host does not wait: every use of the column must be on `stream` or
+ * already complete.  The handle is invalid after either call. */
 void lc_free(lc_column* col);
+int lc_free_async(lc_column* col, void* stream);
 
 const char* lc_strerror(int status);
 

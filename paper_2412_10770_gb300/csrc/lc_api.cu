@@ -388,6 +388,23 @@ void lc_free(lc_column* col) {
     delete col;
 }
 
+int lc_free_async(lc_column* col, void* stream) {
+    if (!col) return LC_ERR_INVALID_ARG;
+    HTime ht("free");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != col->device) cudaSetDevice(col->device);
+    const cudaStream_t st = (cudaStream_t)stream;
+    int rc = LC_OK;
+    for (void* p : {(void*)col->blob, (void*)col->chunk_tile_begin, (void*)col->derived2})
+        if (p && !rc) rc = cuda_status(cudaFreeAsync(p, st));
+    if (cur != col->device) cudaSetDevice(cur);
+    delete[] col->h_ckb;
+    delete[] col->h_ctb;
+    delete col;
+    return rc;
+}
+
 static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
                            lc_column** out, bool jump);
 
@@ -812,7 +829,7 @@ int lc_deserialize(const void* host, uint64_t len, void* stream, lc_column** out
     if (rc) { lc_free(col); return rc; }
     cudaStream_t st = (cudaStream_t)stream;
     col->blob_cap = len;
-    if (cudaMalloc((void**)&col->blob, len) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&col->blob, len, st) != cudaSuccess) {  // stream-ordered, like lc_compress's
         col->blob = nullptr;
         lc_free(col);
         return LC_ERR_NOMEM;

@@ -31,7 +31,7 @@ LC_ERR_UNSUPPORTED = -10
 EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", "lc_decode_ranges_noalloc",
            "lc_decode_batch",
            "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
-           "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_strerror",
+           "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_free_async", "lc_strerror",
            "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free", "lc_server_create", "lc_server_submit",
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
@@ -122,6 +122,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_deserialize": ([p, u64, p, pp], i32),
         "lc_status": ([p, p], i32),
         "lc_free": ([p], None),
+        "lc_free_async": ([p, p], i32),
         "lc_strerror": ([i32], ctypes.c_char_p),
         "lc_version": ([], i32),
         "lc_launch_count": ([], u64),
@@ -205,6 +206,13 @@ class Column:
     def free(self) -> None:
         if self.handle and self.handle.value and _lib is not None:
             _lib.lc_free(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def free_async(self, stream=None) -> None:
+        """lc_free_async: release in the order of `stream` without waiting."""
+        if self.handle and self.handle.value and _lib is not None:
+            h, self.handle = self.handle, ctypes.c_void_p(0)
+            _check(_lib.lc_free_async(h, _stream(stream)), "lc_free_async")
         self.handle = ctypes.c_void_p(0)
 
     def __del__(self):
@@ -446,6 +454,10 @@ def lc_status(col: Column, stream=None) -> int:
 
 def lc_free(col: Column) -> None:
     col.free()
+
+
+def lc_free_async(col: Column, stream=None) -> None:
+    col.free_async(stream)
 
 
 def lc_version() -> int:

@@ -334,3 +334,23 @@ def test_lower_bound_skewed_buckets_and_capped_table():
     # more than 2^21 segments: the table stops growing at 2^22 buckets
     big = inputs.lognormal_gaps(6_000_000, seed=12, mu=1.0, sigma=1.0)
     _lower_bound_matches(big, 0, check_bytes=False)
+
+
+def test_free_async_in_stream_order():
+    # columns released in stream order while their decodes are still queued:
+    # the outputs stay right and the memory is reused
+    keys = inputs.lognormal_gaps(300000, seed=41)
+    s = torch.cuda.Stream()
+    outs = []
+    with torch.cuda.stream(s):
+        d = dev(keys)
+        for r in range(6):
+            col = lc.lc_compress(d, eps=7 + r, stream=s)
+            out = torch.empty(keys.size, dtype=col.dtype, device="cuda")
+            lc.lc_decode(col, 0, keys.size, out, stream=s)
+            lc.lc_free_async(col, stream=s)
+            assert not col.handle.value
+            outs.append(out)
+    s.synchronize()
+    for out in outs:
+        assert np.array_equal(host(out), keys)
