@@ -498,8 +498,13 @@ __device__ __forceinline__ uint64_t access_one(const ColView& v, uint64_t i, uin
 template <typename KT>
 __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint64_t m, KT* __restrict__ out) {
     const uint64_t keep = policy_keep(), stream = policy_stream();
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i = ld_stream(idx + q, stream);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // the next query's rank is loaded while this one's dependent loads run
+    uint64_t in = q < m ? ld_stream(idx + q, stream) : 0;
+    for (; q < m; q += step) {
+        const uint64_t i = in;
+        if (q + step < m) in = ld_stream(idx + q + step, stream);
         if (i >= v.N) {
             atomicOr(v.status, kStOutOfRange);
             out[q] = 0;
@@ -581,8 +586,15 @@ template <typename KT>
 __global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m,
                                                           uint64_t* __restrict__ out) {
     const uint64_t keep = policy_keep(), stream = policy_stream();
-    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < m; q += (uint64_t)gridDim.x * blockDim.x)
-        st_stream(out + q, lower_bound_one<KT>(v, ld_stream(vals + q, stream), keep, stream), stream);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // the next query's value is loaded while this one's dependent loads run
+    uint64_t xn = q < m ? ld_stream(vals + q, stream) : 0;
+    for (; q < m; q += step) {
+        const uint64_t x = xn;
+        if (q + step < m) xn = ld_stream(vals + q + step, stream);
+        st_stream(out + q, lower_bound_one<KT>(v, x, keep, stream), stream);
+    }
 }
 
 // ------------------------------------------------------------------ quantiles and segments-only (approximate) keys
@@ -611,8 +623,12 @@ template <typename KT>
 __global__ void quantile_kernel(ColView v, const uint64_t* __restrict__ ks, uint64_t m, uint64_t q, int exact,
                                 KT* __restrict__ out) {
     const uint64_t keep = policy_keep(), stream = policy_stream();
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m; r += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = ks[r];
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t kn = r < m ? ld_stream(ks + r, stream) : 0;  // the next query, loaded ahead
+    for (; r < m; r += step) {
+        const uint64_t k = kn;
+        if (r + step < m) kn = ld_stream(ks + r + step, stream);
         if (k > q) {
             atomicOr(v.status, kStOutOfRange);
             out[r] = 0;
