@@ -82,6 +82,17 @@ namespace {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Page-locked staging a batch of nqreq query requests (nq queries) and ndreq
+// decodes needs: descriptors, work offsets and queries in, query results out
+// (the layout launch_batch writes).
+size_t staging_bytes(size_t nqreq, size_t ndreq, size_t nq) {
+    const size_t o_d = al256(sizeof(SrvReq) * nqreq);
+    const size_t o_w = al256(o_d + sizeof(SrvReq) * ndreq);
+    const size_t o_in = al256(o_w + 8 * (ndreq + 1));
+    const size_t o_out = al256(o_in + 8 * nq);
+    return o_out + 8 * nq;
+}
+
 uint64_t device_need(const lc_server* s, const lc_request& r) {
     if (r.op == LC_OP_DECODE) return al256(r.count * s->kb);
     return 16 * r.count;  // one 8-byte query in and one 8-byte result out
@@ -364,12 +375,22 @@ int lc_server_create(lc_column* const* cols, int ncols, uint64_t hbm_budget, int
         return LC_ERR_CUDA;
     }
     s->slots.resize(slots);
+    // every slot's staging sized for the largest batch the admission rules let
+    // through (a single request above the query cap still grows it): growing
+    // it while serving page-locks memory and synchronises the device
+    const size_t stage = staging_bytes(kMaxBatchRequests, kMaxBatchDecodes, kMaxBatchQueries);
     for (Slot& sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
             lc_server_destroy(s);
             return LC_ERR_CUDA;
         }
+        if (cudaMallocHost((void**)&sl.h_stage, stage) != cudaSuccess) {
+            sl.h_stage = nullptr;
+            lc_server_destroy(s);
+            return LC_ERR_NOMEM;
+        }
+        sl.h_cap = stage;
     }
     s->th = std::thread(scheduler, s);
     *out = s;
