@@ -84,18 +84,21 @@ def dist_env():
     return world, rank, local
 
 
+# The sources the step's kernels are built from (the serving runtime and the
+# FOR baseline hold none of them).
+STEP_SOURCES = ("lc_api.cu", "lc_compress.cu", "lc_query.cu", "lc_internal.h", "lc_math.cuh")
+
+
 def kernel_sources_sha256() -> str:
-    """Hash of the CUDA sources the kernels are built from (the traffic
+    """Hash of the CUDA sources the step's kernels are built from (the traffic
     profile below applies only to exactly these sources)."""
-    import glob
     import hashlib
 
     d = os.path.join(ROOT, "paper_2412_10770_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.h")) +
-                    glob.glob(os.path.join(d, "*.cuh"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in sorted(STEP_SOURCES):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
