@@ -10,14 +10,17 @@
 //                 32-key block.
 //   chain_kernel  one warp per chunk follows the blocks in order: a ballot
 //                 accepts every run of blocks whose walks join up, the warp
-//                 walks the cone itself elsewhere; the true anchors as one bit
+//                 walks the cone itself elsewhere (256 keys per step, 32-bit
+//                 fractions where the keys allow); the true anchors as one bit
 //                 per key, the segment count per chunk, and the slope of every
 //                 segment longer than 96 keys (its walk ends with the cone).
 //   scan          chunk_seg_begin.
 //   fit_short_kernel  one CTA per 8192-key window, one thread per 32-key
-//                 block: the cone, slope and width of every segment of at most
-//                 96 keys that starts in the block (sequential, keys in shared
-//                 memory); longer segments queue their width pass.
+//                 block, split by keys: the cone, slope and width of every
+//                 segment of at most 96 keys that starts in the block, with
+//                 the keys of later blocks merged as partial cones through
+//                 shared memory (keys in shared memory); longer segments queue
+//                 their width pass.
 //   long_width_kernel  one warp per 2048-key piece of a long segment.
 //   bitoff_kernel one CTA per chunk: bit offsets (a scan of w (n-1)).
 //   scan          chunk_word_begin.

@@ -2,12 +2,15 @@
 // access and value lower_bound (Def. 1 decoding, Fig. 2 decoding stage
 // K[i] = floor(f_j(i)) + Delta[i]; Table 2 / Sec. III-A segment search).
 //
-// Decode works on tiles of 2048 keys that never cross a chunk.  A CTA stages
-// the model of every segment that meets its tile (intercept, slope, bit base,
-// start, width) and the tile's payload words in shared memory, marks the
-// segment starts in a 2048-bit map, and then every key finds its segment by a
-// rank (popcount) on that map: no search per key.  Keys are written with
-// consecutive threads on consecutive keys (coalesced).
+// Decode works on tiles of 2048 keys that never cross a chunk.  A persistent
+// CTA copies a tile's rank words (segment starts as bits, with the count
+// before), the records of every segment that meets it and its payload words
+// into shared memory with bulk copies, two tiles in flight; every key then
+// finds its segment by a rank (popcount): no search per key.  A thread
+// decodes two neighbouring keys and stores them as one aligned vector, the
+// warp's stores covering consecutive keys.  Access and lower_bound are
+// dependent random loads from the same derived directories (rank words,
+// 32-byte records, a radix table and 16/32-bit intercept offsets).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
