@@ -1,5 +1,6 @@
 """Host-side helpers of bench.py that need no GPU: the traffic profile built
-from an ncu --csv metrics log, and its source-hash guard."""
+from an ncu --csv metrics log with its source-hash guard, and the oracle
+baseline spread over every host core."""
 from __future__ import annotations
 
 import json
@@ -45,3 +46,19 @@ def test_write_traffic_means_per_launch_and_maps_names(tmp_path):
     assert abs(k["decode"]["ms_per_launch_under_ncu"] - 0.003) < 1e-12
     assert k["decode_ranges"]["dram_bytes_per_launch"] == 2000
     assert prof["source_sha256"] == bench.kernel_sources_sha256()
+
+
+def test_oracle_all_cores_runs_the_sample_in_chunk_aligned_pieces():
+    import os
+
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_2412_10770_gb300 import inputs
+
+    oracle.build()
+    cols = [inputs.column(g, 3 * 65536 + 123, seed=5, dtype=np.uint64) for g in ("lognormal", "clusters")]
+    wall, procs = bench.oracle_all_cores(cols, 63, 1000)
+    assert procs == (os.cpu_count() or 1)
+    assert wall > 0
