@@ -357,6 +357,15 @@ int lc_deserialize(const void* host, uint64_t len, void* stream, lc_column** out
  * (LC_OK or the first LC_ERR_* recorded by a kernel).  Synchronous. */
 int lc_status(const lc_column* col, void* stream);
 
+/* Check of the library's bounded device waits, with no fault and no hang: one
+ * thread waits, for at most `polls` polls (1 .. 2^20), on an mbarrier that
+ * nobody completes, the same wait the decoders use on their bulk copies
+ * (there with a limit of 2^22 polls, after which a decode records
+ * LC_ERR_TIMEOUT in the column's status word and stops).  Returns
+ * LC_ERR_TIMEOUT when the wait gave up as designed, LC_OK if it completed
+ * (never), LC_ERR_INVALID_ARG for a polls value out of range.  Synchronous. */
+int lc_selftest_wait(uint32_t polls, void* stream);
+
 /* Release the column.  lc_free first waits for the whole device;
  * lc_free_async releases the device memory in the order of `stream` instead,
  * so the host does not wait: every use of the column must be on `stream` or

@@ -841,6 +841,11 @@ int lc_deserialize(const void* host, uint64_t len, void* stream, lc_column** out
     return LC_OK;
 }
 
+int lc_selftest_wait(uint32_t polls, void* stream) {
+    if (polls == 0 || polls > (1u << 20)) return LC_ERR_INVALID_ARG;
+    return wait_selftest(polls, (cudaStream_t)stream);
+}
+
 int lc_status(const lc_column* col, void* stream) {
     if (!col) return LC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;

@@ -210,6 +210,10 @@ int stage_h2d(void* dst_dev, const void* src_host, size_t bytes, cudaStream_t st
 int stage_d2h(const void* src_dev, size_t bytes, cudaStream_t st, const void** host_out);
 int stage_sync(cudaStream_t st);
 
+// lc_selftest_wait: the decoders' bounded mbarrier wait on a barrier nobody
+// completes, limited to `polls` polls.
+int wait_selftest(uint32_t polls, cudaStream_t st);
+
 // Count of kernel launches issued by the library in this process.
 void note_launch(uint32_t k = 1);
 

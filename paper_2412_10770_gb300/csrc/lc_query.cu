@@ -97,10 +97,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
 __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity; false if it gave up
+// after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit = kSpinLimit) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -133,6 +134,17 @@ __device__ __forceinline__ DecStage dec_stage_at(uint8_t* smem, uint32_t ms, uin
     d.rec = (SegRec*)(b + kRankPerTile * 16);
     d.pay = (uint32_t*)(b + kRankPerTile * 16 + (size_t)ms * 32);
     return d;
+}
+
+// The decoders' bounded wait, made to run out: one thread waits on an
+// mbarrier that expects one arrival which never comes, and records in
+// *status whether the wait gave up (kStTimeout) or, impossibly, completed.
+__global__ void wait_selftest_kernel(uint32_t* __restrict__ status, uint32_t polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *status = mbar_wait(&bar, 0u, polls) ? 0u : kStTimeout;
 }
 
 // Thread 0: fetch tile t of v into stage s; the item is written before the
@@ -1503,5 +1515,19 @@ int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, u
 }
 
 uint64_t tile_of_key(const lc_column* col, uint64_t i) { return host_tile_of(col, i); }
+
+int wait_selftest(uint32_t polls, cudaStream_t st) {
+    uint32_t* d = nullptr;
+    if (cudaMallocAsync((void**)&d, 4, st) != cudaSuccess) return LC_ERR_NOMEM;
+    wait_selftest_kernel<<<1, 32, 0, st>>>(d, polls);
+    note_launch();
+    int rc = cuda_status(cudaGetLastError());
+    uint32_t h = 0;
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    cudaFreeAsync(d, st);
+    if (rc) return rc;
+    return (h & kStTimeout) ? LC_ERR_TIMEOUT : LC_OK;
+}
 
 }  // namespace lcx

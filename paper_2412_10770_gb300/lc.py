@@ -31,7 +31,8 @@ LC_ERR_UNSUPPORTED = -10
 EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", "lc_decode_ranges_noalloc",
            "lc_decode_batch",
            "lc_access", "lc_lower_bound", "lc_access1", "lc_lower_bound1", "lc_ratio", "lc_size",
-           "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_free", "lc_free_async", "lc_strerror",
+           "lc_info", "lc_serialize", "lc_deserialize", "lc_status", "lc_selftest_wait", "lc_free", "lc_free_async",
+           "lc_strerror",
            "lc_version", "lc_launch_count", "lc_graph_decode", "lc_graph_launch", "lc_graph_free", "lc_server_create", "lc_server_submit",
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
@@ -123,6 +124,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_status": ([p, p], i32),
         "lc_free": ([p], None),
         "lc_free_async": ([p, p], i32),
+        "lc_selftest_wait": ([ctypes.c_uint32, p], i32),
         "lc_strerror": ([i32], ctypes.c_char_p),
         "lc_version": ([], i32),
         "lc_launch_count": ([], u64),
@@ -450,6 +452,11 @@ def lc_deserialize(blob: bytes, stream=None) -> Column:
 
 def lc_status(col: Column, stream=None) -> int:
     return load().lc_status(col.handle, _stream(stream))
+
+
+def lc_selftest_wait(polls: int = 1024, stream=None) -> int:
+    """The decoders' bounded wait run out on purpose; LC_ERR_TIMEOUT expected."""
+    return load().lc_selftest_wait(int(polls), _stream(stream))
 
 
 def lc_free(col: Column) -> None:
