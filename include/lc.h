@@ -40,7 +40,7 @@
  *     (cudaMallocAsync).  The first lc_compress / lc_compress_batch /
  *     lc_deserialize on a device raises that pool's release threshold to
  *     8 GiB, so that up to 8 GiB of freed blocks stay mapped for the next
- *     column instead of being returned to the driver at every synchronisation.
+ *     column instead of being handed back to the CUDA driver at every synchronisation.
  *   - Device-side errors (an index >= N in lc_access) are recorded in the
  *     column's status word and reported by lc_status.
  */
