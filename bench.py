@@ -1040,7 +1040,7 @@ def run_e2e(args, cols, lc, torch, stream):
     results out.  The copies are pipelined the way a streaming caller would do
     it: each input travels in on one copy stream (keys first, then the windows
     and the queries, the next column's while this one computes), each result
-    travels out on another as soon as the call that makes it is done, over two
+    travels out on another as soon as the call that makes it is done, over three
     sets of device buffers ordered by events, and the steps run back to back
     (the timed region ends when the last step's results are on the host)."""
     N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
@@ -1052,8 +1052,9 @@ def run_e2e(args, cols, lc, torch, stream):
               "rng": torch.empty(nw * wl, dtype=torch.uint64).pin_memory(),
               "acc": torch.empty(m, dtype=torch.uint64).pin_memory(),
               "lb": torch.empty(m, dtype=torch.uint64).pin_memory()}
-    d_in = [{nm: torch.empty_like(t, device="cuda") for nm, t in pinned[0].items()} for _ in range(2)]
-    d_out = [{nm: torch.empty_like(t, device="cuda") for nm, t in outs_h.items()} for _ in range(2)]
+    NB = 3  # device buffer sets: inputs travel in up to two columns ahead of the compute
+    d_in = [{nm: torch.empty_like(t, device="cuda") for nm, t in pinned[0].items()} for _ in range(NB)]
+    d_out = [{nm: torch.empty_like(t, device="cuda") for nm, t in outs_h.items()} for _ in range(NB)]
     h2d = sum(t.numel() * t.element_size() for ph in pinned for t in ph.values())
     d2h = len(cols) * sum(t.numel() * t.element_size() for t in outs_h.values())
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
@@ -1069,14 +1070,14 @@ def run_e2e(args, cols, lc, torch, stream):
     def run(steps):
         """steps x C columns back to back: the copies of one step overlap the
         compute and copies of the next; the columns are freed at the end."""
-        in_ready = [None, None]   # per buffer set: one event per input group
-        in_free = [None, None]    # the compute that last read the set's inputs
-        out_free = [None, None]   # the copies that last read the set's outputs
+        in_ready = [None] * NB    # per buffer set: one event per input group
+        in_free = [None] * NB     # the compute that last read the set's inputs
+        out_free = [None] * NB    # the copies that last read the set's outputs
         live = []
         order = [c for _ in range(steps) for c in range(C)]
 
         def copy_in(k):
-            b, c = k % 2, order[k]
+            b, c = k % NB, order[k]
             if in_free[b] is not None:
                 s_in.wait_event(in_free[b])
             evs = []
@@ -1093,11 +1094,12 @@ def run_e2e(args, cols, lc, torch, stream):
                 for nm in names:
                     outs_h[nm].copy_(d_out[b][nm], non_blocking=True)
 
-        copy_in(0)
+        for k in range(min(NB - 1, len(order))):
+            copy_in(k)
         for k in range(len(order)):
-            b = k % 2
-            if k + 1 < len(order):
-                copy_in(k + 1)  # queued before this column's compress blocks the host
+            b = k % NB
+            if k + NB - 1 < len(order):
+                copy_in(k + NB - 1)  # queued before this column's compress blocks the host
             if out_free[b] is not None:
                 stream.wait_event(out_free[b])
             di, do, ev = d_in[b], d_out[b], in_ready[b]
