@@ -589,6 +589,37 @@ __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uin
         b = fb <= 1.0f ? 1u : (fb >= (float)n ? n : (uint32_t)fb);
         if (a > b) a = b;
     }
+    const uint32_t w = (uint32_t)(r.kstart_w >> 56);
+    if (a < b && w) {
+        // the residuals of the bracket usually lie in 8 payload words: two
+        // 16-byte loads, and the search then runs on registers instead of
+        // two loads per probe
+        const uint64_t bit1 = r.bit1_n & kBitMask;
+        const uint64_t q0 = (bit1 + (uint64_t)w * (a - 1)) >> 5;      // word of residual a
+        const uint64_t q1 = (bit1 + (uint64_t)w * (b - 1) - 1) >> 5;  // word of residual b - 1's last bit
+        const uint64_t base = q0 & ~3ull;
+        if (q1 + 1 < base + 8 && base + 8 <= 2 * v.W) {
+            const ulonglong2 u = ld2_hint(v.pay32 + base, stream), u2 = ld2_hint(v.pay32 + base + 4, stream);
+            const uint32_t wd[8] = {(uint32_t)u.x, (uint32_t)(u.x >> 32), (uint32_t)u.y, (uint32_t)(u.y >> 32),
+                                    (uint32_t)u2.x, (uint32_t)(u2.x >> 32), (uint32_t)u2.y, (uint32_t)(u2.y >> 32)};
+            auto word = [&](uint32_t k) {  // wd[k] by selects (no local memory), k < 8
+                uint32_t r0 = wd[0];
+#pragma unroll
+                for (uint32_t c = 1; c < 8; ++c) r0 = k == c ? wd[c] : r0;
+                return r0;
+            };
+            const uint64_t off = bit1 - 32 * base;
+            while (a < b) {
+                const uint32_t mid = (a + b) >> 1;
+                const uint32_t pos = (uint32_t)(off + (uint64_t)w * (mid - 1)), k = pos >> 5;
+                const uint32_t z = extract_bits(word(k), word(k + 1), pos & 31u, w);
+                const uint64_t key = r.icpt + (uint64_t)(line_at(r.slope, mid) + (int64_t)unzigzag32(z));
+                if (key < x) a = mid + 1;
+                else b = mid;
+            }
+            return ks + a;
+        }
+    }
     while (a < b) {
         const uint32_t mid = (a + b) >> 1;
         if (rec_key_hint(v, r, mid, stream) < x) a = mid + 1;
@@ -598,7 +629,7 @@ __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uin
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(256) lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m,
+__global__ void __launch_bounds__(256, 6) lower_bound_kernel(ColView v, const KT* __restrict__ vals, uint64_t m,
                                                           uint64_t* __restrict__ out) {
     const uint64_t keep = policy_keep(), stream = policy_stream();
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
