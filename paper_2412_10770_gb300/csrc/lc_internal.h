@@ -82,6 +82,7 @@ struct SegRec {
     uint64_t kstart_w;  // anchor key index (low 56 bits) | width << 56
     uint64_t bit1_n;    // payload bit of residual 1 (low 48 bits) | (n_j - 1) << 48
 };
+static_assert(sizeof(SegRec) == 32, "records are read with one 32-byte load");
 constexpr uint64_t kBitMask = (1ull << 48) - 1;
 // RankWord: anchor bits of keys [64q, 64q + 64) and the number of anchors
 // before key 64q, so that the segment of key i is

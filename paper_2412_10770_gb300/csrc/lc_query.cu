@@ -477,13 +477,18 @@ __device__ __forceinline__ uint32_t ld16_hint(const void* ptr, uint64_t pol) {
     return r;
 }
 
+// One 32-byte record in one 256-bit load (records are 32-byte aligned: the
+// array starts the derived allocation): one L1 request per lane, not two.
 __device__ __forceinline__ SegRec load_rec_hint(const SegRec* p, uint64_t pol) {
-    const ulonglong2 a = ld2_hint(p, pol), b = ld2_hint((const ulonglong2*)p + 1, pol);
+    uint64_t a, b, c, d;
+    asm("ld.global.nc.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], %5;"
+        : "=l"(a), "=l"(b), "=l"(c), "=l"(d)
+        : "l"(p), "l"(pol));
     SegRec r;
-    r.icpt = a.x;
-    r.slope = (int64_t)a.y;
-    r.kstart_w = b.x;
-    r.bit1_n = b.y;
+    r.icpt = a;
+    r.slope = (int64_t)b;
+    r.kstart_w = c;
+    r.bit1_n = d;
     return r;
 }
 
@@ -1037,6 +1042,7 @@ int build_derived(lc_column* col, cudaStream_t st) {
         col->derived2 = nullptr;
         return LC_ERR_NOMEM;
     }
+    if ((uintptr_t)col->derived2 % 32) return LC_ERR_INTERNAL;  // records are read with 32-byte loads
     SegRec* recs = (SegRec*)col->derived2;
     RankWord* rank = (RankWord*)(col->derived2 + off_rank);
     uint64_t* rdx = (uint64_t*)(col->derived2 + off_rdx);
