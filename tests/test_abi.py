@@ -64,6 +64,9 @@ def test_invalid_arguments_are_rejected_before_any_device_work(libpath):
     assert lib.lc_compress(None, 10, 8, ctypes.byref(prm), None, ctypes.byref(h)) == lc.LC_ERR_INVALID_ARG
     assert lib.lc_decode(None, 0, 0, None, None) == lc.LC_ERR_INVALID_ARG
     assert lib.lc_ratio(None) < 0
+    assert lib.lc_free_async(None, None) == lc.LC_ERR_INVALID_ARG
+    assert lib.lc_selftest_wait(0, None) == lc.LC_ERR_INVALID_ARG
+    assert lib.lc_selftest_wait((1 << 20) + 1, None) == lc.LC_ERR_INVALID_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
