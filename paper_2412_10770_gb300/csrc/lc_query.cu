@@ -605,19 +605,21 @@ __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uin
         const uint64_t base = q0 & ~3ull;
         if (q1 + 1 < base + 8 && base + 8 <= 2 * v.W) {
             const ulonglong2 u = ld2_hint(v.pay32 + base, stream), u2 = ld2_hint(v.pay32 + base + 4, stream);
-            const uint32_t wd[8] = {(uint32_t)u.x, (uint32_t)(u.x >> 32), (uint32_t)u.y, (uint32_t)(u.y >> 32),
-                                    (uint32_t)u2.x, (uint32_t)(u2.x >> 32), (uint32_t)u2.y, (uint32_t)(u2.y >> 32)};
-            auto word = [&](uint32_t k) {  // wd[k] by selects (no local memory), k < 8
-                uint32_t r0 = wd[0];
+            // pr[k] = words k and k + 1 of the window as one 64-bit value, k < 7
+            const uint64_t pr[7] = {u.x, (u.x >> 32) | (u.y << 32), u.y, (u.y >> 32) | (u2.x << 32),
+                                    u2.x, (u2.x >> 32) | (u2.y << 32), u2.y};
+            auto pair = [&](uint32_t k) {  // pr[k] by selects (no local memory)
+                uint64_t r0 = pr[0];
 #pragma unroll
-                for (uint32_t c = 1; c < 8; ++c) r0 = k == c ? wd[c] : r0;
+                for (uint32_t c = 1; c < 7; ++c) r0 = k == c ? pr[c] : r0;
                 return r0;
             };
             const uint64_t off = bit1 - 32 * base;
+            const uint64_t wmask = (1ull << w) - 1;  // w <= 32
             while (a < b) {
                 const uint32_t mid = (a + b) >> 1;
-                const uint32_t pos = (uint32_t)(off + (uint64_t)w * (mid - 1)), k = pos >> 5;
-                const uint32_t z = extract_bits(word(k), word(k + 1), pos & 31u, w);
+                const uint32_t pos = (uint32_t)(off + (uint64_t)w * (mid - 1));
+                const uint32_t z = (uint32_t)((pair(pos >> 5) >> (pos & 31u)) & wmask);
                 const uint64_t key = r.icpt + (uint64_t)(line_at(r.slope, mid) + (int64_t)unzigzag32(z));
                 if (key < x) a = mid + 1;
                 else b = mid;
