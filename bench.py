@@ -71,9 +71,7 @@ def parse_args():
     ap.add_argument("--budget-gb", type=float, default=16.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--write-traffic", metavar="CSV",
-                    help="turn an ncu --csv capture of dram__bytes_read.sum, dram__bytes_write.sum and "
-                         "gpu__time_duration.sum over the large-column step into the traffic profile, then exit")
+    ap.add_argument("--no-analytics", action="store_true", help="skip the quantile and segments-only rows")
     return ap.parse_args()
 
 
@@ -84,89 +82,45 @@ def dist_env():
     return world, rank, local
 
 
-# The sources the step's kernels are built from (the serving runtime and the
-# FOR baseline hold none of them).
-STEP_SOURCES = ("lc_api.cu", "lc_compress.cu", "lc_query.cu", "lc_internal.h", "lc_math.cuh")
+# DRAM traffic of single kernels, each from its own small ncu capture (one
+# kernel, one launch, a few GB on the device), per unit of work (key or query)
+# so that it scales to a full launch.  An entry applies only while the sources
+# it names are unchanged.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 
-def kernel_sources_sha256() -> str:
-    """Hash of the CUDA sources the step's kernels are built from (the traffic
-    profile below applies only to exactly these sources)."""
+def sources_sha256(names) -> str:
+    """Hash of the named CUDA sources of the library."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_2412_10770_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(STEP_SOURCES):
+    for f in sorted(names):
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def dram_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` on the large-column workload, from the
-    committed ncu capture (profiles/traffic_large_column_eps63.json), or None
-    when the kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "traffic_large_column_eps63.json")
+def dram_traffic(kernel: str, units_per_launch: float):
+    """DRAM bytes (read + write) of one launch of `kernel` that processes
+    `units_per_launch` keys or queries, scaled from its committed capture, with
+    a note of where it came from; (None, None) when there is no capture of the
+    current sources."""
     try:
-        with open(path) as fh:
+        with open(TRAFFIC_PROFILE) as fh:
             prof = json.load(fh)
     except (OSError, ValueError):
-        return None
-    if prof.get("source_sha256") != kernel_sources_sha256():
-        return None
+        return None, None
     k = prof.get("kernels", {}).get(kernel)
-    return k["dram_bytes_per_launch"] if k else None
-
-
-# ncu kernel name -> the bench's name for it
-TRAFFIC_KERNELS = {"spec_kernel": "fit_spec", "chain_kernel": "fit_chain", "fit_short_kernel": "model_short",
-                   "long_width_kernel": "model_long", "pack_kernel": "pack", "decode_kernel": "decode",
-                   "decode_ranges_kernel": "decode_ranges", "access_kernel": "access",
-                   "lower_bound_kernel": "lower_bound", "decode_approx_kernel": "decode_approx",
-                   "quantile_kernel": "quantile (exact and approximate)"}
-TRAFFIC_UNITS = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
-                 "nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3, "ns": 1e-6, "us": 1e-3,
-                 "ms": 1.0, "s": 1e3}
-
-
-def write_traffic(csv_path: str, command: str, out_path: str | None = None) -> dict:
-    """Per kernel of TRAFFIC_KERNELS: launches and mean DRAM bytes per launch
-    from an ncu --csv metrics log, stamped with the current source hash."""
-    import csv
-    import re
-
-    with open(csv_path, newline="") as fh:
-        rows = list(csv.reader(fh))
-    head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
-    hdr = rows[head]
-    acc = {}
-    for r in rows[head + 1:]:
-        d = dict(zip(hdr, r))
-        m = re.search(r"(\w+)(?:<[^(]*)?\(", d.get("Kernel Name", ""))
-        name = TRAFFIC_KERNELS.get(m.group(1)) if m else None
-        if name is None:
-            continue
-        v = float(d["Metric Value"].replace(",", "")) * TRAFFIC_UNITS[d["Metric Unit"]]
-        k = acc.setdefault(name, {"ids": set(), "rd": 0.0, "wr": 0.0, "ms": 0.0})
-        k["ids"].add(d["ID"])
-        k[{"dram__bytes_read.sum": "rd", "dram__bytes_write.sum": "wr", "gpu__time_duration.sum": "ms"}
-          [d["Metric Name"]]] += v
-    kernels = {}
-    for name, k in acc.items():
-        n = len(k["ids"])
-        kernels[name] = {"launches": n, "dram_read_bytes_per_launch": k["rd"] / n,
-                         "dram_write_bytes_per_launch": k["wr"] / n,
-                         "dram_bytes_per_launch": (k["rd"] + k["wr"]) / n, "ms_per_launch_under_ncu": k["ms"] / n}
-    prof = {"workload": "large single column: 3 x N=2e8 sorted uint64 keys (lognormal, piecewise, clusters), eps=63, "
-                        "one warm-up and one timed step, then the quantile and segments-only rows",
-            "command": command,
-            "one_pass_check": "the same three metrics on lower_bound_kernel of a 3e7-key column reported 1 pass",
-            "source_sha256": kernel_sources_sha256(), "kernels": kernels}
-    with open(out_path or os.path.join(ROOT, "profiles", "traffic_large_column_eps63.json"), "w") as fh:
-        json.dump(prof, fh, indent=1)
-        fh.write("\n")
-    return prof
+    if not k or not k.get("captures") or k.get("sources_sha256") != sources_sha256(k.get("sources", [])):
+        return None, None
+    caps = k["captures"]
+    per_unit = sum(c["dram_bytes_per_launch"] / c["units_per_launch"] for c in caps) / len(caps)
+    note = (f"mean DRAM bytes per {k['unit'][:-1]} of {len(caps)} single-launch ncu captures "
+            f"({'; '.join(c['workload'] for c in caps)}), scaled to {units_per_launch:.3g} {k['unit']}: "
+            f"{k['summary']}")
+    return per_unit * units_per_launch, note
 
 
 def rank_seed(seed: int, rank: int) -> int:
@@ -365,13 +319,6 @@ def workload_config(args):
 
 def main():
     args = parse_args()
-    if args.write_traffic:
-        cmd = ("python bench.py --steps 1 --warmup 1 --no-e2e --no-cpu-baseline > gpurun_out/p3_full.log 2>&1 && "
-               "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none "
-               "--csv --log-file gpurun_out/p3_traffic_full.csv python bench.py --steps 1 --warmup 1 --no-e2e "
-               "--no-cpu-baseline; python bench.py --write-traffic gpurun_out/p3_traffic_full.csv")
-        write_traffic(args.write_traffic, cmd)
-        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -543,6 +490,8 @@ def main():
     dom = max((k for k in kernels if k in kalg), key=lambda k: ktimes[k][1])
     achieved = kernels[dom]["alg_gbs"]
     value = job_throughput(world, ncols * N, ms)
+    units_launch = {"access": m, "lower_bound": m, "decode_ranges": nw * wl}.get(dom, N)
+    traffic, traffic_note = dram_traffic(dom, units_launch)
 
     line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -550,20 +499,23 @@ def main():
             "phases": phase_out, "kernels": kernels,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
-                         "ms_per_launch": kernels[dom]["ms_per_launch"], "traffic": dram_traffic(dom)},
+                         "ms_per_launch": kernels[dom]["ms_per_launch"], "traffic": traffic,
+                         "traffic_source": traffic_note},
             "ratio": {g: blob_bytes[g] / (N * kb) for g in gens},
             "segments": {g: sizes[g][1] for g in gens},
             "clocks": clocks, "gpu_launches": launches}
 
-    # DRAM bytes actually moved by the dominant kernel (ncu capture of these
-    # sources): the traffic, and the DRAM throughput it implies at the live time
+    # DRAM bytes the dominant kernel actually moves (its own small ncu capture
+    # of these sources, scaled to this launch) and the DRAM throughput they
+    # imply at the live time
     tr = line["roofline"]["traffic"]
     if tr:
         line["roofline"]["dram_gbs"] = tr / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
         line["roofline"]["dram_frac"] = line["roofline"]["dram_gbs"] / peak
 
     # the quantile and segments-only rows (Sec. III-C), timed apart from the step
-    line["analytics"] = measure_analytics(args, cols, lc, torch, stream, out_dec, out_acc, peak)
+    if not args.no_analytics:
+        line["analytics"] = measure_analytics(args, cols, lc, torch, stream, out_dec, out_acc, peak)
 
     # end to end through the C ABI with host buffers
     if not args.no_e2e:

@@ -140,13 +140,16 @@ int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_de
 
 /* Several ranges in one launch: range r is keys [begin[r], begin[r] +
  * count[r]) written to out_dev at out_off[r] keys.  begin_dev, count_dev and
- * out_off_dev are device arrays of m uint64 values (validated on the device;
- * a range past N is recorded in the status word and skipped).  Asynchronous. */
+ * out_off_dev are device arrays of m uint64 values; out_dev holds out_cap keys.
+ * Both are validated on the device: a range past N, or one whose output
+ * [out_off[r], out_off[r] + count[r]) does not fit in out_cap keys, is
+ * recorded in the status word (LC_ERR_OUT_OF_RANGE) and skipped.
+ * Asynchronous. */
 int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
-                     const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream);
+                     const uint64_t* out_off_dev, uint64_t m, void* out_dev, uint64_t out_cap, void* stream);
 
-/* lc_decode_ranges for callers that cannot allocate device memory.  It does
- * the same work and writes the same output, but calls no cudaMalloc, cudaFree
+/* lc_decode_ranges for callers that cannot allocate device memory.  It takes
+ * the same arguments, does the same work and writes the same output, but calls no cudaMalloc, cudaFree
  * or allocating library routine.  This helps callers whose request path must
  * not allocate: a serving loop that has to keep the allocator, and the device
  * synchronisation a cudaFree can cause, out of its latency; or an application
@@ -163,7 +166,8 @@ int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint
  *     (other streams, other host threads) race on it. */
 #define LC_NOALLOC_MAX_RANGES 32768
 int lc_decode_ranges_noalloc(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
-                             const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream);
+                             const uint64_t* out_off_dev, uint64_t m, void* out_dev, uint64_t out_cap,
+                             void* stream);
 
 /* Every key of every list (list mode) or of the column.  Same as
  * lc_decode(col, 0, N, ...). */
@@ -380,6 +384,13 @@ int lc_version(void);
 
 /* Diagnostics: kernels this process has launched through the library so far. */
 uint64_t lc_launch_count(void);
+
+/* Diagnostics: bytes of the current device's default stream-ordered memory
+ * pool (where the library's per-call device buffers come from) in use now,
+ * and the most in use at once since the high-water mark was last reset.
+ * reset = 1 first resets that mark to the current use.  Either output may be
+ * NULL.  Synchronous (host only). */
+int lc_pool_usage(int reset, uint64_t* used_now, uint64_t* used_high);
 
 /* Tracing: while enabled, every kernel the library launches is bracketed by
  * two CUDA events recorded on its own stream, and its device time is added to

@@ -322,6 +322,24 @@ int lc_version(void) { return 10000; }
 
 uint64_t lc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int lc_pool_usage(int reset, uint64_t* used_now, uint64_t* used_high) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e == cudaSuccess && reset) {
+        uint64_t zero = 0;  // resets the mark to the current use
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    }
+    uint64_t now = 0, high = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &now);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (used_now) *used_now = now;
+    if (used_high) *used_high = high;
+    return LC_OK;
+}
+
 int lc_timing_enable(int on) {
     g_timing.store(on != 0);
     return LC_OK;
@@ -541,19 +559,20 @@ int lc_decode(const lc_column* col, uint64_t begin, uint64_t count, void* out_de
 }
 
 int lc_decode_ranges(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
-                     const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream) {
+                     const uint64_t* out_off_dev, uint64_t m, void* out_dev, uint64_t out_cap, void* stream) {
     if (!col || (m && (!begin_dev || !count_dev || !out_off_dev || !out_dev))) return LC_ERR_INVALID_ARG;
     if (misaligned(col, out_dev)) return LC_ERR_INVALID_ARG;
     if (col->N == 0) return LC_OK;
-    return decode_ranges(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
+    return decode_ranges(col, begin_dev, count_dev, out_off_dev, m, out_dev, out_cap, (cudaStream_t)stream);
 }
 
 int lc_decode_ranges_noalloc(const lc_column* col, const uint64_t* begin_dev, const uint64_t* count_dev,
-                             const uint64_t* out_off_dev, uint64_t m, void* out_dev, void* stream) {
+                             const uint64_t* out_off_dev, uint64_t m, void* out_dev, uint64_t out_cap,
+                             void* stream) {
     if (!col || (m && (!begin_dev || !count_dev || !out_off_dev || !out_dev))) return LC_ERR_INVALID_ARG;
     if (m > LC_NOALLOC_MAX_RANGES || misaligned(col, out_dev)) return LC_ERR_INVALID_ARG;
     if (col->N == 0) return LC_OK;
-    return decode_ranges_noalloc(col, begin_dev, count_dev, out_off_dev, m, out_dev, (cudaStream_t)stream);
+    return decode_ranges_noalloc(col, begin_dev, count_dev, out_off_dev, m, out_dev, out_cap, (cudaStream_t)stream);
 }
 
 int lc_decode_batch(const lc_column* col, void* out_dev, void* stream) {

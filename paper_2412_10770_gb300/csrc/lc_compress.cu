@@ -1239,9 +1239,6 @@ pack_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, c
 
 // ------------------------------------------------------------------ device-wide exclusive scan
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;
 
 __device__ __forceinline__ uint64_t scan_val(uint32_t v, ScanOp op) {
     if (op == ScanOp::Identity) return v;
@@ -1322,19 +1319,16 @@ int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n, ScanOp op, voi
 
 // ------------------------------------------------------------------ host pipeline
 
-static int ensure_magic(int dev) {
-    static bool done[64] = {false};
-    if (dev < 0 || dev >= 64) return LC_ERR_INTERNAL;
-    if (done[dev]) return LC_OK;
-    std::vector<uint64_t> m(kMaxChunk, 0);
-    for (uint32_t d = 2; d < kMaxChunk; ++d) {
-        const unsigned __int128 two64 = (unsigned __int128)1 << 64;
-        m[d] = (uint64_t)((two64 + d - 1) / d);
-    }
-    cudaError_t e = cudaMemcpyToSymbol(g_magic, m.data(), m.size() * sizeof(uint64_t));
-    if (e != cudaSuccess) return cuda_status(e);
-    done[dev] = true;
-    return LC_OK;
+static int ensure_magic() {
+    static DeviceOnce once;
+    return once_per_device(once, [] {
+        std::vector<uint64_t> m(kMaxChunk, 0);
+        for (uint32_t d = 2; d < kMaxChunk; ++d) {
+            const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+            m[d] = (uint64_t)((two64 + d - 1) / d);
+        }
+        return cuda_status(cudaMemcpyToSymbol(g_magic, m.data(), m.size() * sizeof(uint64_t)));
+    });
 }
 
 // Keys covered by the chunk table (the reach array is indexed like the keys).
@@ -1373,14 +1367,9 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
     uint8_t* blob = col->blob;
     const Layout& lay = col->lay;
     if (stage == 0) {
-        static bool attr[2] = {false, false};
+        static DeviceOnce once;
         const size_t smem = sizeof(uint32_t) * kSpecSlots;
-        if (!attr[sizeof(KT) == 8]) {
-            int rc = cuda_status(
-                cudaFuncSetAttribute(spec_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (rc) return rc;
-            attr[sizeof(KT) == 8] = true;
-        }
+        if (int rc = smem_attr_once(once, spec_kernel<KT>, smem)) return rc;
         {
             KTime kt("fit_spec", st);
             spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.entry,
@@ -1395,14 +1384,9 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         int rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         if (fs.roff) {
-            static bool attr_r[2] = {false, false};
+            static DeviceOnce once_r;
             const size_t rsm = sizeof(uint32_t) * kShortSlots;
-            if (!attr_r[sizeof(KT) == 8]) {
-                rc = cuda_status(cudaFuncSetAttribute(reach_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)rsm));
-                if (rc) return rc;
-                attr_r[sizeof(KT) == 8] = true;
-            }
+            if ((rc = smem_attr_once(once_r, reach_kernel<KT>, rsm))) return rc;
             {
                 KTime kt("jump_reach", st);
                 reach_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, rsm, st>>>(keys, chunks_d, fs.wins, fs.roff);
@@ -1419,14 +1403,9 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         return scan_exclusive(counts, csb, C, ScanOp::Identity, tmp, tmp_bytes, st);
     }
     {
-        static bool attr[2] = {false, false};
+        static DeviceOnce once_s;
         const size_t smem = sizeof(KT) * kShortSlots;
-        if (!attr[sizeof(KT) == 8]) {
-            int rc = cuda_status(
-                cudaFuncSetAttribute(fit_short_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (rc) return rc;
-            attr[sizeof(KT) == 8] = true;
-        }
+        if (int rc = smem_attr_once(once_s, fit_short_kernel<KT>, smem)) return rc;
         KTime kt("model_short", st);
         fit_short_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, smem, st>>>(
             keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
@@ -1463,7 +1442,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
 
 int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
                   uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump) {
-    int rc = ensure_magic(col->device);
+    int rc = ensure_magic();
     if (rc) return rc;
     // windows of the speculation kernel
     std::vector<WinDesc> wins;

@@ -2,8 +2,10 @@
 // GB300 learned-compression library (not part of the public C ABI).
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/lc.h"
@@ -172,9 +174,9 @@ int build_derived(lc_column* col, cudaStream_t st);
 
 int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);
 int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count,
-                  const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
+                  const uint64_t* out_off, uint64_t m, void* out, uint64_t out_cap, cudaStream_t st);
 int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uint64_t* count,
-                          const uint64_t* out_off, uint64_t m, void* out, cudaStream_t st);
+                          const uint64_t* out_off, uint64_t m, void* out, uint64_t out_cap, cudaStream_t st);
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st);
 int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
 int quantile(const lc_column* col, const uint64_t* ks, uint64_t m, uint64_t q, int exact, void* out, cudaStream_t st);
@@ -192,11 +194,43 @@ uint64_t tile_of_key(const lc_column* col, uint64_t i);
 // Exclusive scan of n uint32 counts into n+1 uint64 offsets (out[n] = total),
 // optionally applying f(count) = even_words(count bits) first.
 enum class ScanOp { Identity, BitsToEvenWords };
+// scan_exclusive's tile: kScanThreads x kScanItems values per CTA, one
+// uint64 partial per tile in tmp (scan_tmp_bytes).
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr uint64_t kScanTile = (uint64_t)kScanThreads * kScanItems;
 int scan_exclusive(const uint32_t* in, uint64_t* out, uint64_t n, ScanOp op, void* tmp,
                    size_t tmp_bytes, cudaStream_t st);
 size_t scan_tmp_bytes(uint64_t n);
 
 int cuda_status(cudaError_t e);
+
+// Per-device set-up (kernel attributes, constant tables) done once per device
+// and process.  Thread-safe; a set-up that fails is tried again on the next
+// call.  Use one DeviceOnce object per set-up step, at namespace scope.
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+    std::mutex mu;
+    std::atomic<bool> done[kMaxDevices];
+};
+template <typename F>
+int once_per_device(DeviceOnce& o, F&& f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LC_ERR_INTERNAL;
+    if (o.done[dev].load(std::memory_order_acquire)) return LC_OK;
+    std::lock_guard<std::mutex> lk(o.mu);
+    if (o.done[dev].load(std::memory_order_relaxed)) return LC_OK;
+    const int rc = f();
+    if (rc == LC_OK) o.done[dev].store(true, std::memory_order_release);
+    return rc;
+}
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per device.
+template <typename K>
+int smem_attr_once(DeviceOnce& o, K* kernel, size_t bytes) {
+    return once_per_device(o, [&] {
+        return cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    });
+}
 
 // Small host <-> device transfers (descriptors, headers, counts) made by
 // kernels on page-locked mapped host memory instead of by the copy engines,

@@ -370,10 +370,11 @@ __global__ void __launch_bounds__(kDecThreads, 12) decode_approx_kernel(ColView 
 // Work items of a multi-range decode: range r covers tiles
 // [first[r], first[r] + ntiles[r]).
 __global__ void range_tiles_kernel(ColView v, const uint64_t* __restrict__ begin, const uint64_t* __restrict__ count,
-                                   uint64_t m, uint64_t* __restrict__ first, uint32_t* __restrict__ ntiles) {
+                                   const uint64_t* __restrict__ out_off, uint64_t out_cap, uint64_t m,
+                                   uint64_t* __restrict__ first, uint32_t* __restrict__ ntiles) {
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < m; r += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t b = begin[r], cnt = count[r];
-        if (cnt == 0 || b > v.N || cnt > v.N - b) {
+        const uint64_t b = begin[r], cnt = count[r], o = out_off[r];
+        if (cnt == 0 || b > v.N || cnt > v.N - b || o > out_cap || cnt > out_cap - o) {
             if (cnt) atomicOr(v.status, kStOutOfRange);
             first[r] = 0;
             ntiles[r] = 0;
@@ -588,7 +589,9 @@ __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uin
         const uint32_t w = (uint32_t)(r.kstart_w >> 56);
         const float s = (float)r.slope * 2.3283064365386963e-10f;  // keys per index
         const float th = (float)(x - r.icpt) / s;
-        const float dl = ((float)((1u << w) >> 1) + 1.0f) / s + 2.0f;
+        // |residual| <= 2^(w-1) for a w-bit zigzag code (w = 32 is legal: eps up to 2^30)
+        const float half = w ? (float)(1ull << (w - 1)) : 0.0f;
+        const float dl = (half + 1.0f) / s + 2.0f;
         const float fa = th - dl, fb = th + dl + 1.0f;
         a = fa <= 1.0f ? 1u : (fa >= (float)n ? n : (uint32_t)fa);
         b = fb <= 1.0f ? 1u : (fb >= (float)n ? n : (uint32_t)fb);
@@ -992,14 +995,15 @@ int sm_count() {
 
 template <typename KT>
 int set_smem() {
-    static bool done = false;
-    if (done) return LC_OK;
-    cudaError_t e = cudaFuncSetAttribute(decode_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(decode_ranges_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem);
-    if (e != cudaSuccess) return cuda_status(e);
-    done = true;
-    return LC_OK;
+    static DeviceOnce once;
+    return once_per_device(once, [] {
+        cudaError_t e =
+            cudaFuncSetAttribute(decode_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(decode_ranges_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kDecSmem);
+        return cuda_status(e);
+    });
 }
 
 }  // namespace
@@ -1216,7 +1220,7 @@ int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out
 }
 
 int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count, const uint64_t* out_off,
-                  uint64_t m, void* out, cudaStream_t st) {
+                  uint64_t m, void* out, uint64_t out_cap, cudaStream_t st) {
     if (m == 0) return LC_OK;
     const size_t tmp_b = scan_tmp_bytes(m);
     const size_t bytes = 8 * m + 4 * m + 8 * (m + 1) + tmp_b + 64;
@@ -1226,8 +1230,8 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
     uint64_t* work_off = first + m;
     uint32_t* ntiles = (uint32_t*)(work_off + m + 1);
     void* tmp = (void*)(((uintptr_t)(ntiles + m) + 15) & ~(uintptr_t)15);
-    range_tiles_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 4096), 256, 0, st>>>(col->view, begin, count,
-                                                                                              m, first, ntiles);
+    range_tiles_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 4096), 256, 0, st>>>(
+        col->view, begin, count, out_off, out_cap, m, first, ntiles);
     note_launch();
     int rc = cuda_status(cudaGetLastError());
     if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, tmp_b, st);
@@ -1309,25 +1313,15 @@ int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* ou
     const uint64_t t0 = host_tile_of(col, begin), nt = host_tile_of(col, begin + count - 1) - t0 + 1;
     const size_t smem = dec_smem(col->view.max_tile_segs);
     if (col->key_bytes == 4) {
-        static bool attr = false;
-        if (!attr) {
-            int rc = cuda_status(cudaFuncSetAttribute(decode_approx_kernel<uint32_t>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem));
-            if (rc) return rc;
-            attr = true;
-        }
+        static DeviceOnce once;
+        if (int rc = smem_attr_once(once, decode_approx_kernel<uint32_t>, kDecSmem)) return rc;
         const unsigned grid = (unsigned)std::min<uint64_t>(nt, dec_grid(decode_approx_kernel<uint32_t>, smem));
         KTime kt("decode_approx", st);
         decode_approx_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count,
                                                                         (uint32_t*)out);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            int rc = cuda_status(cudaFuncSetAttribute(decode_approx_kernel<uint64_t>,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem));
-            if (rc) return rc;
-            attr = true;
-        }
+        static DeviceOnce once;
+        if (int rc = smem_attr_once(once, decode_approx_kernel<uint64_t>, kDecSmem)) return rc;
         const unsigned grid = (unsigned)std::min<uint64_t>(nt, dec_grid(decode_approx_kernel<uint64_t>, smem));
         KTime kt("decode_approx", st);
         decode_approx_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count,
@@ -1443,12 +1437,13 @@ constexpr size_t kNoAllocFirstOff = 0;                                          
 constexpr size_t kNoAllocWorkOff = kNoAllocFirstOff + 8 * kNoAllocMaxRanges;          // uint64 work_off[m+1]
 constexpr size_t kNoAllocTilesOff = (kNoAllocWorkOff + 8 * (kNoAllocMaxRanges + 1) + 255) & ~(size_t)255;
 constexpr size_t kNoAllocScanOff = (kNoAllocTilesOff + 4 * kNoAllocMaxRanges + 255) & ~(size_t)255;
-constexpr size_t kNoAllocScanBytes = 8 * ((kNoAllocMaxRanges + 4095) / 4096 + 1);    // scan partials
+constexpr size_t kNoAllocScanBytes = 8 * ((kNoAllocMaxRanges + kScanTile - 1) / kScanTile + 1);  // scan partials
 constexpr size_t kNoAllocScratchBytes = kNoAllocScanOff + kNoAllocScanBytes;
 
+static_assert(kNoAllocScanBytes >= 8 * ((kNoAllocMaxRanges + kScanTile - 1) / kScanTile),
+              "scan_exclusive needs one partial per scan tile");
 __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
 uint8_t* g_noalloc_ptr[kMaxDevices] = {nullptr};
 std::mutex g_noalloc_mu;
 
@@ -1474,7 +1469,7 @@ int noalloc_scratch(uint8_t** out) {
 }  // namespace
 
 int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uint64_t* count, const uint64_t* out_off,
-                          uint64_t m, void* out, cudaStream_t st) {
+                          uint64_t m, void* out, uint64_t out_cap, cudaStream_t st) {
     if (m > kNoAllocMaxRanges) return LC_ERR_INVALID_ARG;
     if (m == 0) return LC_OK;
     uint8_t* scratch = nullptr;
@@ -1487,8 +1482,8 @@ int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uin
     uint64_t* work_off = (uint64_t*)(scratch + kNoAllocWorkOff);
     uint32_t* ntiles = (uint32_t*)(scratch + kNoAllocTilesOff);
     void* tmp = scratch + kNoAllocScanOff;
-    range_tiles_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 4096), 256, 0, st>>>(col->view, begin, count,
-                                                                                              m, first, ntiles);
+    range_tiles_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 4096), 256, 0, st>>>(
+        col->view, begin, count, out_off, out_cap, m, first, ntiles);
     note_launch();
     rc = cuda_status(cudaGetLastError());
     if (!rc) rc = scan_exclusive(ntiles, work_off, m, ScanOp::Identity, tmp, kNoAllocScanBytes, st);
@@ -1525,24 +1520,14 @@ int serve_launch(const ColView* views_d, int key_bytes, const SrvReq* qreqs_d, u
     if (nwork) {
         const size_t smem = dec_smem(max_tile_segs);
         if (key_bytes == 4) {
-            static bool done = false;
-            if (!done) {
-                if ((rc = cuda_status(cudaFuncSetAttribute(serve_decode_kernel<uint32_t>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem))))
-                    return rc;
-                done = true;
-            }
+            static DeviceOnce once;
+            if ((rc = smem_attr_once(once, serve_decode_kernel<uint32_t>, kDecSmem))) return rc;
             const unsigned grid = (unsigned)std::min<uint64_t>(nwork, dec_grid(serve_decode_kernel<uint32_t>, smem));
             serve_decode_kernel<uint32_t><<<grid, kDecThreads, smem, st>>>(views_d, dreqs_d, ndreq, work_off_d,
                                                                           max_tile_segs);
         } else {
-            static bool done = false;
-            if (!done) {
-                if ((rc = cuda_status(cudaFuncSetAttribute(serve_decode_kernel<uint64_t>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecSmem))))
-                    return rc;
-                done = true;
-            }
+            static DeviceOnce once;
+            if ((rc = smem_attr_once(once, serve_decode_kernel<uint64_t>, kDecSmem))) return rc;
             const unsigned grid = (unsigned)std::min<uint64_t>(nwork, dec_grid(serve_decode_kernel<uint64_t>, smem));
             serve_decode_kernel<uint64_t><<<grid, kDecThreads, smem, st>>>(views_d, dreqs_d, ndreq, work_off_d,
                                                                           max_tile_segs);

@@ -37,7 +37,8 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_server_poll", "lc_server_wait", "lc_server_stats", "lc_server_destroy", "lc_serve_sync",
            "lc_timing_enable", "lc_timing_read",
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
-           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes", "lc_compress_jump")
+           "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes", "lc_compress_jump",
+           "lc_pool_usage")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -109,8 +110,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_compress": ([p, u64, i32, ctypes.POINTER(_Params), p, pp], i32),
         "lc_compress_batch": ([p, p, u64, i32, p, p, p, pp], i32),
         "lc_decode": ([p, u64, u64, p, p], i32),
-        "lc_decode_ranges": ([p, p, p, p, u64, p, p], i32),
-        "lc_decode_ranges_noalloc": ([p, p, p, p, u64, p, p], i32),
+        "lc_decode_ranges": ([p, p, p, p, u64, p, u64, p], i32),
+        "lc_decode_ranges_noalloc": ([p, p, p, p, u64, p, u64, p], i32),
         "lc_decode_batch": ([p, p, p], i32),
         "lc_access": ([p, p, u64, p, p], i32),
         "lc_lower_bound": ([p, p, u64, p, p], i32),
@@ -128,6 +129,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_strerror": ([i32], ctypes.c_char_p),
         "lc_version": ([], i32),
         "lc_launch_count": ([], u64),
+        "lc_pool_usage": ([i32, pu64, pu64], i32),
         "lc_graph_decode": ([p, u64, u64, p, p, pp], i32),
         "lc_graph_launch": ([p, p], i32),
         "lc_graph_free": ([p], None),
@@ -185,6 +187,27 @@ def _dev(t: torch.Tensor, name: str) -> torch.Tensor:
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t
+
+
+def _out_keys(col: "Column", out: torch.Tensor, need: int, name: str = "out") -> torch.Tensor:
+    """An output buffer of the column's key width holding at least `need` keys."""
+    _dev(out, name)
+    if out.element_size() != col.key_bytes or out.is_floating_point():
+        raise TypeError(f"{name} must hold {8 * col.key_bytes}-bit integer keys")
+    if out.numel() < need:
+        raise ValueError(f"{name} holds {out.numel()} keys, {need} needed")
+    return out
+
+
+def _ranges_args(begin: torch.Tensor, count: torch.Tensor, out_off: torch.Tensor) -> int:
+    """begin, count and out_off: CUDA, contiguous, 64-bit integers, one entry per range."""
+    for t, nm in ((begin, "begin"), (count, "count"), (out_off, "out_off")):
+        _dev(t, nm)
+        if t.element_size() != 8 or t.is_floating_point():
+            raise TypeError(f"{nm} must hold 64-bit integers")
+    if not (begin.numel() == count.numel() == out_off.numel()):
+        raise ValueError("begin, count and out_off must have one entry per range")
+    return begin.numel()
 
 
 def key_dtype(key_bytes: int) -> torch.dtype:
@@ -283,18 +306,21 @@ def lc_decode(col: Column, begin: int = 0, count: int | None = None, out=None, s
         count = col.n - begin
     if out is None:
         out = torch.empty(count, dtype=col.dtype, device="cuda")
-    _dev(out, "out")
+    _out_keys(col, out, int(count))
     _check(lib.lc_decode(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream)), "lc_decode")
     return out
 
 
 def lc_decode_ranges(col: Column, begin: torch.Tensor, count: torch.Tensor, out_off: torch.Tensor, out: torch.Tensor,
                      stream=None) -> torch.Tensor:
+    """Range r = keys [begin[r], begin[r] + count[r]) into out at out_off[r];
+    a range past N or past the end of out is skipped and recorded in the
+    column's status word (lc_status)."""
     lib = load()
-    for t, nm in ((begin, "begin"), (count, "count"), (out_off, "out_off"), (out, "out")):
-        _dev(t, nm)
-    _check(lib.lc_decode_ranges(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(), begin.numel(),
-                                out.data_ptr(), _stream(stream)), "lc_decode_ranges")
+    m = _ranges_args(begin, count, out_off)
+    _out_keys(col, out, 0)
+    _check(lib.lc_decode_ranges(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(), m,
+                                out.data_ptr(), out.numel(), _stream(stream)), "lc_decode_ranges")
     return out
 
 
@@ -306,10 +332,10 @@ def lc_decode_ranges_noalloc(col: Column, begin: torch.Tensor, count: torch.Tens
     """lc_decode_ranges without any device allocation (at most
     LC_NOALLOC_MAX_RANGES ranges; see include/lc.h)."""
     lib = load()
-    for t, nm in ((begin, "begin"), (count, "count"), (out_off, "out_off"), (out, "out")):
-        _dev(t, nm)
-    _check(lib.lc_decode_ranges_noalloc(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(),
-                                        begin.numel(), out.data_ptr(), _stream(stream)), "lc_decode_ranges_noalloc")
+    m = _ranges_args(begin, count, out_off)
+    _out_keys(col, out, 0)
+    _check(lib.lc_decode_ranges_noalloc(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(), m,
+                                        out.data_ptr(), out.numel(), _stream(stream)), "lc_decode_ranges_noalloc")
     return out
 
 
@@ -317,7 +343,7 @@ def lc_decode_batch(col: Column, out=None, stream=None) -> torch.Tensor:
     lib = load()
     if out is None:
         out = torch.empty(col.n, dtype=col.dtype, device="cuda")
-    _dev(out, "out")
+    _out_keys(col, out, col.n)
     _check(lib.lc_decode_batch(col.handle, out.data_ptr(), _stream(stream)), "lc_decode_batch")
     return out
 
@@ -329,7 +355,7 @@ def lc_access(col: Column, idx: torch.Tensor, out=None, stream=None) -> torch.Te
         raise TypeError("idx must hold 64-bit indices")
     if out is None:
         out = torch.empty(idx.numel(), dtype=col.dtype, device="cuda")
-    _dev(out, "out")
+    _out_keys(col, out, idx.numel())
     _check(lib.lc_access(col.handle, idx.data_ptr(), idx.numel(), out.data_ptr(), _stream(stream)), "lc_access")
     return out
 
@@ -342,6 +368,8 @@ def lc_lower_bound(col: Column, values: torch.Tensor, out=None, stream=None) -> 
     if out is None:
         out = torch.empty(values.numel(), dtype=torch.uint64, device="cuda")
     _dev(out, "out")
+    if out.element_size() != 8 or out.numel() < values.numel():
+        raise ValueError("out must hold one 64-bit position per value")
     _check(lib.lc_lower_bound(col.handle, values.data_ptr(), values.numel(), out.data_ptr(), _stream(stream)),
            "lc_lower_bound")
     return out
@@ -357,6 +385,14 @@ def lc_lower_bound1(col: Column, x: int) -> int:
     v = ctypes.c_uint64()
     _check(load().lc_lower_bound1(col.handle, int(x), ctypes.byref(v)), "lc_lower_bound1")
     return v.value
+
+
+def lc_pool_usage(reset: bool = False) -> tuple[int, int]:
+    """(bytes in use now, most in use since the last reset) of the current
+    device's default stream-ordered pool; reset=True resets the mark first."""
+    now, high = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().lc_pool_usage(1 if reset else 0, ctypes.byref(now), ctypes.byref(high)), "lc_pool_usage")
+    return now.value, high.value
 
 
 def lc_ratio(col: Column) -> float:
@@ -379,9 +415,11 @@ def lc_quantile(col: Column, ks: torch.Tensor, q: int, exact: bool = True, out=N
     """The ks[r]-th q-quantiles (exact keys, or floor(f) from the segments alone)."""
     lib = load()
     _dev(ks, "ks")
+    if ks.element_size() != 8:
+        raise TypeError("ks must hold 64-bit integers")
     if out is None:
         out = torch.empty(ks.numel(), dtype=col.dtype, device="cuda")
-    _dev(out, "out")
+    _out_keys(col, out, ks.numel())
     _check(lib.lc_quantile(col.handle, ks.data_ptr(), ks.numel(), int(q), 1 if exact else 0, out.data_ptr(),
                            _stream(stream)), "lc_quantile")
     return out
@@ -394,7 +432,7 @@ def lc_decode_approx(col: Column, begin: int = 0, count: int | None = None, out=
         count = col.n - begin
     if out is None:
         out = torch.empty(count, dtype=col.dtype, device="cuda")
-    _dev(out, "out")
+    _out_keys(col, out, int(count))
     _check(lib.lc_decode_approx(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream)),
            "lc_decode_approx")
     return out
