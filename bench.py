@@ -72,6 +72,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-analytics", action="store_true", help="skip the quantile and segments-only rows")
+    ap.add_argument("--no-eps-rows", action="store_true", help="skip the compress/decode rows at eps 1 and 255")
+    ap.add_argument("--no-served", action="store_true", help="skip the serving measurement of the default run")
     return ap.parse_args()
 
 
@@ -521,8 +523,25 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(args, cols, lc, torch, stream)
         e2e["ms"] = max_over_ranks(pg, e2e["ms"], "cuda")
+        link = measure_link(torch)
+        # the host link's floor for these bytes: each direction at its own peak, or both at the duplex peak
+        floor_ms = 1e3 * max(e2e["h2d"] / (link["h2d_gbs"] * 1e9), e2e["d2h"] / (link["d2h_gbs"] * 1e9),
+                             (e2e["h2d"] + e2e["d2h"]) / (link["both_gbs"] * 1e9))
         line["e2e"] = {"value": job_throughput(world, ncols * N, e2e["ms"]), "unit": "keys/s",
-                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"]}
+                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"], "ms_per_step": e2e["ms"],
+                       "api": "lc_compress_host / lc_decode_host / lc_decode_ranges_host / lc_access_host / "
+                              "lc_lower_bound_host (copies inside the C-ABI calls)",
+                       "host_link": link, "link_floor_ms": floor_ms, "frac_of_link": floor_ms / e2e["ms"]}
+    # config-2 compress and decode at eps 1 and 255 (beside the step's eps)
+    if not args.no_eps_rows:
+        line["eps_rows"] = measure_eps_rows(args, cols, lc, torch, stream, peak)
+    # the metric's served half: continuous batching against the plain path
+    if not args.no_served and world == 1:
+        del out_dec, out_rng, out_acc, out_lb
+        for _, _, dev in cols:
+            dev.clear()
+        torch.cuda.empty_cache()
+        line["served"] = serve_measure(args, lc, torch, fractions=(0.1, 0.5, 1.0), requests=args.requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
 
@@ -911,19 +930,16 @@ def _run_plain_open_loop(lc, cols, reqs, arrivals, stream):
     return lat, span
 
 
-def run_serve(args):
-    """Serving: 64 device-resident compressed uint64 columns of 5e7 keys
-    (generators of the large-column workload, eps = 63), open-loop Poisson
-    arrivals swept to saturation, p50/p99 latency and keys/s of the continuous-
-    batching server against the plain synchronous per-request path."""
-    import torch
+def serve_measure(args, lc, torch, fractions, requests: int) -> dict:
+    """Serving (the large-column generators, eps = 63): args.columns
+    device-resident compressed uint64 columns of args.column_keys keys; the
+    continuous-batching server's saturation throughput (closed loop), then
+    open-loop Poisson arrivals at the given fractions of it, p50/p99 latency
+    (arrival to completion) and keys/s for the server and, where the offered
+    rate is within the plain path's capacity, for the plain synchronous
+    per-request path on the same requests and arrival times."""
+    from paper_2412_10770_gb300 import inputs
 
-    from paper_2412_10770_gb300 import build as lcbuild
-    from paper_2412_10770_gb300 import inputs, lc
-
-    lcbuild.build()
-    lc.load()
-    torch.cuda.set_device(0)
     sys.setswitchinterval(1e-4)  # the submitting loop spins; let the draining thread run promptly
     stream = torch.cuda.Stream()
     cols, keys_n, key_max, raw = [], [], [], 0
@@ -938,7 +954,7 @@ def run_serve(args):
     torch.cuda.synchronize()
     t_build = time.time() - t0
     comp = sum(lc.lc_size(c) for c in cols)
-    reqs, arena = _serve_requests(keys_n, key_max, args.requests, seed=inputs.seed_for(4, 99))
+    reqs, arena = _serve_requests(keys_n, key_max, requests, seed=inputs.seed_for(4, 99))
     keys_per_req = np.array([q[2] for q in reqs], dtype=np.float64)
     budget = int(args.budget_gb * (1 << 30))
     srv = lc.lc_server_create(cols, budget, slots=args.slots)
@@ -946,11 +962,12 @@ def run_serve(args):
     _run_server_open_loop(lc, srv, reqs, np.zeros(len(reqs)))  # warm-up: grows the staging buffers and the pool
     lat, span, _ = _run_server_open_loop(lc, srv, reqs, np.zeros(len(reqs)))
     x_srv = len(reqs) / span
-    lat_p, span_p = _run_plain_open_loop(lc, cols, reqs[:600], np.zeros(600), stream)
-    x_plain = 600 / span_p
+    n_plain = min(600, len(reqs))
+    lat_p, span_p = _run_plain_open_loop(lc, cols, reqs[:n_plain], np.zeros(n_plain), stream)
+    x_plain = n_plain / span_p
     rng = np.random.default_rng(3)
     sweep = []
-    for f in (0.1, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5):
+    for f in fractions:
         rate = f * x_srv
         n = int(min(len(reqs), max(200, rate * 2.0)))
         arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
@@ -961,126 +978,161 @@ def run_serve(args):
                "server": {"p50_ms": 1e3 * s50, "p99_ms": 1e3 * s99, "req_per_s": n / ss,
                           "keys_per_s": keys_per_req[:n].sum() / ss,
                           "client_max_submit_lag_ms": 1e3 * lag}}
-        if rate <= 3 * x_plain:  # the plain path falls behind without bound above its own capacity
+        if rate <= x_plain:  # above its own capacity the plain path's queue grows without bound
             lp, sp = _run_plain_open_loop(lc, cols, reqs[:n], arr, stream)
             p50, p99 = _pcts(lp)
             row["plain"] = {"p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99, "req_per_s": n / sp,
                             "keys_per_s": keys_per_req[:n].sum() / sp}
+        else:
+            row["plain"] = {"saturated": True, "capacity_req_per_s": x_plain}
         sweep.append(row)
     st = srv.stats()
     srv.close()
     for c in cols:
         c.free()
-    line = {"metric": METRIC, "value": keys_per_req.sum() / span, "unit": "keys/s", "n_gpus": 1,
-            "steps": len(sweep), "warmup": 1, "ms_per_step": 1e3 * span, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"serving: {args.columns} resident uint64 columns x {args.column_keys} keys "
-                                   "(lognormal/piecewise/clusters, eps=63); requests 40% access 1-4096, 40% "
-                                   "lower_bound 1-4096, 20% range decode log-uniform [1, 1.6e7]; open-loop Poisson",
-                       "slots": args.slots, "hbm_budget_gb": args.budget_gb, "requests": len(reqs)},
+    del arena
+    return {"workload": f"{args.columns} resident uint64 columns x {args.column_keys} keys (lognormal/piecewise/"
+                        "clusters, eps=63); requests 40% access 1-4096, 40% lower_bound 1-4096, 20% range decode "
+                        "log-uniform [1, 1.6e7]; open-loop Poisson",
+            "slots": args.slots, "hbm_budget_gb": args.budget_gb, "requests": len(reqs),
             "closed_loop": {"server_req_per_s": x_srv, "server_keys_per_s": keys_per_req.sum() / span,
                             "server_p50_ms": 1e3 * _pcts(lat)[0], "server_p99_ms": 1e3 * _pcts(lat)[1],
-                            "plain_req_per_s": x_plain, "plain_keys_per_s": keys_per_req[:600].sum() / span_p,
+                            "plain_req_per_s": x_plain, "plain_keys_per_s": keys_per_req[:n_plain].sum() / span_p,
                             "plain_p50_ms": 1e3 * _pcts(lat_p)[0], "plain_p99_ms": 1e3 * _pcts(lat_p)[1]},
             "sweep": sweep, "server_stats": st, "ratio": comp / raw, "build_s": t_build}
+
+
+def run_serve(args):
+    """Serving workload alone: 64 device-resident compressed uint64 columns of
+    5e7 keys, the open-loop sweep from 10% to 150% of the server's
+    saturation (serve_measure)."""
+    import torch
+
+    from paper_2412_10770_gb300 import build as lcbuild
+    from paper_2412_10770_gb300 import lc
+
+    lcbuild.build()
+    lc.load()
+    torch.cuda.set_device(0)
+    res = serve_measure(args, lc, torch, fractions=(0.1, 0.25, 0.5, 0.75, 1.0, 1.25, 1.5), requests=args.requests)
+    cl = res["closed_loop"]
+    line = {"metric": METRIC, "value": cl["server_keys_per_s"], "unit": "keys/s", "n_gpus": 1,
+            "steps": len(res["sweep"]), "warmup": 1, "ms_per_step": 1e3 * res["requests"] / cl["server_req_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "serving: " + res["workload"], "slots": args.slots,
+                       "hbm_budget_gb": args.budget_gb, "requests": res["requests"]},
+            **{k: res[k] for k in ("closed_loop", "sweep", "server_stats", "ratio", "build_s")}}
     print(json.dumps(line), flush=True)
 
 
-def run_e2e(args, cols, lc, torch, stream):
-    """The same step through the C ABI with inputs and results in pinned host
-    memory: every step copies keys and queries in and decoded keys and query
-    results out.  The copies are pipelined the way a streaming caller would do
-    it: each input travels in on one copy stream (keys first, then the windows
-    and the queries, the next column's while this one computes), each result
-    travels out on another as soon as the call that makes it is done, over three
-    sets of device buffers ordered by events, and the steps run back to back
-    (the timed region ends when the last step's results are on the host)."""
-    N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
-    pinned = []
-    for g, host, dev in cols:
-        ph = {nm: torch.from_numpy(a).pin_memory() for nm, a in host.items()}
-        pinned.append(ph)
-    outs_h = {"dec": torch.empty(N, dtype=torch.uint64).pin_memory(),
-              "rng": torch.empty(nw * wl, dtype=torch.uint64).pin_memory(),
-              "acc": torch.empty(m, dtype=torch.uint64).pin_memory(),
-              "lb": torch.empty(m, dtype=torch.uint64).pin_memory()}
-    NB = 3  # device buffer sets: inputs travel in up to two columns ahead of the compute
-    d_in = [{nm: torch.empty_like(t, device="cuda") for nm, t in pinned[0].items()} for _ in range(NB)]
-    d_out = [{nm: torch.empty_like(t, device="cuda") for nm, t in outs_h.items()} for _ in range(NB)]
-    h2d = sum(t.numel() * t.element_size() for ph in pinned for t in ph.values())
-    d2h = len(cols) * sum(t.numel() * t.element_size() for t in outs_h.values())
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    C = len(pinned)
-    groups = (("keys",), ("wb", "wc", "wo"), ("idx",), ("vals",))  # in the order the calls need them
-    assert sorted(sum(groups, ())) == sorted(pinned[0])
+def measure_eps_rows(args, cols, lc, torch, stream, peak) -> dict:
+    """Compress and full decode of every column at eps 1 and 255 (beside the
+    step's eps): mean of 3 runs each, CUDA events; algorithmic bytes as in the
+    step (compress N kb + |K^c|, decode |K^c| + N kb)."""
+    N, kb = args.n, 8
+    out = torch.empty(N, dtype=torch.uint64, device="cuda")
+    rows = {}
+    for eps in (1, 255):
+        per = {}
+        for g, host, dev in cols:
+            tc = td = 0.0
+            size = 0
+            for _ in range(3):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                col = lc.lc_compress(dev["keys"], eps=eps, chunk_log2=16, stream=stream)
+                e1.record(stream)
+                lc.lc_decode(col, 0, N, out, stream=stream)
+                e2.record(stream)
+                e2.synchronize()
+                tc += e0.elapsed_time(e1) / 3
+                td += e1.elapsed_time(e2) / 3
+                size = lc.lc_size(col)
+                col.free_async(stream)
+            assert torch.equal(out, dev["keys"]), f"decode at eps {eps} differs from the keys"
+            per[g] = {"compress_ms": tc, "compress_keys_per_s": N / tc * 1e3,
+                      "compress_hbm_frac": (N * kb + size) / (tc / 1e3) / 1e9 / peak,
+                      "decode_ms": td, "decode_keys_per_s": N / td * 1e3,
+                      "decode_hbm_frac": (N * kb + size) / (td / 1e3) / 1e9 / peak,
+                      "ratio": size / (N * kb)}
+        rows[str(eps)] = per
+    return rows
 
-    def recorded(s):
-        e = torch.cuda.Event()
-        e.record(s)
-        return e
+
+def measure_link(torch, nbytes: int = 2 << 30, reps: int = 3) -> dict:
+    """The host link's page-locked copy bandwidth (one cudaMemcpyAsync per
+    copy through torch): host to device alone, device to host alone, and both
+    at once on two streams; best of `reps`, GB/s of bytes moved."""
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best
+
+    def both():
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+
+    t_h2d = timed(lambda: d_a.copy_(h_in, non_blocking=True))
+    t_d2h = timed(lambda: h_out.copy_(d_b, non_blocking=True))
+    t_both = timed(both)
+    del h_in, h_out, d_a, d_b
+    return {"h2d_gbs": nbytes / t_h2d / 1e9, "d2h_gbs": nbytes / t_d2h / 1e9, "both_gbs": 2 * nbytes / t_both / 1e9,
+            "bytes_per_copy": nbytes, "how": "pinned host memory, one cudaMemcpyAsync per copy, best of 3"}
+
+
+def run_e2e(args, cols, lc, torch, stream):
+    """The step end to end through the host-buffer C-ABI calls: every input
+    (keys, range windows, query ranks and values) is in page-locked host
+    memory and every result is copied back to it, by the library, inside the
+    calls (lc_compress_host, lc_decode_host, lc_decode_ranges_host,
+    lc_access_host, lc_lower_bound_host).  Each column runs on its own stream,
+    so one column's copies overlap the other columns' kernels; the timed
+    region ends when the last result is on the host."""
+    N, m, nw, wl = args.n, args.queries, args.windows, args.window_len
+    pin = [{nm: torch.from_numpy(a).pin_memory() for nm, a in host.items()} for _, host, _ in cols]
+    outs = [{"dec": torch.empty(N, dtype=torch.uint64).pin_memory(),
+             "rng": torch.empty(nw * wl, dtype=torch.uint64).pin_memory(),
+             "acc": torch.empty(m, dtype=torch.uint64).pin_memory(),
+             "lb": torch.empty(m, dtype=torch.uint64).pin_memory()} for _ in cols]
+    h2d = sum(t.numel() * t.element_size() for ph in pin for t in ph.values())
+    d2h = sum(t.numel() * t.element_size() for o in outs for t in o.values())
+    streams = [torch.cuda.Stream() for _ in cols]
 
     def run(steps):
-        """steps x C columns back to back: the copies of one step overlap the
-        compute and copies of the next; the columns are freed at the end."""
-        in_ready = [None] * NB    # per buffer set: one event per input group
-        in_free = [None] * NB     # the compute that last read the set's inputs
-        out_free = [None] * NB    # the copies that last read the set's outputs
-        live = []
-        order = [c for _ in range(steps) for c in range(C)]
-
-        def copy_in(k):
-            b, c = k % NB, order[k]
-            if in_free[b] is not None:
-                s_in.wait_event(in_free[b])
-            evs = []
-            with torch.cuda.stream(s_in):
-                for grp in groups:
-                    for nm in grp:
-                        d_in[b][nm].copy_(pinned[c][nm], non_blocking=True)
-                    evs.append(recorded(s_in))
-            in_ready[b] = evs
-
-        def copy_out(b, names):
-            s_out.wait_event(recorded(stream))
-            with torch.cuda.stream(s_out):
-                for nm in names:
-                    outs_h[nm].copy_(d_out[b][nm], non_blocking=True)
-
-        for k in range(min(NB - 1, len(order))):
-            copy_in(k)
-        for k in range(len(order)):
-            b = k % NB
-            if k + NB - 1 < len(order):
-                copy_in(k + NB - 1)  # queued before this column's compress blocks the host
-            if out_free[b] is not None:
-                stream.wait_event(out_free[b])
-            di, do, ev = d_in[b], d_out[b], in_ready[b]
-            stream.wait_event(ev[0])
-            col = lc.lc_compress(di["keys"], eps=args.eps, chunk_log2=16, stream=stream)
-            live.append(col)
-            lc.lc_decode(col, 0, N, do["dec"], stream=stream)
-            copy_out(b, ("dec",))
-            stream.wait_event(ev[1])
-            lc.lc_decode_ranges(col, di["wb"], di["wc"], di["wo"], do["rng"], stream=stream)
-            copy_out(b, ("rng",))
-            stream.wait_event(ev[2])
-            lc.lc_access(col, di["idx"], do["acc"], stream=stream)
-            copy_out(b, ("acc",))
-            stream.wait_event(ev[3])
-            lc.lc_lower_bound(col, di["vals"], do["lb"], stream=stream)
-            in_free[b] = recorded(stream)
-            copy_out(b, ("lb",))
-            out_free[b] = recorded(s_out)
+        for _ in range(steps):
+            for c in range(len(cols)):
+                s, pc, oc = streams[c], pin[c], outs[c]
+                col = lc.lc_compress_host(pc["keys"], eps=args.eps, chunk_log2=16, stream=s)
+                lc.lc_decode_host(col, oc["dec"], stream=s)
+                lc.lc_decode_ranges_host(col, pc["wb"], pc["wc"], pc["wo"], oc["rng"], stream=s)
+                lc.lc_access_host(col, pc["idx"], oc["acc"], stream=s)
+                lc.lc_lower_bound_host(col, pc["vals"], oc["lb"], stream=s)
+                col.free_async(s)
         torch.cuda.synchronize()
-        for col in live:
-            col.free()
 
     run(1)
-    torch.cuda.synchronize()
+    g, host, _ = cols[-1]
+    assert np.array_equal(outs[-1]["dec"].numpy(), host["keys"]), "end-to-end decode differs from the keys"
+    want = np.searchsorted(host["keys"], host["vals"][:100000], side="left")
+    assert np.array_equal(outs[-1]["lb"].numpy()[:100000].astype(np.int64), want), "end-to-end lower_bound differs"
     t0 = time.perf_counter()
     run(args.steps)
-    torch.cuda.synchronize()
-    return {"ms": 1e3 * (time.perf_counter() - t0) / args.steps, "h2d": h2d, "d2h": d2h}
+    ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    del pin, outs
+    return {"ms": ms, "h2d": h2d, "d2h": d2h}
 
 
 if __name__ == "__main__":

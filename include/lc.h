@@ -199,6 +199,29 @@ int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* o
 int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t* out_dev,
                    void* stream);
 
+/* End to end from host memory: the calls above with their inputs and
+ * outputs in host memory.  The library copies them to and from device
+ * buffers it takes from the stream-ordered pool and releases in the order of
+ * `stream`; with page-locked ("pinned") host memory every copy is
+ * asynchronous on `stream`, so that calls on several streams overlap their
+ * copies with one another's kernels (with pageable memory the copies are
+ * synchronous).  Host buffers must stay valid, and outputs unread, until the
+ * work queued on `stream` has finished.
+ *   lc_compress_host: keys_host as lc_compress's keys_dev; synchronous like
+ *     lc_compress (the column is complete on return).
+ *   lc_decode_host: Dec(K^c)[begin .. begin+count) into out_host.
+ *   lc_decode_ranges_host: begin/count/out_off (m uint64 each) in host
+ *     memory; out_host holds out_cap keys and is copied back whole.
+ *   lc_access_host, lc_lower_bound_host: m queries in, m results out.
+ * Errors as the device calls. */
+int lc_compress_host(const void* keys_host, uint64_t n, int key_bytes, const lc_params* params, void* stream,
+                     lc_column** out);
+int lc_decode_host(const lc_column* col, uint64_t begin, uint64_t count, void* out_host, void* stream);
+int lc_decode_ranges_host(const lc_column* col, const uint64_t* begin_host, const uint64_t* count_host,
+                          const uint64_t* out_off_host, uint64_t m, void* out_host, uint64_t out_cap, void* stream);
+int lc_access_host(const lc_column* col, const uint64_t* idx_host, uint64_t m, void* out_host, void* stream);
+int lc_lower_bound_host(const lc_column* col, const void* v_host, uint64_t m, uint64_t* out_host, void* stream);
+
 /* Quantiles (Sec. III-C, Table 2): out[r] = the k[r]-th q-quantile of the
  * column, the key at index floor(N k / q) (the last key for k = q; the index
  * is computed exactly).  exact = 1: f(i) + Delta[i], the key itself (rank

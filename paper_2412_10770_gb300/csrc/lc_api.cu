@@ -653,6 +653,103 @@ int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t
     return lower_bound(col, v_dev, m, out_dev, (cudaStream_t)stream);
 }
 
+// ------------------------------------------------------------------ host-buffer entry points
+//
+// The same calls with inputs and outputs in host memory: the library copies
+// them to and from device buffers it takes from the stream-ordered pool and
+// releases in stream order.  With page-locked host memory every copy is
+// asynchronous on `stream`, so that calls on several streams overlap their
+// copies with one another's kernels.
+
+namespace {
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st;
+    explicit DevBuf(cudaStream_t s) : st(s) {}
+    int alloc(size_t bytes) {
+        if (!bytes) return LC_OK;
+        return cudaMallocAsync(&p, bytes, st) == cudaSuccess ? LC_OK : (p = nullptr, LC_ERR_NOMEM);
+    }
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+int h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return bytes ? cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)) : LC_OK;
+}
+int d2h(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return bytes ? cuda_status(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st)) : LC_OK;
+}
+}  // namespace
+
+int lc_compress_host(const void* keys_host, uint64_t n, int key_bytes, const lc_params* params, void* stream,
+                     lc_column** out) {
+    if (!out || (n && !keys_host) || (key_bytes != 4 && key_bytes != 8)) return LC_ERR_INVALID_ARG;
+    if (n > (1ull << 40)) return LC_ERR_INVALID_ARG;
+    const cudaStream_t st = (cudaStream_t)stream;
+    DevBuf k(st);
+    int rc = k.alloc(n * (uint64_t)key_bytes);
+    if (!rc) rc = h2d(k.p, keys_host, n * (uint64_t)key_bytes, st);
+    if (rc) return rc;
+    return compress_column(k.p, n, key_bytes, params, stream, out, false);
+}
+
+int lc_decode_host(const lc_column* col, uint64_t begin, uint64_t count, void* out_host, void* stream) {
+    if (!col || (count && !out_host)) return LC_ERR_INVALID_ARG;
+    if (begin > col->N || count > col->N - begin) return LC_ERR_OUT_OF_RANGE;
+    const cudaStream_t st = (cudaStream_t)stream;
+    DevBuf o(st);
+    int rc = o.alloc(count * col->key_bytes);
+    if (!rc && count) rc = decode_range(col, begin, count, o.p, st);
+    if (!rc) rc = d2h(out_host, o.p, count * col->key_bytes, st);
+    return rc;
+}
+
+int lc_decode_ranges_host(const lc_column* col, const uint64_t* begin_host, const uint64_t* count_host,
+                          const uint64_t* out_off_host, uint64_t m, void* out_host, uint64_t out_cap, void* stream) {
+    if (!col || (m && (!begin_host || !count_host || !out_off_host || (out_cap && !out_host))))
+        return LC_ERR_INVALID_ARG;
+    if (col->N == 0 || m == 0) return LC_OK;
+    const cudaStream_t st = (cudaStream_t)stream;
+    DevBuf in(st), o(st);
+    int rc = in.alloc(24 * m);
+    if (!rc) rc = o.alloc(out_cap * col->key_bytes);
+    uint64_t* b = (uint64_t*)in.p;
+    if (!rc) rc = h2d(b, begin_host, 8 * m, st);
+    if (!rc) rc = h2d(b + m, count_host, 8 * m, st);
+    if (!rc) rc = h2d(b + 2 * m, out_off_host, 8 * m, st);
+    if (!rc) rc = decode_ranges(col, b, b + m, b + 2 * m, m, o.p, out_cap, st);
+    if (!rc) rc = d2h(out_host, o.p, out_cap * col->key_bytes, st);
+    return rc;
+}
+
+int lc_access_host(const lc_column* col, const uint64_t* idx_host, uint64_t m, void* out_host, void* stream) {
+    if (!col || (m && (!idx_host || !out_host))) return LC_ERR_INVALID_ARG;
+    if (m == 0) return LC_OK;
+    const cudaStream_t st = (cudaStream_t)stream;
+    DevBuf in(st), o(st);
+    int rc = in.alloc(8 * m);
+    if (!rc) rc = o.alloc(m * col->key_bytes);
+    if (!rc) rc = h2d(in.p, idx_host, 8 * m, st);
+    if (!rc) rc = lc_access(col, (const uint64_t*)in.p, m, o.p, stream);
+    if (!rc) rc = d2h(out_host, o.p, m * col->key_bytes, st);
+    return rc;
+}
+
+int lc_lower_bound_host(const lc_column* col, const void* v_host, uint64_t m, uint64_t* out_host, void* stream) {
+    if (!col || (m && (!v_host || !out_host))) return LC_ERR_INVALID_ARG;
+    if (col->list_mode) return LC_ERR_UNSUPPORTED;
+    if (m == 0) return LC_OK;
+    const cudaStream_t st = (cudaStream_t)stream;
+    DevBuf in(st), o(st);
+    int rc = in.alloc(m * col->key_bytes);
+    if (!rc) rc = o.alloc(8 * m);
+    if (!rc) rc = h2d(in.p, v_host, m * col->key_bytes, st);
+    if (!rc) rc = lower_bound(col, in.p, m, (uint64_t*)o.p, st);
+    if (!rc) rc = d2h(out_host, o.p, 8 * m, st);
+    return rc;
+}
+
 int lc_quantile(const lc_column* col, const uint64_t* k_dev, uint64_t m, uint64_t q, int exact, void* out_dev,
                 void* stream) {
     if (!col || q == 0 || (m && (!k_dev || !out_dev))) return LC_ERR_INVALID_ARG;

@@ -38,7 +38,8 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_timing_enable", "lc_timing_read",
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
            "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes", "lc_compress_jump",
-           "lc_pool_usage")
+           "lc_pool_usage", "lc_compress_host", "lc_decode_host", "lc_decode_ranges_host", "lc_access_host",
+           "lc_lower_bound_host")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -130,6 +131,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_version": ([], i32),
         "lc_launch_count": ([], u64),
         "lc_pool_usage": ([i32, pu64, pu64], i32),
+        "lc_compress_host": ([p, u64, i32, ctypes.POINTER(_Params), p, pp], i32),
+        "lc_decode_host": ([p, u64, u64, p, p], i32),
+        "lc_decode_ranges_host": ([p, p, p, p, u64, p, u64, p], i32),
+        "lc_access_host": ([p, p, u64, p, p], i32),
+        "lc_lower_bound_host": ([p, p, u64, p, p], i32),
         "lc_graph_decode": ([p, u64, u64, p, p, pp], i32),
         "lc_graph_launch": ([p, p], i32),
         "lc_graph_free": ([p], None),
@@ -385,6 +391,74 @@ def lc_lower_bound1(col: Column, x: int) -> int:
     v = ctypes.c_uint64()
     _check(load().lc_lower_bound1(col.handle, int(x), ctypes.byref(v)), "lc_lower_bound1")
     return v.value
+
+
+def _host(t: torch.Tensor, name: str) -> torch.Tensor:
+    if t.is_cuda:
+        raise ValueError(f"{name} must be in host memory (page-locked for asynchronous copies)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def lc_compress_host(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, stream=None) -> Column:
+    """lc_compress from keys in host memory (the library copies them in)."""
+    lib = load()
+    _host(keys, "keys")
+    kb = _key_bytes(keys)
+    h = ctypes.c_void_p()
+    prm = _Params(int(eps), int(chunk_log2))
+    _check(lib.lc_compress_host(keys.data_ptr(), keys.numel(), kb, ctypes.byref(prm), _stream(stream),
+                                ctypes.byref(h)), "lc_compress_host")
+    return Column(h.value)
+
+
+def lc_decode_host(col: Column, out: torch.Tensor, begin: int = 0, count: int | None = None, stream=None):
+    lib = load()
+    if count is None:
+        count = col.n - begin
+    _host(out, "out")
+    if out.element_size() != col.key_bytes or out.numel() < count:
+        raise ValueError("out must hold count keys of the column's width")
+    _check(lib.lc_decode_host(col.handle, int(begin), int(count), out.data_ptr(), _stream(stream)), "lc_decode_host")
+    return out
+
+
+def lc_decode_ranges_host(col: Column, begin: torch.Tensor, count: torch.Tensor, out_off: torch.Tensor,
+                          out: torch.Tensor, stream=None) -> torch.Tensor:
+    lib = load()
+    for t, nm in ((begin, "begin"), (count, "count"), (out_off, "out_off"), (out, "out")):
+        _host(t, nm)
+    if not (begin.numel() == count.numel() == out_off.numel()) or begin.element_size() != 8:
+        raise ValueError("begin, count and out_off: one 64-bit entry per range")
+    if out.element_size() != col.key_bytes:
+        raise TypeError("out must hold keys of the column's width")
+    _check(lib.lc_decode_ranges_host(col.handle, begin.data_ptr(), count.data_ptr(), out_off.data_ptr(),
+                                     begin.numel(), out.data_ptr(), out.numel(), _stream(stream)),
+           "lc_decode_ranges_host")
+    return out
+
+
+def lc_access_host(col: Column, idx: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    lib = load()
+    _host(idx, "idx")
+    _host(out, "out")
+    if idx.element_size() != 8 or out.element_size() != col.key_bytes or out.numel() < idx.numel():
+        raise ValueError("idx: 64-bit indices; out: one key of the column's width per index")
+    _check(lib.lc_access_host(col.handle, idx.data_ptr(), idx.numel(), out.data_ptr(), _stream(stream)),
+           "lc_access_host")
+    return out
+
+
+def lc_lower_bound_host(col: Column, values: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+    lib = load()
+    _host(values, "values")
+    _host(out, "out")
+    if values.element_size() != col.key_bytes or out.element_size() != 8 or out.numel() < values.numel():
+        raise ValueError("values: keys of the column's width; out: one 64-bit position per value")
+    _check(lib.lc_lower_bound_host(col.handle, values.data_ptr(), values.numel(), out.data_ptr(), _stream(stream)),
+           "lc_lower_bound_host")
+    return out
 
 
 def lc_pool_usage(reset: bool = False) -> tuple[int, int]:
