@@ -532,9 +532,10 @@ def main():
                        "api": "lc_compress_host / lc_decode_host / lc_decode_ranges_host / lc_access_host / "
                               "lc_lower_bound_host (copies inside the C-ABI calls)",
                        "host_link": link, "link_floor_ms": floor_ms, "frac_of_link": floor_ms / e2e["ms"]}
-    # config-2 compress and decode at eps 1 and 255 (beside the step's eps)
+    # config-2 compress and decode at eps 1 and 255 (beside the step's eps), and compress at every span
     if not args.no_eps_rows:
         line["eps_rows"] = measure_eps_rows(args, cols, lc, torch, stream, peak)
+        line["span_rows"] = measure_span_rows(args, cols, lc, torch, stream)
     # the metric's served half: continuous batching against the plain path
     if not args.no_served and world == 1:
         del out_dec, out_rng, out_acc, out_lb
@@ -618,6 +619,7 @@ def run_batch(args):
     t_gen = time.time() - t0
     t0 = time.time()
     eps, log2, table = tune.tune(ids, begin, sample_lists=16, sample_keys=1 << 20)
+    span, span_ms = tune.tune_span(ids, begin, eps, log2)
     t_tune = time.time() - t0
     stream = torch.cuda.current_stream()
     out = torch.empty(N, dtype=torch.uint32, device="cuda")
@@ -625,7 +627,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         if col is not None:
             col.free()
-        col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream)
+        col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream, span_log2=span)
     graph, _ = lc.lc_graph_decode(col, 0, N, out, stream=stream)
     graph.launch(stream)
     torch.cuda.synchronize()
@@ -643,7 +645,7 @@ def run_batch(args):
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
         lc.lc_timing_enable(True)  # per-kernel times of the compress (not of the graph's capture)
-        col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream)
+        col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream, span_log2=span)
         lc.lc_timing_enable(False)
         b.record(stream)
         graph, _ = lc.lc_graph_decode(col, 0, N, out, stream=stream)
@@ -662,6 +664,25 @@ def run_batch(args):
     K = args.steps
     compress_kernels = {name: {"launches_per_step": nl / K, "ms_per_step": tms / K}
                         for name, (nl, tms) in sorted(lc.lc_timing_read().items(), key=lambda x: -x[1][1])}
+    # the whole batch (compress + decode of every list) as one CUDA graph, replayed
+    bt = lc.Batch(ids, begin, out, eps, log2, stream=stream, span_log2=span)
+    for _ in range(2):
+        bt.launch(stream)
+    torch.cuda.synchronize()
+    out.zero_()
+    gms = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bt.launch(stream)
+        b.record(stream)
+        b.synchronize()
+        gms.append(a.elapsed_time(b))
+    assert lc.lc_status(bt.column, stream) == lc.LC_OK
+    assert torch.equal(out, ids), "graph-replayed batch decode differs from the ids"
+    assert lc.lc_size(bt.column) == size
+    bt.free()
+    ms_g = float(np.mean(gms))
     # one call per list, on a random sample of lists
     rng = np.random.default_rng(7)
     sample = rng.choice(len(begin) - 1, size=min(args.per_list_sample, len(begin) - 1), replace=False)
@@ -691,11 +712,18 @@ def run_batch(args):
                         "decode_alg_gbs": alg_d / (ms_d / 1e3) / 1e9, "decode_hbm_frac": alg_d / (ms_d / 1e3) / 1e9 / peak,
                         "compress_alg_gbs": (4 * N + size) / (ms_c / 1e3) / 1e9,
                         "compress_kernels": compress_kernels},
+            "graph": {"ms_per_launch": ms_g, "keys_per_s": N / (ms_g / 1e3), "launches": len(gms),
+                      "what": "lc_batch_launch: one CUDA graph holding the batched compress (fit, models, widths, "
+                              "bit offsets, packing, derived directories) and the decode of every list"},
             "per_list": {"lists_sampled": int(sample.size), "keys": int(skeys),
                          "keys_per_s": skeys / tp, "note": "one lc_compress + lc_decode per list, host-timed"},
             "batched_over_per_list": value / (skeys / tp),
             "ratio": size / (4 * N), "bits_per_id": 8 * size / N, "segments": segs,
-            "tuning": table, "gen_s": t_gen, "tune_s": t_tune, "clocks": clocks, "gpu_launches": launches}
+            "tuning": {"per_length_bucket": table, "span_log2": span, "span_compress_ms": span_ms,
+                       "parameters": "eps and chunk_log2 per list-length bucket (smallest K^c on a sample), "
+                                     "span_log2 (keys per speculating thread) per batch (fastest compress)"},
+            "gen_s": t_gen, "tune_s": t_tune, "clocks": clocks, "gpu_launches": launches}
+    line["batched_graph_over_per_list"] = (N / (ms_g / 1e3)) / (skeys / tp)
     line["setops"] = measure_setops(args, ids, begin, eps, log2, lc, torch, stream)
     print(json.dumps(line), flush=True)
 
@@ -1023,6 +1051,27 @@ def run_serve(args):
                        "hbm_budget_gb": args.budget_gb, "requests": res["requests"]},
             **{k: res[k] for k in ("closed_loop", "sweep", "server_stats", "ratio", "build_s")}}
     print(json.dumps(line), flush=True)
+
+
+def measure_span_rows(args, cols, lc, torch, stream) -> dict:
+    """Compress of every column at the step's eps with each span of the fit's
+    speculating threads (2^5, 2^6, 2^7 keys): mean ms of 3 runs, CUDA events."""
+    rows = {}
+    for sp in (5, 6, 7):
+        per = {}
+        for g, host, dev in cols:
+            t = 0.0
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                col = lc.lc_compress(dev["keys"], eps=args.eps, chunk_log2=16, stream=stream, span_log2=sp)
+                e1.record(stream)
+                e1.synchronize()
+                t += e0.elapsed_time(e1) / 3
+                col.free_async(stream)
+            per[g] = t
+        rows[str(sp)] = per
+    return rows
 
 
 def measure_eps_rows(args, cols, lc, torch, stream, peak) -> dict:

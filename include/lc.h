@@ -64,16 +64,21 @@ enum {
     LC_ERR_TIMEOUT = -7,      /* a bounded device or host wait gave up */
     LC_ERR_BUSY = -8,         /* serving: no slot or HBM budget free right now */
     LC_ERR_UNSUPPORTED = -10, /* operation not defined for this column (lower_bound on a list column) */
-    LC_ERR_INTERNAL = -9
+    LC_ERR_INTERNAL = -9,
+    LC_ERR_STALE = -11        /* a replayed batch graph met keys whose K^c does not fit its plan */
 };
 
 typedef struct lc_column lc_column;
 
 /* Fit parameters.  eps: the error bound of Def. 2, 0 <= eps <= 2^30.
- * chunk_log2: log2 of the chunk length in keys, 8..16 (16 by default). */
+ * chunk_log2: log2 of the chunk length in keys, 8..16 (16 by default).
+ * span_log2: log2 of the keys each speculating GPU thread of the fit walks,
+ * 5, 6 or 7 (0: the default, 6); a launch parameter only: K^c is the same for
+ * every value. */
 typedef struct {
     uint64_t eps;
     uint32_t chunk_log2;
+    uint32_t span_log2;
 } lc_params;
 
 /* Header facts of a column (synchronous, host-side copy). */
@@ -123,10 +128,34 @@ int lc_compress_jump(const void* keys_dev, uint64_t n, int key_bytes, const lc_p
  * list_begin[l+1]), each list non-decreasing on its own.  eps and chunk_log2:
  * one entry per list (host memory), or NULL for 0 and 16.  Every list is
  * compressed as its own column (chunks restart at each list), all lists in
- * one launch of each kernel.  Synchronous like lc_compress. */
+ * one launch of each kernel.  span_log2: as in lc_params (0: default), one
+ * value for the batch.  Synchronous like lc_compress. */
 int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists,
-                      int key_bytes, const uint64_t* eps, const uint8_t* chunk_log2,
+                      int key_bytes, const uint64_t* eps, const uint8_t* chunk_log2, uint32_t span_log2,
                       void* stream, lc_column** out);
+
+/* The batching path as one CUDA graph.  lc_batch_create compresses the lists
+ * once, as lc_compress_batch does (synchronously), which fixes the column's
+ * layout (segments, payload words, decode tiles).  It then records into one
+ * CUDA graph every step of that compress (speculation, chain, segment models
+ * and widths, bit offsets, packing, the derived directories) writing into the
+ * same column, followed by a decode of every list into out_dev (device, N keys
+ * of key_bytes).  lc_batch_launch replays the graph on `stream` with no host
+ * synchronisation: the lists in ids_dev are compressed again and decoded.
+ * For the same ids the column's bytes are those of lc_compress_batch.  The
+ * graph checks on the device that the replay's segment and payload-word
+ * totals equal the plan's; if not, the steps after the check do nothing,
+ * lc_status on the column returns LC_ERR_STALE, and the column must be freed
+ * (re-plan with lc_batch_create).  ids_dev and out_dev must outlive the
+ * batch; lc_batch_column returns the column (owned by the batch, freed by
+ * lc_batch_free).  Same arguments and errors as lc_compress_batch. */
+typedef struct lc_batch lc_batch;
+int lc_batch_create(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists, int key_bytes,
+                    const uint64_t* eps, const uint8_t* chunk_log2, uint32_t span_log2, void* out_dev, void* stream,
+                    lc_batch** out);
+int lc_batch_launch(lc_batch* batch, void* stream);
+const lc_column* lc_batch_column(const lc_batch* batch);
+void lc_batch_free(lc_batch* batch);
 
 /* ------------------------------------------------------------ decoding */
 

@@ -386,6 +386,7 @@ const char* lc_strerror(int s) {
         case LC_ERR_BUSY: return "busy";
         case LC_ERR_UNSUPPORTED: return "unsupported for this column";
         case LC_ERR_INTERNAL: return "internal error";
+        case LC_ERR_STALE: return "batch keys do not fit the planned layout";
         default: return "unknown status";
     }
 }
@@ -423,6 +424,11 @@ int lc_free_async(lc_column* col, void* stream) {
     return rc;
 }
 
+static bool span_ok(uint32_t& span_log2) {
+    if (span_log2 == 0) span_log2 = 6;
+    return span_log2 >= 5 && span_log2 <= 7;
+}
+
 static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, const lc_params* params, void* stream,
                            lc_column** out, bool jump);
 
@@ -443,7 +449,8 @@ static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, cons
     if (key_bytes != 4 && key_bytes != 8) return LC_ERR_INVALID_ARG;
     const uint64_t eps = params ? params->eps : 0;
     const uint32_t log2 = params ? params->chunk_log2 : 16;
-    if (eps > (1ull << 30) || log2 < 8 || log2 > 16) return LC_ERR_INVALID_ARG;
+    uint32_t span_log2 = params ? params->span_log2 : 0;
+    if (eps > (1ull << 30) || log2 < 8 || log2 > 16 || !span_ok(span_log2)) return LC_ERR_INVALID_ARG;
     if (n > (1ull << 40)) return LC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     lc_column* col = new_column();
@@ -475,7 +482,8 @@ static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, cons
             ch[c].pad = 0;
             bound += bound_words(ch[c].n, eps);
         }
-        rc = compress_impl(keys_dev, key_bytes, ch.data(), col->C, col->C * (cs / 32), bound, st, col, jump);
+        rc = compress_impl(keys_dev, key_bytes, ch.data(), col->C, col->C * (cs / 32), bound, st, col, jump,
+                           span_log2);
     }
     if (!rc) rc = finish_column(col, st, nullptr, nullptr, nullptr, nullptr);
     if (rc) { lc_free(col); return rc; }
@@ -483,10 +491,63 @@ static int compress_column(const void* keys_dev, uint64_t n, int key_bytes, cons
     return LC_OK;
 }
 
-int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists, int key_bytes,
-                      const uint64_t* eps, const uint8_t* chunk_log2, void* stream, lc_column** out) {
-    if (!out || !list_begin) return LC_ERR_INVALID_ARG;
-    *out = nullptr;
+// The chunk table of a batch of lists (chunks restart at every list) and the
+// list directory; fills col's list-mode fields.
+struct BatchTable {
+    std::vector<uint64_t> le, lcb;
+    std::vector<uint8_t> lg;
+    std::vector<ChunkDesc> ch;
+    uint64_t bitwords = 0, bound = 0;
+};
+
+static int batch_table(const uint64_t* list_begin, uint64_t nlists, int key_bytes, const uint64_t* eps,
+                       const uint8_t* chunk_log2, lc_column* col, BatchTable* bt) {
+    col->key_bytes = (uint32_t)key_bytes;
+    col->chunk_log2 = 0;
+    col->list_mode = 1;
+    col->N = list_begin[nlists];
+    col->eps = 0;
+    col->NL = nlists;
+    bt->le.assign(nlists, 0);
+    bt->lcb.assign(nlists + 1, 0);
+    bt->lg.assign(nlists, 16);
+    uint64_t C = 0;
+    for (uint64_t l = 0; l < nlists; ++l) {
+        bt->le[l] = eps ? eps[l] : 0;
+        bt->lg[l] = chunk_log2 ? chunk_log2[l] : 16;
+        const uint64_t cs = 1ull << bt->lg[l];
+        bt->lcb[l] = C;
+        C += (list_begin[l + 1] - list_begin[l] + cs - 1) / cs;
+    }
+    bt->lcb[nlists] = C;
+    col->C = C;
+    col->h_ckb = new (std::nothrow) uint64_t[C + 1];
+    if (!col->h_ckb) return LC_ERR_NOMEM;
+    bt->ch.resize(C);
+    uint64_t c = 0;
+    for (uint64_t l = 0; l < nlists; ++l) {
+        const uint64_t cs = 1ull << bt->lg[l];
+        for (uint64_t b = list_begin[l]; b < list_begin[l + 1]; b += cs, ++c) {
+            const uint64_t e = std::min(b + cs, list_begin[l + 1]);
+            col->h_ckb[c] = b;
+            ChunkDesc& d = bt->ch[c];
+            d.key_begin = b;
+            d.bitword_begin = bt->bitwords;
+            d.n = (uint32_t)(e - b);
+            d.eps = (uint32_t)bt->le[l];
+            d.check_prev = b > list_begin[l];
+            d.pad = 0;
+            bt->bitwords += (e - b + 31) / 32;
+            bt->bound += bound_words(e - b, bt->le[l]);
+        }
+    }
+    col->h_ckb[C] = col->N;
+    return LC_OK;
+}
+
+static int check_batch_args(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists, int key_bytes,
+                            const uint64_t* eps, const uint8_t* chunk_log2) {
+    if (!list_begin) return LC_ERR_INVALID_ARG;
     if (key_bytes != 4 && key_bytes != 8) return LC_ERR_INVALID_ARG;
     if (list_begin[0] != 0) return LC_ERR_INVALID_ARG;
     for (uint64_t l = 0; l < nlists; ++l) {
@@ -497,54 +558,82 @@ int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t 
     const uint64_t n = list_begin[nlists];
     if (n && !ids_dev) return LC_ERR_INVALID_ARG;
     if (n > (1ull << 40)) return LC_ERR_INVALID_ARG;
+    return LC_OK;
+}
+
+int lc_compress_batch(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists, int key_bytes,
+                      const uint64_t* eps, const uint8_t* chunk_log2, uint32_t span_log2, void* stream,
+                      lc_column** out) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!span_ok(span_log2)) return LC_ERR_INVALID_ARG;
+    int rc = check_batch_args(ids_dev, list_begin, nlists, key_bytes, eps, chunk_log2);
+    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     lc_column* col = new_column();
     if (!col) return LC_ERR_NOMEM;
-    cudaGetDevice(&col->device);
-    col->key_bytes = (uint32_t)key_bytes;
-    col->chunk_log2 = 0;
-    col->list_mode = 1;
-    col->N = n;
-    col->eps = 0;
-    col->NL = nlists;
-    std::vector<uint64_t> le(nlists), lcb(nlists + 1, 0);
-    std::vector<uint8_t> lg(nlists);
-    uint64_t C = 0;
-    for (uint64_t l = 0; l < nlists; ++l) {
-        le[l] = eps ? eps[l] : 0;
-        lg[l] = chunk_log2 ? chunk_log2[l] : 16;
-        const uint64_t cs = 1ull << lg[l];
-        lcb[l] = C;
-        C += (list_begin[l + 1] - list_begin[l] + cs - 1) / cs;
-    }
-    lcb[nlists] = C;
-    col->C = C;
-    col->h_ckb = new (std::nothrow) uint64_t[C + 1];
-    if (!col->h_ckb) { lc_free(col); return LC_ERR_NOMEM; }
-    std::vector<ChunkDesc> ch(C);
-    uint64_t bitwords = 0, bound = 0, c = 0;
-    for (uint64_t l = 0; l < nlists; ++l) {
-        const uint64_t cs = 1ull << lg[l];
-        for (uint64_t b = list_begin[l]; b < list_begin[l + 1]; b += cs, ++c) {
-            const uint64_t e = std::min(b + cs, list_begin[l + 1]);
-            col->h_ckb[c] = b;
-            ch[c].key_begin = b;
-            ch[c].bitword_begin = bitwords;
-            ch[c].n = (uint32_t)(e - b);
-            ch[c].eps = (uint32_t)le[l];
-            ch[c].check_prev = b > list_begin[l];
-            ch[c].pad = 0;
-            bitwords += (e - b + 31) / 32;
-            bound += bound_words(e - b, le[l]);
-        }
-    }
-    col->h_ckb[C] = n;
-    int rc = C == 0 ? alloc_empty_blob(col, st)
-                    : compress_impl(ids_dev, key_bytes, ch.data(), C, bitwords, bound, st, col);
-    if (!rc) rc = finish_column(col, st, list_begin, lcb.data(), le.data(), lg.data());
+    BatchTable bt;
+    rc = batch_table(list_begin, nlists, key_bytes, eps, chunk_log2, col, &bt);
+    if (!rc) rc = col->C == 0 ? alloc_empty_blob(col, st)
+                              : compress_impl(ids_dev, key_bytes, bt.ch.data(), col->C, bt.bitwords, bt.bound, st, col,
+                                              false, span_log2);
+    if (!rc) rc = finish_column(col, st, list_begin, bt.lcb.data(), bt.le.data(), bt.lg.data());
     if (rc) { lc_free(col); return rc; }
     *out = col;
     return LC_OK;
+}
+
+struct lc_batch {
+    lc_column* col;
+    lcx::BatchGraph* graph;
+};
+
+int lc_batch_create(const void* ids_dev, const uint64_t* list_begin, uint64_t nlists, int key_bytes,
+                    const uint64_t* eps, const uint8_t* chunk_log2, uint32_t span_log2, void* out_dev, void* stream,
+                    lc_batch** out) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!span_ok(span_log2)) return LC_ERR_INVALID_ARG;
+    int rc = check_batch_args(ids_dev, list_begin, nlists, key_bytes, eps, chunk_log2);
+    if (rc) return rc;
+    if (list_begin[nlists] == 0 || !out_dev || ((uintptr_t)out_dev % key_bytes)) return LC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    lc_column* col = new_column();
+    if (!col) return LC_ERR_NOMEM;
+    BatchTable bt;
+    rc = batch_table(list_begin, nlists, key_bytes, eps, chunk_log2, col, &bt);
+    if (!rc) rc = compress_impl(ids_dev, key_bytes, bt.ch.data(), col->C, bt.bitwords, bt.bound, st, col, false,
+                                span_log2);
+    if (!rc) rc = finish_column(col, st, list_begin, bt.lcb.data(), bt.le.data(), bt.lg.data());
+    BatchGraph* g = nullptr;
+    if (!rc)
+        rc = batch_graph_build(ids_dev, key_bytes, bt.ch.data(), col->C, bt.bitwords, span_log2, col, out_dev, st, &g);
+    lc_batch* b = nullptr;
+    if (!rc) {
+        b = new (std::nothrow) lc_batch{col, g};
+        if (!b) rc = LC_ERR_NOMEM;
+    }
+    if (rc) {
+        batch_graph_free(g);
+        lc_free(col);
+        return rc;
+    }
+    *out = b;
+    return LC_OK;
+}
+
+int lc_batch_launch(lc_batch* b, void* stream) {
+    if (!b) return LC_ERR_INVALID_ARG;
+    return batch_graph_launch(b->graph, (cudaStream_t)stream);
+}
+
+const lc_column* lc_batch_column(const lc_batch* b) { return b ? b->col : nullptr; }
+
+void lc_batch_free(lc_batch* b) {
+    if (!b) return;
+    batch_graph_free(b->graph);
+    lc_free(b->col);
+    delete b;
 }
 
 // Output keys are stored whole: the buffer must be aligned to the key width.
@@ -974,6 +1063,7 @@ int lc_status(const lc_column* col, void* stream) {
     if (s & kStOutOfRange) return LC_ERR_OUT_OF_RANGE;
     if (s & kStUnsorted) return LC_ERR_UNSORTED;
     if (s & kStTimeout) return LC_ERR_TIMEOUT;
+    if (s & kStPlan) return LC_ERR_STALE;
     if (s) return LC_ERR_INTERNAL;
     return LC_OK;
 }

@@ -257,11 +257,9 @@ __device__ __forceinline__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t
 
 constexpr uint32_t kFB = 32;                    // keys per fit block: one 32-bit word of anchor bits
 constexpr uint32_t kWinKeys = 8192;             // keys per window, one CTA
-constexpr uint32_t kSpan = 64;                  // keys per speculating thread (two blocks)
 constexpr uint32_t kWarm = 96;                  // keys a speculative walk runs before its span
-constexpr int kSpecThreads = kWinKeys / kSpan;  // 128
 constexpr uint32_t kSpecKeys = kWarm + kWinKeys + 96;  // a walk ends at most 96 keys past its span
-constexpr uint32_t kSpecSlots = kSpecKeys + kSpecKeys / 64 + 1;
+constexpr uint32_t kSpecSlots = kSpecKeys + kSpecKeys / 32 + 1;  // the densest padding (one per 32 keys)
 constexpr int kShortThreads = kWinKeys / kFB;   // 256: one thread per block in fit_short_kernel
 constexpr int kChainThreads = 128;              // four chunks per CTA, one warp each
 constexpr uint32_t kShortMax = 96;              // segments of at most this many keys: one thread fits each
@@ -309,50 +307,47 @@ struct Staged {
         return (uint64_t)s[q + (q >> 5)];
     }
 };
-// The same with one pad slot per 64 keys, for lanes 64 keys apart.
-template <typename KT>
-struct Staged64 {
-    const KT* s;
-    uint32_t base;
-    __device__ __forceinline__ uint64_t operator()(uint32_t i) const {
-        const uint32_t q = i - base;
-        return (uint64_t)s[q + (q >> 6)];
-    }
-};
 
 
-// What one speculative walk leaves for its two blocks: its anchors in each
-// block, its first anchor at or after the span's start (entry of block 0), at
-// or after the second block's start (exit of block 0 = entry of block 1), and
-// at or after the span's end (exit of block 1); kNone where the walk stopped
-// before finding it.
+// What one speculative walk leaves for its kB 32-key blocks: its anchors in
+// each block (m), and e[k] = its first anchor at or after the start of block k
+// (e[0]: the span's start = entry of block 0; e[kB]: the span's end = exit of
+// the last block); kNone where the walk stopped before finding it.
+template <int kB>
 struct SpecOut {
-    uint32_t m0, m1;
-    uint32_t ent, mid, ex;
+    uint32_t m[kB];
+    uint32_t e[kB + 1];
 };
 
-__device__ __forceinline__ void spec_record(SpecOut& o, uint32_t i, uint32_t s0) {
+template <int kB>
+__device__ __forceinline__ void spec_record(SpecOut<kB>& o, uint32_t i, uint32_t s0) {
     const uint32_t r = i - s0;
-    if (r < 32) o.m0 |= 1u << r;
-    else if (r < 64) o.m1 |= 1u << (r - 32);
-    if (o.ent == kNone) o.ent = i;
-    if (o.mid == kNone && r >= 32) o.mid = i;
-    if (r >= 64) o.ex = i;
+#pragma unroll
+    for (int k = 0; k < kB; ++k)
+        if (r >= 32u * k && r < 32u * (k + 1)) o.m[k] |= 1u << (r - 32u * k);
+#pragma unroll
+    for (int k = 0; k <= kB; ++k)
+        if (o.e[k] == kNone && r >= 32u * k) o.e[k] = i;
 }
 
 // One thread's speculative walk: the greedy from `p` (taken as an anchor)
-// until its first anchor at or after s0 + 64 (the span's end) or the chunk's
-// end n.  A segment that would grow past kShortMax keys stops it (its end is
-// left to the chain, which walks long segments itself), so every segment the
-// walk closes has at most kShortMax keys.  The narrow walk reads 32-bit key
-// offsets from shared memory (exact differences: the walk's key range is
-// below 2^31); the wide one reads 64-bit keys from global memory.
-template <bool kNarrow, typename ST>
-__device__ __forceinline__ SpecOut spec_walk(const ST& st, uint32_t p, uint32_t n, uint32_t s0, int64_t eps) {
-    SpecOut o{0u, 0u, kNone, kNone, kNone};
-    const uint32_t lim = min(n, s0 + kSpan + kShortMax);
+// until its first anchor at or after s0 + 32 kB (the span's end) or the
+// chunk's end n.  A segment that would grow past kShortMax keys stops it (its
+// end is left to the chain, which walks long segments itself), so every
+// segment the walk closes has at most kShortMax keys.  The narrow walk reads
+// 32-bit key offsets from shared memory (exact differences: the walk's key
+// range is below 2^31); the wide one reads 64-bit keys from global memory.
+template <bool kNarrow, int kB, typename ST>
+__device__ __forceinline__ SpecOut<kB> spec_walk(const ST& st, uint32_t p, uint32_t n, uint32_t s0, int64_t eps) {
+    constexpr uint32_t kSpanB = 32u * kB;
+    SpecOut<kB> o;
+#pragma unroll
+    for (int k = 0; k < kB; ++k) o.m[k] = 0u;
+#pragma unroll
+    for (int k = 0; k <= kB; ++k) o.e[k] = kNone;
+    const uint32_t lim = min(n, s0 + kSpanB + kShortMax);
     uint32_t x = p;
-    if (p >= s0) spec_record(o, p, s0);
+    if (p >= s0) spec_record<kB>(o, p, s0);
     uint32_t i = p + 1;
     if (kNarrow) {
         // branch-free steps: every lane runs the same instructions whether its
@@ -379,8 +374,8 @@ __device__ __forceinline__ SpecOut spec_walk(const ST& st, uint32_t p, uint32_t 
                 x = i;
                 kx = Ki;
                 if (i >= s0) {
-                    spec_record(o, i, s0);
-                    if (i >= s0 + kSpan) break;
+                    spec_record<kB>(o, i, s0);
+                    if (i >= s0 + kSpanB) break;
                 }
             }
         }
@@ -394,19 +389,31 @@ __device__ __forceinline__ SpecOut spec_walk(const ST& st, uint32_t p, uint32_t 
             kx = Ki;
             c = frac_open();
             if (i >= s0) {
-                spec_record(o, i, s0);
-                if (i >= s0 + kSpan) break;
+                spec_record<kB>(o, i, s0);
+                if (i >= s0 + kSpanB) break;
             }
         }
     }
     // the walk ran into the chunk's end inside a segment of at most kShortMax keys: n is its next anchor
     if (i >= n && i - x <= kShortMax) {
-        if (o.ent == kNone) o.ent = n;
-        if (o.mid == kNone) o.mid = n;
-        if (o.ex == kNone) o.ex = n;
+#pragma unroll
+        for (int k = 0; k <= kB; ++k)
+            if (o.e[k] == kNone) o.e[k] = n;
     }
     return o;
 }
+
+// A window's keys staged in shared memory with one pad slot per 2^kShift keys,
+// for lanes 2^kShift keys apart (distinct banks).
+template <typename KT, int kShift>
+struct StagedS {
+    const KT* s;
+    uint32_t base;
+    __device__ __forceinline__ uint64_t operator()(uint32_t i) const {
+        const uint32_t q = i - base;
+        return (uint64_t)s[q + (q >> kShift)];
+    }
+};
 
 // Key i of a chunk from global memory (the wide speculative walk).
 template <typename KT>
@@ -417,21 +424,26 @@ struct GlobalKeys {
 
 // One CTA per window of 8192 keys of one chunk; keys [w0 - kWarm, w1 + 96)
 // staged in shared memory as 32-bit offsets from the first staged key.
-// Thread t owns the span of blocks 2t, 2t+1 and runs the greedy from kWarm
-// keys before the span (from the chunk start if that is closer) to its first
-// anchor past the span.  Greedy walks from different starts meet after a few
-// segments, so by the span the walk is almost always on the true chain; the
-// chain kernel checks that (a block is exact iff the walk enters it where the
-// previous block's walk leaves it) and walks itself where it does not hold.
-// Per block: the walk's anchors in the block (spec), its first anchor at or
-// after the block's start (entry) and after its end (exit); kNone if the walk
-// stopped inside a segment of more than kShortMax keys before reaching it, the
-// chunk's length if the chunk ends first.  Also checks sortedness.
-template <typename KT>
-__global__ void __launch_bounds__(kSpecThreads)
+// Thread t owns the span of blocks kB t .. kB t + kB - 1 (32 kB keys) and runs
+// the greedy from kWarm keys before the span (from the chunk start if that is
+// closer) to its first anchor past the span.  Greedy walks from different
+// starts meet after a few segments, so by the span the walk is almost always
+// on the true chain; the chain kernel checks that (a block is exact iff the
+// walk enters it where the previous block's walk leaves it) and walks itself
+// where it does not hold.  Per block: the walk's anchors in the block (spec),
+// its first anchor at or after the block's start (entry) and after its end
+// (exit); kNone if the walk stopped inside a segment of more than kShortMax
+// keys before reaching it, the chunk's length if the chunk ends first.  Also
+// checks sortedness.  kB (1, 2 or 4 blocks per thread: 256, 128 or 64 threads
+// per window) trades parallelism against the warm-up walked per key.
+template <typename KT, int kB>
+__global__ void __launch_bounds__(kWinKeys / (32 * kB))
 spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
             uint32_t* __restrict__ spec_g, uint32_t* __restrict__ entry_g, uint32_t* __restrict__ exit_g,
             uint32_t* __restrict__ status) {
+    constexpr uint32_t kSpanB = 32u * kB;
+    constexpr int kThreads = kWinKeys / kSpanB;
+    constexpr int kShift = kB == 1 ? 5 : (kB == 2 ? 6 : 7);
     extern __shared__ __align__(16) uint8_t smem[];
     const WinDesc wd = wins[blockIdx.x];
     const ChunkDesc cd = chunks[wd.chunk];
@@ -446,35 +458,36 @@ spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, c
     uint32_t* s = (uint32_t*)smem;
     const uint64_t kbase = (uint64_t)__ldg(K + base);
 #pragma unroll 4
-    for (uint32_t q = tid; q < top - base; q += kSpecThreads) s[q + (q >> 6)] = (uint32_t)((uint64_t)__ldg(K + base + q) - kbase);
+    for (uint32_t q = tid; q < top - base; q += kThreads)
+        s[q + (q >> kShift)] = (uint32_t)((uint64_t)__ldg(K + base + q) - kbase);
     // sortedness: key i against key i - 1 for i in [max(w0, 1), w1)
     bool unsorted = false;
 #pragma unroll 4
-    for (uint32_t i = max(w0, 1u) + tid; i < w1; i += kSpecThreads) unsorted |= __ldg(K + i - 1) > __ldg(K + i);
+    for (uint32_t i = max(w0, 1u) + tid; i < w1; i += kThreads) unsorted |= __ldg(K + i - 1) > __ldg(K + i);
     if (w0 == 0 && cd.check_prev && tid == 0) unsorted |= __ldg(K - 1) > __ldg(K);
     if (unsorted) atomicOr(status, kStUnsorted);
     __syncthreads();
-    const Staged64<uint32_t> st{s, base};
+    const StagedS<uint32_t, kShift> st{s, base};
 
-    const uint32_t s0 = w0 + tid * kSpan;  // this thread's span [s0, s0 + 64) (may start past w1)
+    const uint32_t s0 = w0 + tid * kSpanB;  // this thread's span [s0, s0 + 32 kB) (may start past w1)
     const bool active = s0 < w1;
     const uint32_t p = s0 >= base + kWarm ? s0 - kWarm : base;
-    const uint32_t lim = active ? min(n, s0 + kSpan + kShortMax) : p + 1;
+    const uint32_t lim = active ? min(n, s0 + kSpanB + kShortMax) : p + 1;
     // the walk may use 32-bit numerators when its whole key range allows it (warp-uniform choice)
     const uint64_t span_keys = active ? (uint64_t)__ldg(K + lim - 1) - (uint64_t)__ldg(K + p) : 0;
     const bool narrow = __all_sync(0xFFFFFFFFu, span_keys + (uint64_t)eps + 1 < (1ull << 31));
     if (!active) return;
-    const SpecOut o = narrow ? spec_walk<true>(st, p, n, s0, eps) : spec_walk<false>(GlobalKeys<KT>{K}, p, n, s0, eps);
+    const SpecOut<kB> o = narrow ? spec_walk<true, kB>(st, p, n, s0, eps)
+                                 : spec_walk<false, kB>(GlobalKeys<KT>{K}, p, n, s0, eps);
     const uint64_t g = cd.bitword_begin + s0 / kFB;
-    const uint32_t e0 = min(s0 + kFB, n);
-    spec_g[g] = o.m0 & (e0 - s0 < 32 ? (1u << (e0 - s0)) - 1u : 0xFFFFFFFFu);
-    entry_g[g] = o.ent;
-    exit_g[g] = o.mid;
-    if (s0 + kFB < w1) {
-        const uint32_t e1 = min(s0 + 2 * kFB, n);
-        spec_g[g + 1] = o.m1 & (e1 - s0 - kFB < 32 ? (1u << (e1 - s0 - kFB)) - 1u : 0xFFFFFFFFu);
-        entry_g[g + 1] = o.mid;
-        exit_g[g + 1] = o.ex;
+#pragma unroll
+    for (int k = 0; k < kB; ++k) {
+        const uint32_t b0 = s0 + kFB * k;
+        if (b0 >= w1) break;
+        const uint32_t e = min(b0 + kFB, n);
+        spec_g[g + k] = o.m[k] & (e - b0 < 32 ? (1u << (e - b0)) - 1u : 0xFFFFFFFFu);
+        entry_g[g + k] = o.e[k];
+        exit_g[g + k] = o.e[k + 1];
     }
 }
 
@@ -782,7 +795,8 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
                  uint32_t* __restrict__ bitoff, uint16_t* __restrict__ start, uint8_t* __restrict__ width,
                  LongItem* __restrict__ items, uint32_t* __restrict__ nitems, uint32_t items_cap,
                  Piece* __restrict__ pieces, uint32_t* __restrict__ npieces, uint32_t pieces_cap,
-                 ulonglong2* __restrict__ cones, uint32_t* __restrict__ status) {
+                 ulonglong2* __restrict__ cones, uint32_t* __restrict__ status, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0) return;  // a batch replay that does not fit its plan
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr uint32_t kWords = kWinKeys / kFB;
     __shared__ uint32_t s_T[kWords + 4];
@@ -1089,7 +1103,8 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
 template <typename KT>
 __global__ void __launch_bounds__(256)
 long_width_kernel(const KT* __restrict__ keys, LongItem* __restrict__ items, const Piece* __restrict__ pieces,
-                  const uint32_t* __restrict__ npieces, uint32_t pieces_cap) {
+                  const uint32_t* __restrict__ npieces, uint32_t pieces_cap, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     const uint32_t np = min(*npieces, pieces_cap);
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
@@ -1119,7 +1134,8 @@ long_width_kernel(const KT* __restrict__ keys, LongItem* __restrict__ items, con
 __global__ void __launch_bounds__(256)
 bitoff_kernel(const ChunkDesc* __restrict__ chunks, const uint64_t* __restrict__ csb,
               const LongItem* __restrict__ items, uint32_t* __restrict__ bitoff, const uint16_t* __restrict__ start,
-              uint8_t* __restrict__ width, uint32_t* __restrict__ chunk_bits) {
+              uint8_t* __restrict__ width, uint32_t* __restrict__ chunk_bits, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ uint32_t s_scan[32];
     const uint32_t n = chunks[blockIdx.x].n;
     const uint64_t s0 = csb[blockIdx.x], s1 = csb[blockIdx.x + 1];
@@ -1152,7 +1168,9 @@ __global__ void __launch_bounds__(kPackThreads)
 pack_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const uint32_t* __restrict__ tbits,
             const uint64_t* __restrict__ csb, const uint64_t* __restrict__ cwb, const KT* __restrict__ icpt,
             const int64_t* __restrict__ slope, const uint32_t* __restrict__ bitoff,
-            const uint16_t* __restrict__ start, const uint8_t* __restrict__ width, uint32_t* __restrict__ pay32) {
+            const uint16_t* __restrict__ start, const uint8_t* __restrict__ width, uint32_t* __restrict__ pay32,
+            const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0) return;
     __shared__ uint32_t s_T[kMaxChunk / 32];
     __shared__ uint32_t s_pref[kMaxChunk / 32];
     __shared__ uint32_t s_buf[kWin + 4];
@@ -1346,6 +1364,7 @@ static int device_sms() {
 struct FitScratch {
     const WinDesc* wins;
     uint64_t nwins;
+    uint32_t span_log2;  // keys per speculating thread: 2^5, 2^6 (default) or 2^7
     uint32_t *spec, *entry, *exit;
     LongInfo* longinfo;
     LongItem* items;
@@ -1363,25 +1382,40 @@ constexpr uint32_t kShortSlots = (kWinKeys + kShortMax) + (kWinKeys + kShortMax)
 template <typename KT>
 static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, const FitScratch& fs, uint32_t* tbits,
                         uint32_t* counts, uint64_t* csb, uint32_t* status, void* tmp, size_t tmp_bytes,
-                        lc_column* col, cudaStream_t st, int stage) {
+                        lc_column* col, cudaStream_t st, int stage, const uint32_t* gate = nullptr) {
     uint8_t* blob = col->blob;
     const Layout& lay = col->lay;
     if (stage == 0) {
-        static DeviceOnce once;
         const size_t smem = sizeof(uint32_t) * kSpecSlots;
-        if (int rc = smem_attr_once(once, spec_kernel<KT>, smem)) return rc;
+        static DeviceOnce once1, once2, once4;
+        int rc = LC_OK;
         {
             KTime kt("fit_spec", st);
-            spec_kernel<KT><<<(unsigned)fs.nwins, kSpecThreads, smem, st>>>(keys, chunks_d, fs.wins, fs.spec, fs.entry,
-                                                                            fs.exit, status);
+            if (fs.span_log2 == 5) {
+                if (!(rc = smem_attr_once(once1, spec_kernel<KT, 1>, smem)))
+                    spec_kernel<KT, 1><<<(unsigned)fs.nwins, kWinKeys / 32, smem, st>>>(keys, chunks_d, fs.wins,
+                                                                                       fs.spec, fs.entry, fs.exit,
+                                                                                       status);
+            } else if (fs.span_log2 == 7) {
+                if (!(rc = smem_attr_once(once4, spec_kernel<KT, 4>, smem)))
+                    spec_kernel<KT, 4><<<(unsigned)fs.nwins, kWinKeys / 128, smem, st>>>(keys, chunks_d, fs.wins,
+                                                                                        fs.spec, fs.entry, fs.exit,
+                                                                                        status);
+            } else {
+                if (!(rc = smem_attr_once(once2, spec_kernel<KT, 2>, smem)))
+                    spec_kernel<KT, 2><<<(unsigned)fs.nwins, kWinKeys / 64, smem, st>>>(keys, chunks_d, fs.wins,
+                                                                                       fs.spec, fs.entry, fs.exit,
+                                                                                       status);
+            }
         }
+        if (rc) return rc;
         {
             KTime kt("fit_chain", st);
             chain_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0, st>>>(
                 keys, chunks_d, C, fs.spec, fs.entry, fs.exit, tbits, counts, fs.longinfo);
         }
         note_launch(2);
-        int rc = cuda_status(cudaGetLastError());
+        rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         if (fs.roff) {
             static DeviceOnce once_r;
@@ -1411,18 +1445,18 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
             keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
             (int64_t*)(blob + lay.slope), (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start),
             (uint8_t*)(blob + lay.width), fs.items, fs.counters, fs.items_cap, fs.pieces, fs.counters + 1,
-            fs.pieces_cap, fs.cones, status);
+            fs.pieces_cap, fs.cones, status, gate);
     }
     {
         KTime kt("model_long", st);
         long_width_kernel<KT><<<(unsigned)(device_sms() * 8), 256, 0, st>>>(keys, fs.items, fs.pieces, fs.counters + 1,
-                                                                          fs.pieces_cap);
+                                                                          fs.pieces_cap, gate);
     }
     {
         KTime kt("bitoff", st);
         bitoff_kernel<<<(unsigned)C, 256, 0, st>>>(chunks_d, (const uint64_t*)(blob + lay.csb), fs.items,
                                                    (uint32_t*)(blob + lay.bitoff), (const uint16_t*)(blob + lay.start),
-                                                   (uint8_t*)(blob + lay.width), counts);
+                                                   (uint8_t*)(blob + lay.width), counts, gate);
     }
     note_launch(3);
     int rc = cuda_status(cudaGetLastError());
@@ -1434,63 +1468,112 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         pack_kernel<KT><<<(unsigned)C, kPackThreads, 0, st>>>(
             keys, chunks_d, tbits, (const uint64_t*)(blob + lay.csb), (const uint64_t*)(blob + lay.cwb),
             (const KT*)(blob + lay.icpt), (const int64_t*)(blob + lay.slope), (const uint32_t*)(blob + lay.bitoff),
-            (const uint16_t*)(blob + lay.start), (const uint8_t*)(blob + lay.width), (uint32_t*)(blob + lay.payload));
+            (const uint16_t*)(blob + lay.start), (const uint8_t*)(blob + lay.width), (uint32_t*)(blob + lay.payload),
+            gate);
     }
     note_launch();
     return cuda_status(cudaGetLastError());
 }
 
+// The compress pipeline's scratch: chunk table, windows, per-block fit state,
+// anchor bitmap, per-chunk counts, scan partials, status, chunk_seg_begin,
+// long-segment records, their width-pass items and pieces.
+struct PipeScratch {
+    std::vector<WinDesc> wins;
+    uint64_t nwins = 0, C = 0, bitwords = 0, items_cap = 0, pieces_cap = 0;
+    size_t off_chunks = 0, off_wins = 0, off_blk = 0, off_bits = 0, off_counts = 0, off_tmp = 0, off_status = 0,
+           off_csb = 0, off_long = 0, off_items = 0, off_pieces = 0, off_counters = 0, bytes = 0, tmp_bytes = 0;
+    ChunkDesc* chunks_d = nullptr;
+    uint32_t *tbits = nullptr, *counts = nullptr, *status = nullptr;
+    uint64_t* csb_tmp = nullptr;
+    void* tmp = nullptr;
+
+    // Windows and offsets for a chunk table; returns the bytes to allocate.
+    size_t plan(const ChunkDesc* chunks_h, uint64_t C_, uint64_t bitwords_) {
+        C = C_;
+        bitwords = bitwords_;
+        wins.clear();
+        for (uint64_t c = 0; c < C; ++c)
+            for (uint32_t off = 0; off < chunks_h[c].n; off += kWinKeys) wins.push_back(WinDesc{(uint32_t)c, off});
+        nwins = wins.size();
+        tmp_bytes = scan_tmp_bytes(C);
+        auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        off_chunks = 0;
+        off_wins = al(off_chunks + C * sizeof(ChunkDesc));
+        off_blk = al(off_wins + nwins * sizeof(WinDesc));
+        off_bits = al(off_blk + 3 * 4 * bitwords);
+        off_counts = al(off_bits + bitwords * 4);
+        off_tmp = al(off_counts + (C + 1) * 4);
+        off_status = al(off_tmp + tmp_bytes);
+        off_csb = al(off_status + 256);
+        // long segments (> kShortMax keys): at most one per 32-key block, N / (kShortMax + 1) in all
+        uint64_t nkeys = 0;
+        for (uint64_t c = 0; c < C; ++c) nkeys += chunks_h[c].n;
+        items_cap = std::min<uint64_t>(nkeys / (kShortMax + 1) + 1, 0xFFFFFFFFull);
+        pieces_cap = std::min<uint64_t>(items_cap + nkeys / kPiece + 1, 0xFFFFFFFFull);
+        off_long = al(off_csb + (C + 1) * sizeof(uint64_t));
+        off_items = al(off_long + bitwords * sizeof(LongInfo));
+        off_pieces = al(off_items + items_cap * sizeof(LongItem));
+        off_counters = al(off_pieces + pieces_cap * sizeof(Piece));
+        bytes = off_counters + 256;
+        return bytes;
+    }
+    FitScratch bind(uint8_t* scratch) {
+        chunks_d = (ChunkDesc*)(scratch + off_chunks);
+        tbits = (uint32_t*)(scratch + off_bits);
+        counts = (uint32_t*)(scratch + off_counts);
+        tmp = scratch + off_tmp;
+        status = (uint32_t*)(scratch + off_status);
+        csb_tmp = (uint64_t*)(scratch + off_csb);
+        FitScratch fs;
+        fs.wins = (const WinDesc*)(scratch + off_wins);
+        fs.nwins = nwins;
+        fs.spec = (uint32_t*)(scratch + off_blk);
+        fs.entry = fs.spec + bitwords;
+        fs.exit = fs.entry + bitwords;
+        fs.longinfo = (LongInfo*)(scratch + off_long);
+        fs.items = (LongItem*)(scratch + off_items);
+        fs.pieces = (Piece*)(scratch + off_pieces);
+        fs.counters = (uint32_t*)(scratch + off_counters);
+        fs.items_cap = (uint32_t)items_cap;
+        fs.pieces_cap = (uint32_t)pieces_cap;
+        fs.cones = nullptr;
+        fs.roff = nullptr;
+        fs.jbits = nullptr;
+        fs.jlong = nullptr;
+        fs.span_log2 = 6;
+        return fs;
+    }
+    // The per-run resets the pipeline expects (status, long-segment records, counters, pieces).
+    int reset(const FitScratch& fs, cudaStream_t st) const {
+        int rc = cuda_status(cudaMemsetAsync(status, 0, 4, st));
+        if (!rc) rc = cuda_status(cudaMemsetAsync(fs.longinfo, 0, bitwords * sizeof(LongInfo), st));
+        if (!rc) rc = cuda_status(cudaMemsetAsync(fs.counters, 0, 8, st));
+        if (!rc) rc = cuda_status(cudaMemsetAsync(fs.pieces, 0, pieces_cap * sizeof(Piece), st));
+        return rc;
+    }
+};
+
 int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
-                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump) {
+                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump, uint32_t span_log2) {
     int rc = ensure_magic();
     if (rc) return rc;
-    // windows of the speculation kernel
-    std::vector<WinDesc> wins;
-    for (uint64_t c = 0; c < C; ++c)
-        for (uint32_t off = 0; off < chunks_h[c].n; off += kWinKeys) wins.push_back(WinDesc{(uint32_t)c, off});
-    const uint64_t nwins = wins.size();
-    // scratch: chunk table, windows, per-block fit state, anchor bitmap,
-    // per-chunk counts, scan partials, status, chunk_seg_begin
-    const size_t tmp_bytes = scan_tmp_bytes(C);
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t off_chunks = 0;
-    const size_t off_wins = al(off_chunks + C * sizeof(ChunkDesc));
-    const size_t off_blk = al(off_wins + nwins * sizeof(WinDesc));
-    const size_t off_bits = al(off_blk + 3 * 4 * bitwords);
-    const size_t off_counts = al(off_bits + bitwords * 4);
-    const size_t off_tmp = al(off_counts + (C + 1) * 4);
-    const size_t off_status = al(off_tmp + tmp_bytes);
-    const size_t off_csb = al(off_status + 256);
-    // long segments (> kShortMax keys): at most one per 32-key block, N / (kShortMax + 1) in all
-    uint64_t nkeys = 0;
-    for (uint64_t c = 0; c < C; ++c) nkeys += chunks_h[c].n;
-    const uint64_t items_cap = std::min<uint64_t>(nkeys / (kShortMax + 1) + 1, 0xFFFFFFFFull);
-    const uint64_t pieces_cap = std::min<uint64_t>(items_cap + nkeys / kPiece + 1, 0xFFFFFFFFull);
-    const size_t off_long = al(off_csb + (C + 1) * sizeof(uint64_t));
-    const size_t off_items = al(off_long + bitwords * sizeof(LongInfo));
-    const size_t off_pieces = al(off_items + items_cap * sizeof(LongItem));
-    const size_t off_counters = al(off_pieces + pieces_cap * sizeof(Piece));
-    const size_t scratch_bytes = off_counters + 256;
+    PipeScratch ps;
     uint8_t* scratch = nullptr;
-    if (cudaMallocAsync((void**)&scratch, scratch_bytes, st) != cudaSuccess) return LC_ERR_NOMEM;
-    ChunkDesc* chunks_d = (ChunkDesc*)(scratch + off_chunks);
-    FitScratch fs;
-    fs.wins = (const WinDesc*)(scratch + off_wins);
-    fs.nwins = nwins;
-    fs.spec = (uint32_t*)(scratch + off_blk);
-    fs.entry = fs.spec + bitwords;
-    fs.exit = fs.entry + bitwords;
-    uint32_t* tbits = (uint32_t*)(scratch + off_bits);
-    uint32_t* counts = (uint32_t*)(scratch + off_counts);
-    void* tmp = scratch + off_tmp;
-    uint32_t* status = (uint32_t*)(scratch + off_status);
-    uint64_t* csb_tmp = (uint64_t*)(scratch + off_csb);
-    fs.longinfo = (LongInfo*)(scratch + off_long);
-    fs.items = (LongItem*)(scratch + off_items);
-    fs.pieces = (Piece*)(scratch + off_pieces);
-    fs.counters = (uint32_t*)(scratch + off_counters);
-    fs.items_cap = (uint32_t)items_cap;
-    fs.pieces_cap = (uint32_t)pieces_cap;
+    if (cudaMallocAsync((void**)&scratch, ps.plan(chunks_h, C, bitwords), st) != cudaSuccess) return LC_ERR_NOMEM;
+    FitScratch fs = ps.bind(scratch);
+    fs.span_log2 = span_log2;
+    const std::vector<WinDesc>& wins = ps.wins;
+    const uint64_t nwins = ps.nwins;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t off_wins = ps.off_wins;
+    ChunkDesc* chunks_d = ps.chunks_d;
+    uint32_t* tbits = ps.tbits;
+    uint32_t* counts = ps.counts;
+    void* tmp = ps.tmp;
+    const size_t tmp_bytes = ps.tmp_bytes;
+    uint32_t* status = ps.status;
+    uint64_t* csb_tmp = ps.csb_tmp;
     uint64_t total = 0;
     uint32_t h_status = 0;
     fs.cones = nullptr;
@@ -1521,13 +1604,7 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     if (rc) return fail(rc);
     rc = stage_h2d(chunks_d, chunks_h, C * sizeof(ChunkDesc), st);
     if (rc) return fail(rc);
-    rc = cuda_status(cudaMemsetAsync(status, 0, 4, st));
-    if (rc) return fail(rc);
-    rc = cuda_status(cudaMemsetAsync(fs.longinfo, 0, bitwords * sizeof(LongInfo), st));
-    if (rc) return fail(rc);
-    rc = cuda_status(cudaMemsetAsync(fs.counters, 0, 8, st));
-    if (rc) return fail(rc);
-    rc = cuda_status(cudaMemsetAsync(fs.pieces, 0, pieces_cap * sizeof(Piece), st));
+    rc = ps.reset(fs, st);
     if (rc) return fail(rc);
 
     // stage 0: anchors and segment counts
@@ -1592,6 +1669,108 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     cudaFreeAsync(scratch, st);
     cudaFreeAsync(fs.cones, st);
     if (jscratch) cudaFreeAsync(jscratch, st);
+    return LC_OK;
+}
+
+// ------------------------------------------------------------------ the batching graph
+
+namespace {
+// A replay's check against its plan: *gate = 1 while the device total equals
+// the planned one (and, after the first check, the gate was open), else 0,
+// with kStPlan in the column's status word.
+__global__ void plan_gate_kernel(const uint64_t* __restrict__ total, uint64_t want, uint32_t* __restrict__ gate,
+                                 uint32_t* __restrict__ status, int first) {
+    if (threadIdx.x == 0) {
+        const bool ok = *total == want && (first || *gate != 0u);
+        *gate = ok ? 1u : 0u;
+        if (!ok) atomicOr(status, kStPlan);
+    }
+}
+}  // namespace
+
+struct BatchGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint8_t* scratch = nullptr;  // the pipeline's scratch, the cones, the gate, the derived directories' scan scratch
+};
+
+void batch_graph_free(BatchGraph* g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->scratch) {
+        cudaDeviceSynchronize();
+        cudaFree(g->scratch);
+    }
+    delete g;
+}
+
+int batch_graph_launch(BatchGraph* g, cudaStream_t st) { return cuda_status(cudaGraphLaunch(g->exec, st)); }
+
+template <typename KT>
+static int batch_enqueue(const KT* keys, const PipeScratch& ps, const FitScratch& fs, lc_column* col, uint32_t* gate,
+                         void* dtmp, size_t dtmp_bytes, void* out_dev, cudaStream_t st) {
+    const Layout& lay = col->lay;
+    int rc = ps.reset(fs, st);
+    if (!rc) rc = run_pipeline<KT>(keys, ps.chunks_d, ps.C, fs, ps.tbits, ps.counts, ps.csb_tmp, ps.status, ps.tmp,
+                                   ps.tmp_bytes, col, st, 0);
+    if (rc) return rc;
+    plan_gate_kernel<<<1, 32, 0, st>>>(ps.csb_tmp + ps.C, col->L, gate, col->status, 1);
+    note_launch();
+    rc = cuda_status(cudaMemcpyAsync(col->blob + lay.csb, ps.csb_tmp, (ps.C + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    if (!rc) rc = run_pipeline<KT>(keys, ps.chunks_d, ps.C, fs, ps.tbits, ps.counts, ps.csb_tmp, ps.status, ps.tmp,
+                                   ps.tmp_bytes, col, st, 1, gate);
+    if (rc) return rc;
+    plan_gate_kernel<<<1, 32, 0, st>>>((const uint64_t*)(col->blob + lay.cwb) + ps.C, col->W, gate, col->status, 0);
+    note_launch();
+    rc = cuda_status(cudaGetLastError());
+    if (!rc) rc = derived_replay(col, gate, dtmp, dtmp_bytes, out_dev, st);
+    return rc;
+}
+
+int batch_graph_build(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
+                      uint32_t span_log2, lc_column* col, void* out_dev, cudaStream_t st, BatchGraph** out) {
+    *out = nullptr;
+    if (!col->list_mode || C == 0) return LC_ERR_INVALID_ARG;
+    BatchGraph* g = new (std::nothrow) BatchGraph;
+    if (!g) return LC_ERR_NOMEM;
+    PipeScratch ps;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t pipe = al(ps.plan(chunks_h, C, bitwords));
+    const size_t off_cones = pipe, off_gate = al(off_cones + 16 * std::max<uint64_t>(col->L, 1));
+    const size_t off_dtmp = al(off_gate + 256), dtmp_bytes = derived_replay_tmp_bytes(col);
+    int rc = cuda_status(cudaMalloc((void**)&g->scratch, off_dtmp + dtmp_bytes + 256));
+    if (rc) {
+        g->scratch = nullptr;
+        batch_graph_free(g);
+        return rc;
+    }
+    FitScratch fs = ps.bind(g->scratch);
+    fs.span_log2 = span_log2;
+    fs.cones = (ulonglong2*)(g->scratch + off_cones);
+    uint32_t* gate = (uint32_t*)(g->scratch + off_gate);
+    // the descriptors are uploaded once; the graph reads them on every replay
+    rc = stage_h2d(g->scratch + ps.off_wins, ps.wins.data(), ps.nwins * sizeof(WinDesc), st);
+    if (!rc) rc = stage_h2d(ps.chunks_d, chunks_h, C * sizeof(ChunkDesc), st);
+    if (!rc) rc = stage_sync(st);
+    cudaStream_t cs = nullptr;
+    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (!rc) rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    if (!rc) {
+        const int rk = kb == 4 ? batch_enqueue<uint32_t>((const uint32_t*)keys_dev, ps, fs, col, gate,
+                                                         g->scratch + off_dtmp, dtmp_bytes, out_dev, cs)
+                               : batch_enqueue<uint64_t>((const uint64_t*)keys_dev, ps, fs, col, gate,
+                                                         g->scratch + off_dtmp, dtmp_bytes, out_dev, cs);
+        const int re = cuda_status(cudaStreamEndCapture(cs, &g->graph));
+        rc = rk ? rk : re;
+    }
+    if (!rc) rc = cuda_status(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    if (cs) cudaStreamDestroy(cs);
+    if (rc) {
+        batch_graph_free(g);
+        return rc;
+    }
+    *out = g;
     return LC_OK;
 }
 

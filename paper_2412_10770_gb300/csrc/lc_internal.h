@@ -24,6 +24,7 @@ enum : uint32_t {
     kStOutOfRange = 2u,
     kStInternal = 4u,
     kStTimeout = 8u,
+    kStPlan = 16u,  // a batch graph replay does not fit its plan
 };
 
 // One chunk of the fit: keys [key_begin, key_begin + n) of the input, error
@@ -133,6 +134,7 @@ struct ColView {
     uint32_t max_tile_segs;            // most segments meeting one decode tile
     uint32_t key_bytes;
     uint32_t* status;
+    const uint32_t* gate;  // batch graph replays: the kernels that read the column do nothing while *gate == 0
     uint64_t N, C, L, W, ntiles;
     uint32_t chunk_log2;  // 0 in list mode
     uint32_t list_mode;
@@ -164,8 +166,22 @@ namespace lcx {
 // Allocates col->blob and fills everything but the prefix (header, list
 // directory, chunk_key_begin) and the padding bytes; sets col->L, col->W and
 // col->lay.  Synchronizes `st`.
+// span_log2: keys per speculating thread of the fit, 2^5, 2^6 or 2^7 (the bytes do not depend on it).
 int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
-                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump = false);
+                  uint64_t payload_bound_words, cudaStream_t st, lc_column* col, bool jump = false,
+                  uint32_t span_log2 = 6);
+// The batching graph (lc_batch_*): records a replay of the compress that
+// made `col` (same chunk table) and a decode of every key into out_dev.
+struct BatchGraph;
+int batch_graph_build(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint64_t C, uint64_t bitwords,
+                      uint32_t span_log2, lc_column* col, void* out_dev, cudaStream_t st, BatchGraph** out);
+int batch_graph_launch(BatchGraph* g, cudaStream_t st);
+void batch_graph_free(BatchGraph* g);
+// Enqueue only (no host synchronisation): the list-mode derived directories
+// (tile directory, segment records, rank words) and a decode of every key,
+// all gated by *gate.  tmp: derived_replay_tmp_bytes(col) bytes of device scratch.
+size_t derived_replay_tmp_bytes(const lc_column* col);
+int derived_replay(lc_column* col, const uint32_t* gate, void* tmp, size_t tmp_bytes, void* out, cudaStream_t st);
 // Upload the host-built prefix of the blob and zero its padding bytes.
 int finish_blob(lc_column* col, const uint8_t* prefix_h, uint64_t prefix_len, cudaStream_t st);
 

@@ -332,6 +332,7 @@ struct WholeSrc {
 template <typename KT>
 __global__ void __launch_bounds__(kDecThreads, 12) decode_kernel(ColView v, uint64_t t0, uint64_t nt, uint64_t begin,
                                                              uint64_t end, KT* __restrict__ out) {
+    if (v.gate && *v.gate == 0) return;  // a batch replay that does not fit its plan
     extern __shared__ __align__(16) uint8_t smem[];
     dec_pipeline<KT>(nt, WholeSrc<KT>{&v, t0, begin, end, out}, smem, v.max_tile_segs);
 }
@@ -854,6 +855,7 @@ serve_decode_kernel(const ColView* __restrict__ views, const SrvReq* __restrict_
 // Derived directories: segment records and rank bits (one CTA per chunk).
 template <typename KT>
 __global__ void rec_kernel(ColView v, SegRec* __restrict__ recs, RankWord* __restrict__ rank) {
+    if (v.gate && *v.gate == 0) return;
     const uint64_t c = blockIdx.x;
     const uint64_t ckb = v.ckb[c], bit0 = 64 * v.cwb[c];
     const uint64_t s1 = v.csb[c + 1];
@@ -937,6 +939,7 @@ __global__ void ends_kernel(ColView v, uint64_t* __restrict__ ends) {
 }
 
 __global__ void tile_dir_kernel(ColView v, TileDesc* __restrict__ tiles, uint32_t* __restrict__ max_segs) {
+    if (v.gate && *v.gate == 0) return;
     const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (t >= v.ntiles) return;
     uint64_t lo = 0, hi = v.C - 1;  // chunk: last c with chunk_tile_begin[c] <= t
@@ -1079,6 +1082,7 @@ int build_derived(lc_column* col, cudaStream_t st) {
     v.rdx_shift = 0;
     v.key_bytes = col->key_bytes;
     v.status = col->status;
+    v.gate = nullptr;
     v.N = N;
     v.C = C;
     v.L = L;
@@ -1195,10 +1199,11 @@ static unsigned dec_grid(F kernel, size_t smem) {
 
 template <typename KT>
 static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_t begin, uint64_t count, void* out,
-                         cudaStream_t st) {
+                         cudaStream_t st, const ColView* view = nullptr) {
     int rc = set_smem<KT>();
     if (rc) return rc;
-    const size_t smem = dec_smem(col->view.max_tile_segs);
+    const ColView& v = view ? *view : col->view;
+    const size_t smem = dec_smem(v.max_tile_segs);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel<KT>, kDecThreads, smem) != cudaSuccess ||
         occ < 1)
@@ -1206,7 +1211,7 @@ static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_
     const uint64_t grid = std::min<uint64_t>(nt, (uint64_t)sm_count() * occ);
     {
         KTime kt("decode", st);
-        decode_kernel<KT><<<(unsigned)grid, kDecThreads, smem, st>>>(col->view, t0, nt, begin, begin + count, (KT*)out);
+        decode_kernel<KT><<<(unsigned)grid, kDecThreads, smem, st>>>(v, t0, nt, begin, begin + count, (KT*)out);
     }
     note_launch();
     return cuda_status(cudaGetLastError());
@@ -1217,6 +1222,45 @@ int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out
     const uint64_t t0 = host_tile_of(col, begin), t1 = host_tile_of(col, begin + count - 1);
     if (col->key_bytes == 4) return launch_decode<uint32_t>(col, t0, t1 - t0 + 1, begin, count, out, st);
     return launch_decode<uint64_t>(col, t0, t1 - t0 + 1, begin, count, out, st);
+}
+
+size_t derived_replay_tmp_bytes(const lc_column* col) {
+    const uint64_t nw = (col->N + 63) / 64;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return al(4 * nw) + al(8 * (nw + 1)) + scan_tmp_bytes(nw);
+}
+
+int derived_replay(lc_column* col, const uint32_t* gate, void* tmp, size_t tmp_bytes, void* out, cudaStream_t st) {
+    if (!col->list_mode || col->C == 0) return LC_ERR_INVALID_ARG;
+    if (tmp_bytes < derived_replay_tmp_bytes(col)) return LC_ERR_INTERNAL;
+    ColView v = col->view;
+    v.gate = gate;
+    const uint64_t nw = (col->N + 63) / 64;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    RankWord* rank = const_cast<RankWord*>(v.rank);
+    int rc = cuda_status(cudaMemsetAsync(rank, 0, sizeof(RankWord) * nw, st));
+    if (rc) return rc;
+    tile_dir_kernel<<<(unsigned)((col->ntiles + 255) / 256), 256, 0, st>>>(v, col->tiles, col->status + 1);
+    if (col->key_bytes == 4) rec_kernel<uint32_t><<<(unsigned)col->C, 128, 0, st>>>(v, const_cast<SegRec*>(v.recs), rank);
+    else rec_kernel<uint64_t><<<(unsigned)col->C, 128, 0, st>>>(v, const_cast<SegRec*>(v.recs), rank);
+    note_launch(2);
+    rc = cuda_status(cudaGetLastError());
+    if (rc) return rc;
+    uint8_t* t = (uint8_t*)tmp;
+    uint32_t* pop = (uint32_t*)t;
+    uint64_t* before = (uint64_t*)(t + al(4 * nw));
+    const unsigned g = (unsigned)std::min<uint64_t>((nw + 255) / 256, 65535);
+    rank_pop_kernel<<<g, 256, 0, st>>>(rank, nw, pop);
+    note_launch();
+    rc = scan_exclusive(pop, before, nw, ScanOp::Identity, t + al(4 * nw) + al(8 * (nw + 1)), scan_tmp_bytes(nw), st);
+    if (rc) return rc;
+    rank_before_kernel<<<g, 256, 0, st>>>(rank, nw, before);
+    note_launch();
+    rc = cuda_status(cudaGetLastError());
+    if (rc || !out) return rc;
+    const uint64_t nt = col->ntiles;
+    if (col->key_bytes == 4) return launch_decode<uint32_t>(col, 0, nt, 0, col->N, out, st, &v);
+    return launch_decode<uint64_t>(col, 0, nt, 0, col->N, out, st, &v);
 }
 
 int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* count, const uint64_t* out_off,

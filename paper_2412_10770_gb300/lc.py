@@ -27,6 +27,7 @@ LC_ERR_TIMEOUT = -7
 LC_ERR_BUSY = -8
 LC_ERR_INTERNAL = -9
 LC_ERR_UNSUPPORTED = -10
+LC_ERR_STALE = -11
 
 EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", "lc_decode_ranges_noalloc",
            "lc_decode_batch",
@@ -39,7 +40,7 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
            "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes", "lc_compress_jump",
            "lc_pool_usage", "lc_compress_host", "lc_decode_host", "lc_decode_ranges_host", "lc_access_host",
-           "lc_lower_bound_host")
+           "lc_lower_bound_host", "lc_batch_create", "lc_batch_launch", "lc_batch_column", "lc_batch_free")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
 
@@ -52,7 +53,7 @@ class LcError(RuntimeError):
 
 
 class _Params(ctypes.Structure):
-    _fields_ = [("eps", ctypes.c_uint64), ("chunk_log2", ctypes.c_uint32)]
+    _fields_ = [("eps", ctypes.c_uint64), ("chunk_log2", ctypes.c_uint32), ("span_log2", ctypes.c_uint32)]
 
 
 class _Info(ctypes.Structure):
@@ -109,7 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     pu64 = ctypes.POINTER(ctypes.c_uint64)
     sig = {
         "lc_compress": ([p, u64, i32, ctypes.POINTER(_Params), p, pp], i32),
-        "lc_compress_batch": ([p, p, u64, i32, p, p, p, pp], i32),
+        "lc_compress_batch": ([p, p, u64, i32, p, p, ctypes.c_uint32, p, pp], i32),
         "lc_decode": ([p, u64, u64, p, p], i32),
         "lc_decode_ranges": ([p, p, p, p, u64, p, u64, p], i32),
         "lc_decode_ranges_noalloc": ([p, p, p, p, u64, p, u64, p], i32),
@@ -136,6 +137,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_decode_ranges_host": ([p, p, p, p, u64, p, u64, p], i32),
         "lc_access_host": ([p, p, u64, p, p], i32),
         "lc_lower_bound_host": ([p, p, u64, p, p], i32),
+        "lc_batch_create": ([p, p, u64, i32, p, p, ctypes.c_uint32, p, p, pp], i32),
+        "lc_batch_launch": ([p, p], i32),
+        "lc_batch_column": ([p], p),
+        "lc_batch_free": ([p], None),
         "lc_graph_decode": ([p, u64, u64, p, p, pp], i32),
         "lc_graph_launch": ([p, p], i32),
         "lc_graph_free": ([p], None),
@@ -269,12 +274,12 @@ class Column:
         return lc_ratio(self)
 
 
-def lc_compress(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, stream=None) -> Column:
+def lc_compress(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, stream=None, span_log2: int = 0) -> Column:
     lib = load()
     _dev(keys, "keys")
     kb = _key_bytes(keys)
     h = ctypes.c_void_p()
-    prm = _Params(int(eps), int(chunk_log2))
+    prm = _Params(int(eps), int(chunk_log2), int(span_log2))
     _check(lib.lc_compress(keys.data_ptr(), keys.numel(), kb, ctypes.byref(prm), _stream(stream),
                            ctypes.byref(h)), "lc_compress")
     return Column(h.value)
@@ -292,7 +297,7 @@ def lc_compress_jump(keys: torch.Tensor, eps: int = 0, chunk_log2: int = 16, str
     return Column(h.value)
 
 
-def lc_compress_batch(ids: torch.Tensor, list_begin, eps=0, chunk_log2=16, stream=None) -> Column:
+def lc_compress_batch(ids: torch.Tensor, list_begin, eps=0, chunk_log2=16, stream=None, span_log2: int = 0) -> Column:
     lib = load()
     _dev(ids, "ids")
     kb = _key_bytes(ids)
@@ -302,8 +307,78 @@ def lc_compress_batch(ids: torch.Tensor, list_begin, eps=0, chunk_log2=16, strea
     g = np.ascontiguousarray(np.broadcast_to(np.asarray(chunk_log2, dtype=np.uint8), (nl,)))
     h = ctypes.c_void_p()
     _check(lib.lc_compress_batch(ids.data_ptr(), lb.ctypes.data, nl, kb, e.ctypes.data, g.ctypes.data,
-                                 _stream(stream), ctypes.byref(h)), "lc_compress_batch")
+                                 int(span_log2), _stream(stream), ctypes.byref(h)), "lc_compress_batch")
     return Column(h.value)
+
+
+class _BorrowedColumn(Column):
+    """A column owned by someone else (a Batch): free() and free_async() do nothing."""
+
+    def __init__(self, handle: int):
+        super().__init__(handle)
+
+    def free(self) -> None:
+        self.handle = ctypes.c_void_p(0)
+
+    def free_async(self, stream=None) -> None:
+        self.handle = ctypes.c_void_p(0)
+
+
+class Batch:
+    """lc_batch_*: a batched compress of posting lists plus a decode of every
+    list, recorded once into a CUDA graph and replayed by launch()."""
+
+    def __init__(self, ids: torch.Tensor, list_begin, out: torch.Tensor, eps=0, chunk_log2=16, stream=None,
+                 span_log2: int = 0):
+        lib = load()
+        _dev(ids, "ids")
+        kb = _key_bytes(ids)
+        _dev(out, "out")
+        if out.element_size() != kb or out.numel() < ids.numel():
+            raise ValueError("out must hold every id")
+        lb = np.ascontiguousarray(list_begin, dtype=np.uint64)
+        nl = lb.size - 1
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.uint64), (nl,)))
+        g = np.ascontiguousarray(np.broadcast_to(np.asarray(chunk_log2, dtype=np.uint8), (nl,)))
+        h = ctypes.c_void_p()
+        _check(lib.lc_batch_create(ids.data_ptr(), lb.ctypes.data, nl, kb, e.ctypes.data, g.ctypes.data,
+                                   int(span_log2), out.data_ptr(), _stream(stream), ctypes.byref(h)),
+               "lc_batch_create")
+        self.handle = h
+        self._keep = (ids, out)
+        self.column = _BorrowedColumn(lib.lc_batch_column(h))  # owned by the batch
+
+    def launch(self, stream=None) -> None:
+        _check(load().lc_batch_launch(self.handle, _stream(stream)), "lc_batch_launch")
+
+    def free(self) -> None:
+        if self.handle and self.handle.value and _lib is not None:
+            self.column.free()
+            _lib.lc_batch_free(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def lc_batch_create(ids: torch.Tensor, list_begin, out: torch.Tensor, eps=0, chunk_log2=16, stream=None,
+                    span_log2: int = 0) -> Batch:
+    return Batch(ids, list_begin, out, eps, chunk_log2, stream, span_log2)
+
+
+def lc_batch_launch(batch: Batch, stream=None) -> None:
+    batch.launch(stream)
+
+
+def lc_batch_column(batch: Batch) -> Column:
+    return batch.column
+
+
+def lc_batch_free(batch: Batch) -> None:
+    batch.free()
 
 
 def lc_decode(col: Column, begin: int = 0, count: int | None = None, out=None, stream=None) -> torch.Tensor:

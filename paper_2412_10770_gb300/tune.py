@@ -175,3 +175,30 @@ def partition_eps(keys: torch.Tensor, eps_candidates=(0, 1, 3, 7, 15, 31, 63, 12
     info = {"partitions": len(starts), "dp_bytes": total, "best_single_eps": int(eps_candidates[int(np.argmin(single))]),
             "best_single_bytes": float(single.min())}
     return part_begin, part_eps, info
+
+
+SPAN_CANDIDATES = (5, 6, 7)
+
+
+def tune_span(ids: torch.Tensor, begin: np.ndarray, eps, log2, spans=SPAN_CANDIDATES, reps: int = 2):
+    """The third parameter: keys per speculating thread of the fit (2^span_log2;
+    256, 128 or 64 threads per 8192-key window).  It changes the launch, not
+    the bytes, so it is picked by time: the batch is compressed reps times
+    with each candidate (CUDA events, after one untimed run) and the fastest
+    mean wins.  Returns (span_log2, {span_log2: ms})."""
+    stream = torch.cuda.current_stream()
+    times = {}
+    for sp in spans:
+        lc.lc_compress_batch(ids, begin, eps, log2, stream=stream, span_log2=sp).free()
+        ms = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            col = lc.lc_compress_batch(ids, begin, eps, log2, stream=stream, span_log2=sp)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b) / reps
+            col.free()
+        times[sp] = ms
+    best = min(times, key=lambda k: (times[k], k))
+    return best, times

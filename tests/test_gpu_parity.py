@@ -354,3 +354,21 @@ def test_free_async_in_stream_order():
     s.synchronize()
     for out in outs:
         assert np.array_equal(host(out), keys)
+
+
+@pytest.mark.parametrize("span_log2", [5, 6, 7])
+@pytest.mark.parametrize("gen,eps", [("lognormal", 63), ("piecewise", 15), ("clusters", 1), ("lognormal", 0)])
+def test_fit_span_is_a_launch_parameter_only(span_log2, gen, eps):
+    """K^c is the oracle's for every span of the speculating threads (2^5, 2^6, 2^7 keys)."""
+    keys = inputs.column(gen, 700_000 + 333, seed=41, dtype=np.uint64)
+    col = lc.lc_compress(dev(keys), eps=eps, span_log2=span_log2)
+    assert lc.lc_serialize(col) == oracle.compress(keys, eps, 16)
+    col.free()
+
+
+@pytest.mark.parametrize("span_log2", [5, 7])
+def test_fit_span_in_list_mode(span_log2):
+    ids, begin = inputs.posting_lists(800, 1_500_000, 10_000_000, seed=9)
+    col = lc.lc_compress_batch(dev(ids), begin, 7, 14, span_log2=span_log2)
+    assert lc.lc_serialize(col) == oracle.compress_lists(ids, begin, 7, 14)
+    col.free()
