@@ -412,6 +412,8 @@ def main():
             assert torch.equal(out_dec, dev["keys"]), "decode differs from the keys"
             want = np.searchsorted(host["keys"], host["vals"][:100000], side="left")
             assert np.array_equal(out_lb[:100000].cpu().numpy(), want), "lower_bound differs"
+            want = host["keys"][host["idx"][:100000].astype(np.int64)]
+            assert np.array_equal(out_acc[:100000].cpu().numpy(), want), "access differs"
     torch.cuda.synchronize()
 
     gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)

@@ -38,9 +38,10 @@
  *     be read (decode, access, lower_bound) from several streams at once.
  *   - Device memory comes from the device's default stream-ordered pool
  *     (cudaMallocAsync).  The first lc_compress / lc_compress_batch /
- *     lc_deserialize on a device raises that pool's release threshold to
- *     8 GiB, so that up to 8 GiB of freed blocks stay mapped for the next
- *     column instead of being handed back to the CUDA driver at every synchronisation.
+ *     lc_deserialize on a device raises that pool's release threshold to an
+ *     eighth of the device's memory (at least 8 GiB), so that freed blocks up
+ *     to that size stay mapped for the next column instead of being handed
+ *     back to the CUDA driver at every synchronisation.
  *   - Device-side errors (an index >= N in lc_access) are recorded in the
  *     column's status word and reported by lc_status.
  */
@@ -219,6 +220,29 @@ void lc_graph_free(lc_graph* graph);
  * LC_ERR_OUT_OF_RANGE in the status word.  Asynchronous. */
 int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* out_dev,
               void* stream);
+
+/* How lc_access and lc_lower_bound (and their _host forms) run a batch; the
+ * results do not depend on it.
+ *   LC_QUERIES_DIRECT: one query per thread, in the caller's order: each
+ *     query's dependent loads (rank word or radix entry, 32-byte record,
+ *     payload words) go to DRAM once the column's directories and payload
+ *     exceed the L2 cache.
+ *   LC_QUERIES_PARTITIONED: the queries are first sorted into buckets by the
+ *     part of the column they read (key index for access; for lower_bound,
+ *     the value against the keys at multiples of N/B), each bucket's slice of
+ *     the directories and payload being about 16 MB; the buckets then run in
+ *     order, so that their slices are read from L2, and the results are
+ *     scattered back to query order.  Five streaming launches and 10 bytes
+ *     per query of stream-ordered scratch (LC_ERR_NOMEM if the pool has none).
+ *     Batches of 2^32 queries or more run direct.
+ *   LC_QUERIES_AUTO (the default): lc_access partitioned when m >= 2^21,
+ *     the column's records and rank words are at least 96 MB, and there is
+ *     at least one query per 32 bytes of directories and payload; else, and
+ *     for lc_lower_bound (whose lookups are bound by instruction issue, not
+ *     by DRAM), direct.
+ * Process-wide.  Returns the previous setting, or LC_ERR_INVALID_ARG. */
+enum { LC_QUERIES_AUTO = 0, LC_QUERIES_DIRECT = 1, LC_QUERIES_PARTITIONED = 2 };
+int lc_set_query_plan(int plan);
 
 /* Value lower_bound through the segment directory (Sec. III-A segment
  * pruning, Table 2 binary search over segments): out[q] = first i with

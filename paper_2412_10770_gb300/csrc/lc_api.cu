@@ -246,10 +246,12 @@ static std::vector<uint8_t> build_prefix(const lc_column* col, const uint64_t* l
     return b;
 }
 
-// Keep up to kPoolRetain bytes of freed pool memory mapped (once per device):
-// a column's blob, directories and scratch are allocated and freed per call,
-// and re-mapping them after every synchronisation costs milliseconds.
-constexpr uint64_t kPoolRetain = 8ull << 30;
+// Keep up to an eighth of the device's memory (at least 8 GB) of freed pool
+// memory mapped (once per device): a column's blob, directories and scratch
+// are allocated and freed per call, several columns' worth can be in flight
+// on concurrent streams, and re-mapping them after every synchronisation
+// costs milliseconds.
+constexpr uint64_t kPoolRetainMin = 8ull << 30;
 
 static void retain_pool(int dev) {
     static std::once_flag once[64];
@@ -257,11 +259,12 @@ static void retain_pool(int dev) {
     std::call_once(once[dev], [dev] {
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        size_t free_b = 0, total_b = 0;
+        uint64_t want = kPoolRetainMin;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) want = std::max<uint64_t>(want, total_b / 8);
         uint64_t cur = 0;
-        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < kPoolRetain) {
-            uint64_t thr = kPoolRetain;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-        }
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < want)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
     });
 }
 
@@ -741,6 +744,8 @@ int lc_lower_bound(const lc_column* col, const void* v_dev, uint64_t m, uint64_t
     if (col->list_mode) return LC_ERR_UNSUPPORTED;
     return lower_bound(col, v_dev, m, out_dev, (cudaStream_t)stream);
 }
+
+int lc_set_query_plan(int plan) { return set_query_plan(plan); }
 
 // ------------------------------------------------------------------ host-buffer entry points
 //

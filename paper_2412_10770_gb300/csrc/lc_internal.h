@@ -194,6 +194,7 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
 int decode_ranges_noalloc(const lc_column* col, const uint64_t* begin, const uint64_t* count,
                           const uint64_t* out_off, uint64_t m, void* out, uint64_t out_cap, cudaStream_t st);
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st);
+int set_query_plan(int plan);  // lc_set_query_plan
 int lower_bound(const lc_column* col, const void* v, uint64_t m, uint64_t* out, cudaStream_t st);
 int quantile(const lc_column* col, const uint64_t* ks, uint64_t m, uint64_t q, int exact, void* out, cudaStream_t st);
 int decode_approx(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);

@@ -458,6 +458,12 @@ __device__ __forceinline__ uint64_t ld_stream(const T* p, uint64_t pol) {
         asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
         return r;
     }
+    if (sizeof(T) == 2) {
+        uint16_t r;
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(p), "l"(pol));
+        return r;
+    }
+    static_assert(sizeof(T) == 8 || sizeof(T) == 4 || sizeof(T) == 2, "8-, 4- or 2-byte stream elements");
     uint32_t r;
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
     return r;
@@ -601,37 +607,45 @@ __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uin
     const uint32_t w = (uint32_t)(r.kstart_w >> 56);
     if (a < b && w) {
         // the residuals of the bracket usually lie in 8 payload words: two
-        // 16-byte loads, and the search then runs on registers instead of
-        // two loads per probe
+        // 16-byte loads, and the search then runs on registers instead of a
+        // load per probe.  Probes that read the payload first narrow a
+        // bracket whose residuals do not fit one such window.
         const uint64_t bit1 = r.bit1_n & kBitMask;
-        const uint64_t q0 = (bit1 + (uint64_t)w * (a - 1)) >> 5;      // word of residual a
-        const uint64_t q1 = (bit1 + (uint64_t)w * (b - 1) - 1) >> 5;  // word of residual b - 1's last bit
-        const uint64_t base = q0 & ~3ull;
-        if (q1 + 1 < base + 8 && base + 8 <= 2 * v.W) {
+        auto fits = [&](uint32_t lo_t, uint32_t hi_t) {
+            const uint64_t q0 = (bit1 + (uint64_t)w * (lo_t - 1)) >> 5;      // word of residual lo_t
+            const uint64_t q1 = (bit1 + (uint64_t)w * (hi_t - 1) - 1) >> 5;  // word of residual hi_t - 1's last bit
+            const uint64_t base = q0 & ~3ull;
+            return q1 + 1 < base + 8 && base + 8 <= 2 * v.W;
+        };
+        while (a < b && !fits(a, b)) {
+            const uint32_t mid = (a + b) >> 1;
+            if (rec_key_hint(v, r, mid, stream) < x) a = mid + 1;
+            else b = mid;
+        }
+        if (a < b) {
+            const uint64_t base = ((bit1 + (uint64_t)w * (a - 1)) >> 5) & ~3ull;
             const ulonglong2 u = ld2_hint(v.pay32 + base, stream), u2 = ld2_hint(v.pay32 + base + 4, stream);
-            // pr[k] = words k and k + 1 of the window as one 64-bit value, k < 7
-            const uint64_t pr[7] = {u.x, (u.x >> 32) | (u.y << 32), u.y, (u.y >> 32) | (u2.x << 32),
-                                    u2.x, (u2.x >> 32) | (u2.y << 32), u2.y};
-            auto pair = [&](uint32_t k) {  // pr[k] by selects (no local memory)
-                uint64_t r0 = pr[0];
-#pragma unroll
-                for (uint32_t c = 1; c < 7; ++c) r0 = k == c ? pr[c] : r0;
-                return r0;
-            };
-            const uint64_t off = bit1 - 32 * base;
-            const uint64_t wmask = (1ull << w) - 1;  // w <= 32
+            const uint32_t W0 = (uint32_t)u.x, W1 = (uint32_t)(u.x >> 32), W2 = (uint32_t)u.y,
+                           W3 = (uint32_t)(u.y >> 32), W4 = (uint32_t)u2.x, W5 = (uint32_t)(u2.x >> 32),
+                           W6 = (uint32_t)u2.y, W7 = (uint32_t)(u2.y >> 32);
+            const uint64_t off = bit1 - 32 * base;  // mod 2^64: the positions below are in [0, 256)
             while (a < b) {
                 const uint32_t mid = (a + b) >> 1;
                 const uint32_t pos = (uint32_t)(off + (uint64_t)w * (mid - 1));
-                const uint32_t z = (uint32_t)((pair(pos >> 5) >> (pos & 31u)) & wmask);
+                // words k and k + 1 of the window (k = pos / 32 < 7), three levels of selects
+                const uint32_t k = pos >> 5;
+                const bool b2 = k & 4u, b1 = k & 2u, b0 = k & 1u;
+                const uint32_t a0 = b2 ? W4 : W0, a1 = b2 ? W5 : W1, a2 = b2 ? W6 : W2, a3 = b2 ? W7 : W3;
+                const uint32_t c0 = b1 ? a2 : a0, c1 = b1 ? a3 : a1, c2 = b1 ? (b2 ? W7 : W4) : a2;
+                const uint32_t z = extract_bits(b0 ? c1 : c0, b0 ? c2 : c1, pos & 31u, w);
                 const uint64_t key = r.icpt + (uint64_t)(line_at(r.slope, mid) + (int64_t)unzigzag32(z));
                 if (key < x) a = mid + 1;
                 else b = mid;
             }
-            return ks + a;
         }
+        return ks + a;
     }
-    while (a < b) {
+    while (a < b) {  // w = 0: the keys lie on the line
         const uint32_t mid = (a + b) >> 1;
         if (rec_key_hint(v, r, mid, stream) < x) a = mid + 1;
         else b = mid;
@@ -1009,6 +1023,270 @@ int set_smem() {
     });
 }
 
+// ------------------------------------------------------------------ partitioned batches of random queries
+//
+// A large batch of random queries over a column whose directories exceed L2
+// misses on each of a query's dependent loads (rank word, record, payload
+// word; for lower_bound the radix entry, intercept offsets, record and
+// bracket words): about 70 bytes of DRAM each.  Sorted by the part of the
+// column they read into buckets of about kPartBucketBytes of directories and
+// payload, and run bucket after bucket, the queries of one bucket share an
+// L2-resident slice of the column, so each of its lines comes from DRAM about
+// once.  The results are the same function of each query; only the order of
+// work changes.  The batch is cut into tiles of kPartTile queries, one CTA
+// each, and the queries of bucket b from tile c go to slot base[b * T + c]
+// onwards (bucket-major, so the buckets lie in order).  Launches:
+//   part_count    per tile, the count of each bucket
+//   scan          the bucket-major offsets base[]
+//   part_scatter  per tile, a counting sort in shared memory: the tile's
+//                 queries in bucket order, each bucket's run written to its
+//                 slot range as one coalesced piece, and for each query its
+//                 position in the sorted tile (16 bits)
+//   part_lookup   the queries in bucket order, results over them in place
+//   part_gather   per tile, each bucket's run of results read back as one
+//                 piece into shared memory, then out[q] in query order
+// Buckets: key index >> shift for access; for lower_bound the count of
+// splitters below the value, the splitters being the keys at multiples of N/B
+// (equal key counts per bucket, whatever the value distribution).
+constexpr uint32_t kPartThreads = 256;
+constexpr uint32_t kPartTile = 4096;                      // queries per tile (CTA)
+constexpr uint32_t kPartPer = kPartTile / kPartThreads;   // queries per thread
+constexpr uint32_t kPartMaxBuckets = 256;                 // bucket ids fit a byte
+constexpr uint64_t kPartBucketBytes = 16ull << 20;
+static_assert(kPartMaxBuckets <= kPartThreads, "the tile scan gives one bucket to a thread");
+static_assert(kPartTile <= 65536, "positions within a tile are 16-bit");
+
+__device__ __forceinline__ uint64_t policy_normal() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// A coherent streaming load (the lookup writes its results over the keys it read).
+__device__ __forceinline__ uint64_t ld_rw_stream(const uint64_t* p, uint64_t pol) {
+    uint64_t r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ void st16_hint(void* ptr, uint16_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(ptr), "h"(v), "l"(pol) : "memory");
+}
+
+struct PartPlan {
+    uint32_t B;             // buckets, <= kPartMaxBuckets
+    uint32_t shift;         // access: bucket = index >> shift
+    const uint64_t* split;  // lower_bound: B - 1 ascending keys
+    uint64_t T;             // tiles
+    uint64_t N;
+};
+
+template <bool BY_VALUE>
+__device__ __forceinline__ uint32_t part_bucket(uint64_t key, const PartPlan& pp, const uint64_t* s_split) {
+    if (!BY_VALUE) return (uint32_t)((key < pp.N ? key : pp.N - 1) >> pp.shift);
+    uint32_t lo = 0, hi = pp.B - 1;  // count of splitters < key
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_split[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <bool BY_VALUE>
+__device__ __forceinline__ void part_load_split(const PartPlan& pp, uint64_t* s_split) {
+    if (BY_VALUE)
+        for (uint32_t k = threadIdx.x; k + 1 < pp.B; k += blockDim.x) s_split[k] = pp.split[k];
+}
+
+// Exclusive prefix sum of s[0, B) in place (B <= blockDim.x = kPartThreads).
+__device__ __forceinline__ void tile_scan(uint32_t* s, uint32_t B, uint32_t* s_warp) {
+    const uint32_t t = threadIdx.x, lane = t & 31u, w = t >> 5;
+    const uint32_t v = t < B ? s[t] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(~0u, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t z = lane < kPartThreads / 32 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (uint32_t d = 1; d < kPartThreads / 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(~0u, z, d);
+            if (lane >= d) z += y;
+        }
+        if (lane < kPartThreads / 32) s_warp[lane] = z;
+    }
+    __syncthreads();
+    if (t < B) s[t] = (w ? s_warp[w - 1] : 0u) + x - v;
+    __syncthreads();
+}
+
+// Splitters for lower_bound: the key at floor((k + 1) N / B), k < B - 1.
+__global__ void part_split_kernel(ColView v, uint32_t B, uint64_t* __restrict__ split) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k + 1 >= B) return;
+    const uint64_t q = v.N / B, r = v.N % B;
+    const uint64_t i = q * (k + 1) + r * (k + 1) / B;  // r (k + 1) < B^2
+    split[k] = access_one(v, i, policy_keep(), policy_normal());
+}
+
+template <bool BY_VALUE, typename QT>
+__global__ void __launch_bounds__(kPartThreads) part_count_kernel(const QT* __restrict__ keys, uint64_t m, PartPlan pp,
+                                                                  uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t s_cnt[kPartMaxBuckets];
+    __shared__ uint64_t s_split[BY_VALUE ? kPartMaxBuckets : 1];
+    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) s_cnt[b] = 0;
+    part_load_split<BY_VALUE>(pp, s_split);
+    __syncthreads();
+    const uint64_t pol = policy_stream();
+    const uint64_t c = blockIdx.x, q0 = c * kPartTile;
+    const uint32_t nt = (uint32_t)min((uint64_t)kPartTile, m - q0);
+    uint64_t kk[kPartPer];
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        kk[u] = j < nt ? ld_stream(keys + q0 + j, pol) : 0;
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u)
+        if (u * kPartThreads + threadIdx.x < nt) atomicAdd(&s_cnt[part_bucket<BY_VALUE>(kk[u], pp, s_split)], 1u);
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) cnt[(uint64_t)b * pp.T + c] = s_cnt[b];
+}
+
+template <bool BY_VALUE, typename QT>
+__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const QT* __restrict__ keys, uint64_t m, PartPlan pp,
+                                                                    const uint64_t* __restrict__ base,
+                                                                    uint64_t* __restrict__ bkey,
+                                                                    uint16_t* __restrict__ pos) {
+    __shared__ uint64_t s_key[kPartTile];  // the tile's queries in bucket order
+    __shared__ uint8_t s_bkt[kPartTile];   // and the bucket of each
+    __shared__ uint32_t s_cnt[kPartMaxBuckets];
+    __shared__ uint64_t s_gb[kPartMaxBuckets];
+    __shared__ uint64_t s_split[BY_VALUE ? kPartMaxBuckets : 1];
+    __shared__ uint32_t s_warp[kPartThreads / 32];
+    const uint64_t c = blockIdx.x, q0 = c * kPartTile;
+    const uint32_t nt = (uint32_t)min((uint64_t)kPartTile, m - q0);
+    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) {
+        s_cnt[b] = 0;
+        s_gb[b] = base[(uint64_t)b * pp.T + c];
+    }
+    part_load_split<BY_VALUE>(pp, s_split);
+    __syncthreads();
+    const uint64_t pol = policy_stream();
+    uint64_t kk[kPartPer];
+    uint32_t code[kPartPer];  // bucket << 16 | rank within the bucket
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        kk[u] = j < nt ? ld_stream(keys + q0 + j, pol) : 0;
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        if (u * kPartThreads + threadIdx.x < nt) {
+            const uint32_t b = part_bucket<BY_VALUE>(kk[u], pp, s_split);
+            code[u] = (b << 16) | atomicAdd(&s_cnt[b], 1u);
+        }
+    }
+    __syncthreads();
+    tile_scan(s_cnt, pp.B, s_warp);  // s_cnt[b]: first position of bucket b in the sorted tile
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        if (j < nt) {
+            const uint32_t b = code[u] >> 16, at = s_cnt[b] + (code[u] & 0xffffu);
+            s_key[at] = kk[u];
+            s_bkt[at] = (uint8_t)b;
+            st16_hint(pos + q0 + j, (uint16_t)at, pol);
+        }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < nt; j += kPartThreads) {
+        const uint32_t b = s_bkt[j];
+        bkey[s_gb[b] + (j - s_cnt[b])] = s_key[j];
+    }
+}
+
+// The queries in bucket order; bkey[e] becomes the result of query bkey[e].
+// The column's lines are read with the normal L2 priority: a bucket's slice
+// is reused by its queries, the query stream is not.
+template <bool BY_VALUE, typename KT>
+__global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, uint64_t* __restrict__ bkey, uint64_t m) {
+    const uint64_t normal = policy_normal(), stream = policy_stream();
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t kn = e < m ? ld_rw_stream(bkey + e, stream) : 0;
+    for (; e < m; e += step) {
+        const uint64_t key = kn;
+        if (e + step < m) kn = ld_rw_stream(bkey + e + step, stream);
+        uint64_t r;
+        if (BY_VALUE) {
+            r = lower_bound_one<KT>(v, key, normal, normal);
+        } else if (key < v.N) {
+            r = access_one(v, key, normal, normal);
+        } else {
+            atomicOr(v.status, kStOutOfRange);
+            r = 0;
+        }
+        st64_hint(bkey + e, r, stream);
+    }
+}
+
+template <typename OT>
+__global__ void __launch_bounds__(kPartThreads) part_gather_kernel(const uint64_t* __restrict__ res,
+                                                                   const uint16_t* __restrict__ pos, uint64_t m,
+                                                                   PartPlan pp, const uint32_t* __restrict__ cnt,
+                                                                   const uint64_t* __restrict__ base,
+                                                                   OT* __restrict__ out) {
+    __shared__ uint64_t s_res[kPartTile];  // the tile's results in bucket order
+    __shared__ uint32_t s_lb[kPartMaxBuckets];
+    __shared__ uint64_t s_gb[kPartMaxBuckets];
+    __shared__ uint32_t s_warp[kPartThreads / 32];
+    const uint64_t c = blockIdx.x, q0 = c * kPartTile;
+    const uint32_t nt = (uint32_t)min((uint64_t)kPartTile, m - q0);
+    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) {
+        s_lb[b] = cnt[(uint64_t)b * pp.T + c];
+        s_gb[b] = base[(uint64_t)b * pp.T + c];
+    }
+    __syncthreads();
+    tile_scan(s_lb, pp.B, s_warp);
+    const uint64_t normal = policy_normal(), stream = policy_stream();
+    uint32_t pq[kPartPer];  // each query's position in the sorted tile, loaded early
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        pq[u] = j < nt ? (uint32_t)ld_stream(pos + q0 + j, stream) : 0u;
+    }
+    uint64_t rr[kPartPer];
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        rr[u] = 0;
+        if (j < nt) {
+            uint32_t lo = 0, hi = pp.B - 1;  // the last bucket whose run starts at or before j
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (s_lb[mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            rr[u] = ld64_hint(res + s_gb[lo] + (j - s_lb[lo]), normal);
+        }
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        if (j < nt) s_res[j] = rr[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t u = 0; u < kPartPer; ++u) {
+        const uint32_t j = u * kPartThreads + threadIdx.x;
+        if (j < nt) st_stream(out + q0 + j, s_res[pq[u]], stream);
+    }
+}
+
 }  // namespace
 
 int build_derived(lc_column* col, cudaStream_t st) {
@@ -1305,8 +1583,127 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
     return rc;
 }
 
+// How a batch of access / lower_bound queries runs (lc_set_query_plan).
+static std::atomic<int> g_query_plan{LC_QUERIES_AUTO};
+
+int set_query_plan(int plan) {
+    if (plan != LC_QUERIES_AUTO && plan != LC_QUERIES_DIRECT && plan != LC_QUERIES_PARTITIONED)
+        return LC_ERR_INVALID_ARG;
+    return g_query_plan.exchange(plan);
+}
+
+namespace {
+
+constexpr uint64_t kPartMinQueries = 1ull << 21;
+constexpr uint64_t kPartMinDirBytes = 96ull << 20;  // about three quarters of L2
+
+// The bucket plan of a partitioned batch of m queries, or false when the batch
+// runs direct.  Under LC_QUERIES_AUTO an access batch runs direct when it is
+// small, when the records and rank words would mostly stay in L2 anyway --
+// then a direct lookup misses at most on its payload word, and the
+// partitioned plan, whose lookup is bound by the L2's request rate, is no
+// faster -- or when there are fewer than one query per 32 bytes of
+// directories and payload (little reuse within a bucket).  A lower_bound
+// batch always runs direct under LC_QUERIES_AUTO: its lookup is bound by
+// instruction issue (the search inside the segment), not by DRAM, and the
+// partitioned plan only adds its streaming passes.
+bool part_plan(const lc_column* col, uint64_t m, bool by_value, PartPlan* pp) {
+    const int plan = g_query_plan.load(std::memory_order_relaxed);
+    const ColView& v = col->view;
+    if (plan == LC_QUERIES_DIRECT || m >= (1ull << 32) || v.N == 0) return false;
+    if (plan == LC_QUERIES_AUTO && by_value) return false;
+    const uint64_t dir = by_value ? 32 * v.L + 8 * (((v.kmax - v.kmin) >> v.rdx_shift) + 2) + (uint64_t)v.ioff_bytes * v.L
+                                  : 32 * v.L + 16 * ((v.N + 63) / 64);
+    const uint64_t bytes = dir + 8 * v.W;
+    if (plan == LC_QUERIES_AUTO && (m < kPartMinQueries || dir < kPartMinDirBytes || 32 * m < bytes)) return false;
+    uint64_t B = (bytes + kPartBucketBytes - 1) / kPartBucketBytes;
+    if (plan == LC_QUERIES_PARTITIONED) B = std::max<uint64_t>(B, 16);  // several buckets even on small columns
+    B = std::min<uint64_t>(std::max<uint64_t>(B, 1), kPartMaxBuckets);
+    pp->N = v.N;
+    pp->split = nullptr;
+    pp->shift = 0;
+    if (!by_value) {  // buckets of 2^shift key indices
+        const uint64_t per = (v.N + B - 1) / B;
+        while ((1ull << pp->shift) < per) ++pp->shift;
+        pp->B = (uint32_t)(((v.N - 1) >> pp->shift) + 1);
+    } else {
+        pp->B = (uint32_t)B;
+    }
+    pp->T = (m + kPartTile - 1) / kPartTile;
+    return true;
+}
+
+// A partitioned batch: keys are the m indices (access) or values
+// (lower_bound), out the m results.  Scratch from the stream-ordered pool,
+// released in stream order: 10 bytes per query plus 12 per bucket and tile.
+template <bool BY_VALUE, typename KT, typename QT, typename OT>
+int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan pp, OT* out, cudaStream_t st) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const uint64_t n = (uint64_t)pp.B * pp.T;
+    const size_t tmp_b = scan_tmp_bytes(n);
+    const size_t o_pos = al(8 * m), o_cnt = o_pos + al(2 * m), o_base = o_cnt + al(4 * n);
+    const size_t o_tmp = o_base + al(8 * (n + 1)), o_split = o_tmp + al(tmp_b), total = o_split + al(8 * pp.B);
+    uint8_t* p = nullptr;
+    if (cudaMallocAsync((void**)&p, total, st) != cudaSuccess) return LC_ERR_NOMEM;
+    uint64_t* bkey = (uint64_t*)p;
+    uint16_t* pos = (uint16_t*)(p + o_pos);
+    uint32_t* cnt = (uint32_t*)(p + o_cnt);
+    uint64_t* base = (uint64_t*)(p + o_base);
+    uint64_t* split = (uint64_t*)(p + o_split);
+    int rc = LC_OK;
+    if (BY_VALUE) {
+        pp.split = split;
+        if (pp.B > 1) {
+            part_split_kernel<<<(pp.B + 255) / 256, 256, 0, st>>>(col->view, pp.B, split);
+            note_launch();
+            rc = cuda_status(cudaGetLastError());
+        }
+    }
+    if (!rc) {
+        KTime kt(BY_VALUE ? "lower_bound.count" : "access.count", st);
+        part_count_kernel<BY_VALUE, QT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(keys, m, pp, cnt);
+        note_launch();
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (!rc) rc = scan_exclusive(cnt, base, n, ScanOp::Identity, p + o_tmp, tmp_b, st);
+    if (!rc) {
+        KTime kt(BY_VALUE ? "lower_bound.scatter" : "access.scatter", st);
+        part_scatter_kernel<BY_VALUE, QT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(keys, m, pp, base, bkey, pos);
+        note_launch();
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (!rc) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, part_lookup_kernel<BY_VALUE, KT>, 256, 0) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
+        const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * occ);
+        KTime kt(BY_VALUE ? "lower_bound.lookup" : "access.lookup", st);
+        part_lookup_kernel<BY_VALUE, KT><<<grid, 256, 0, st>>>(col->view, bkey, m);
+        note_launch();
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (!rc) {
+        KTime kt(BY_VALUE ? "lower_bound.gather" : "access.gather", st);
+        part_gather_kernel<OT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(bkey, pos, m, pp, cnt, base, out);
+        note_launch();
+        rc = cuda_status(cudaGetLastError());
+    }
+    const int rf = cuda_status(cudaFreeAsync(p, st));
+    return rc ? rc : rf;
+}
+
+}  // namespace
+
 int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cudaStream_t st) {
     if (m == 0) return LC_OK;
+    PartPlan pp;
+    if (part_plan(col, m, false, &pp)) {
+        KTime kt("access", st);
+        if (col->key_bytes == 4)
+            return run_partitioned<false, uint32_t>(col, idx, m, pp, (uint32_t*)out, st);
+        return run_partitioned<false, uint64_t>(col, idx, m, pp, (uint64_t*)out, st);
+    }
     const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * 16);
     {
         KTime kt("access", st);
@@ -1320,6 +1717,13 @@ int access(const lc_column* col, const uint64_t* idx, uint64_t m, void* out, cud
 int lower_bound(const lc_column* col, const void* vals, uint64_t m, uint64_t* out, cudaStream_t st) {
     if (m == 0) return LC_OK;
     const ColView& v = col->view;
+    PartPlan pp;
+    if (part_plan(col, m, true, &pp)) {
+        KTime kt("lower_bound", st);
+        if (col->key_bytes == 4)
+            return run_partitioned<true, uint32_t>(col, (const uint32_t*)vals, m, pp, out, st);
+        return run_partitioned<true, uint64_t>(col, (const uint64_t*)vals, m, pp, out, st);
+    }
     // one query per thread, as many CTAs as stay resident (grid-stride)
     int occ = 0;
     const cudaError_t oe = col->key_bytes == 4

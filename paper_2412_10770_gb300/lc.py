@@ -40,9 +40,11 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_for_compress", "lc_for_decode", "lc_for_size", "lc_for_serialize", "lc_for_free",
            "lc_quantile", "lc_decode_approx", "lc_intersect", "lc_union", "lc_chunk_bytes", "lc_compress_jump",
            "lc_pool_usage", "lc_compress_host", "lc_decode_host", "lc_decode_ranges_host", "lc_access_host",
-           "lc_lower_bound_host", "lc_batch_create", "lc_batch_launch", "lc_batch_column", "lc_batch_free")
+           "lc_lower_bound_host", "lc_batch_create", "lc_batch_launch", "lc_batch_column", "lc_batch_free",
+           "lc_set_query_plan")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
+LC_QUERIES_AUTO, LC_QUERIES_DIRECT, LC_QUERIES_PARTITIONED = 0, 1, 2
 
 
 class LcError(RuntimeError):
@@ -117,6 +119,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lc_decode_batch": ([p, p, p], i32),
         "lc_access": ([p, p, u64, p, p], i32),
         "lc_lower_bound": ([p, p, u64, p, p], i32),
+        "lc_set_query_plan": ([i32], i32),
         "lc_access1": ([p, u64, pu64], i32),
         "lc_lower_bound1": ([p, u64, pu64], i32),
         "lc_ratio": ([p], ctypes.c_double),
@@ -454,6 +457,15 @@ def lc_lower_bound(col: Column, values: torch.Tensor, out=None, stream=None) -> 
     _check(lib.lc_lower_bound(col.handle, values.data_ptr(), values.numel(), out.data_ptr(), _stream(stream)),
            "lc_lower_bound")
     return out
+
+
+def lc_set_query_plan(plan: int) -> int:
+    """How lc_access / lc_lower_bound run a batch (LC_QUERIES_AUTO, _DIRECT or
+    _PARTITIONED; process-wide); returns the previous setting."""
+    rc = load().lc_set_query_plan(int(plan))
+    if rc < 0:
+        _check(rc, "lc_set_query_plan")
+    return rc
 
 
 def lc_access1(col: Column, i: int) -> int:
