@@ -234,14 +234,21 @@ int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* o
  *     order, so that their slices are read from L2, and the results are
  *     scattered back to query order.  Five streaming launches and 10 bytes
  *     per query of stream-ordered scratch (LC_ERR_NOMEM if the pool has none).
- *     Batches of 2^32 queries or more run direct.
- *   LC_QUERIES_AUTO (the default): lc_access partitioned when m >= 2^21,
- *     the column's records and rank words are at least 96 MB, and there is
- *     at least one query per 32 bytes of directories and payload; else, and
- *     for lc_lower_bound (whose lookups are bound by instruction issue, not
- *     by DRAM), direct.
- * Process-wide.  Returns the previous setting, or LC_ERR_INVALID_ARG. */
-enum { LC_QUERIES_AUTO = 0, LC_QUERIES_DIRECT = 1, LC_QUERIES_PARTITIONED = 2 };
+ *   LC_QUERIES_DECODED: the column is first decoded whole (one bulk decode
+ *     into N keys of stream-ordered scratch), then the queries run
+ *     partitioned against the decoded keys: an access reads its key there, a
+ *     lower_bound finds its segment through the directories and searches the
+ *     segment's decoded keys.  For dense batches (m comparable to N).
+ *   LC_QUERIES_AUTO (the default): lc_access decoded when m >= 2^21,
+ *     m >= N/8 and the keys take at least 64 MB; else partitioned when
+ *     m >= 2^21, the column's records and rank words are at least 96 MB, and
+ *     there is at least one query per 32 bytes of directories and payload;
+ *     else direct.  lc_lower_bound direct (its lookups are bound by
+ *     instruction issue; searching decoded keys is a chain of dependent
+ *     loads).
+ * Batches of 2^32 queries or more run direct.  Process-wide.  Returns the
+ * previous setting, or LC_ERR_INVALID_ARG. */
+enum { LC_QUERIES_AUTO = 0, LC_QUERIES_DIRECT = 1, LC_QUERIES_PARTITIONED = 2, LC_QUERIES_DECODED = 3 };
 int lc_set_query_plan(int plan);
 
 /* Value lower_bound through the segment directory (Sec. III-A segment

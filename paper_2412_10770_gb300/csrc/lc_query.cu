@@ -553,10 +553,9 @@ __global__ void access_kernel(ColView v, const uint64_t* __restrict__ idx, uint6
 // 32-byte record, the payload words of the bracket.
 __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uint64_t x, uint64_t j, uint64_t stream);
 
+// The last segment whose intercept (its first key) is < x, for kmin < x <= kmax.
 template <typename KT>
-__device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x, uint64_t keep, uint64_t stream) {
-    if (v.L == 0 || x <= v.kmin) return 0;
-    if (x > v.kmax) return v.N;
+__device__ __forceinline__ uint64_t segment_below(const ColView& v, uint64_t x, uint64_t keep) {
     const uint64_t q = (x - v.kmin) >> v.rdx_shift;
     uint64_t lo = min(ld64_hint(v.rdx + q, keep), v.L), hi = min(ld64_hint(v.rdx + q + 1, keep), v.L);
     if (v.ioff_bytes) {
@@ -580,8 +579,14 @@ __device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x
             else hi = mid;
         }
     }
-    const uint64_t j = lo ? lo - 1 : 0;  // lo >= 1 for sorted keys: icpt[0] = kmin < x
-    return lower_bound_in_segment(v, x, j, stream);
+    return lo ? lo - 1 : 0;  // lo >= 1 for sorted keys: icpt[0] = kmin < x
+}
+
+template <typename KT>
+__device__ __forceinline__ uint64_t lower_bound_one(const ColView& v, uint64_t x, uint64_t keep, uint64_t stream) {
+    if (v.L == 0 || x <= v.kmin) return 0;
+    if (x > v.kmax) return v.N;
+    return lower_bound_in_segment(v, x, segment_below<KT>(v, x, keep), stream);
 }
 
 // The first key index of segment j or after it whose key is >= x, given
@@ -1073,6 +1078,7 @@ __device__ __forceinline__ void st16_hint(void* ptr, uint16_t v, uint64_t pol) {
 
 struct PartPlan {
     uint32_t B;             // buckets, <= kPartMaxBuckets
+    uint32_t dense;         // 1: the lookups read a decoded copy of the column
     uint32_t shift;         // access: bucket = index >> shift
     const uint64_t* split;  // lower_bound: B - 1 ascending keys
     uint64_t T;             // tiles
@@ -1209,11 +1215,34 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const QT* __
     }
 }
 
+// The first index in [ks + 1, ks + n] whose decoded key is >= x, given that
+// the key at ks (segment j's intercept) is < x: a binary search of the decoded
+// keys of the segment.
+template <typename KT>
+__device__ __forceinline__ uint64_t lower_bound_decoded(const ColView& v, const KT* __restrict__ D, uint64_t x,
+                                                        uint64_t pol) {
+    if (v.L == 0 || x <= v.kmin) return 0;
+    if (x > v.kmax) return v.N;
+    const SegRec r = load_rec_hint(v.recs + segment_below<KT>(v, x, pol), pol);
+    const uint64_t ks = r.kstart_w & kKeyMask;
+    uint32_t a = 1, b = (uint32_t)(r.bit1_n >> 48) + 1u;
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        const uint64_t k = sizeof(KT) == 8 ? ld64_hint(D + ks + mid, pol) : (uint64_t)ld32_hint(D + ks + mid, pol);
+        if (k < x) a = mid + 1;
+        else b = mid;
+    }
+    return ks + a;
+}
+
 // The queries in bucket order; bkey[e] becomes the result of query bkey[e].
 // The column's lines are read with the normal L2 priority: a bucket's slice
-// is reused by its queries, the query stream is not.
-template <bool BY_VALUE, typename KT>
-__global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, uint64_t* __restrict__ bkey, uint64_t m) {
+// is reused by its queries, the query stream is not.  DENSE: D holds every
+// key decoded; access reads its key there, lower_bound searches there inside
+// the segment the directories give.
+template <bool BY_VALUE, bool DENSE, typename KT>
+__global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, const KT* __restrict__ D,
+                                                             uint64_t* __restrict__ bkey, uint64_t m) {
     const uint64_t normal = policy_normal(), stream = policy_stream();
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
     uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -1223,9 +1252,10 @@ __global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, uint64_t
         if (e + step < m) kn = ld_rw_stream(bkey + e + step, stream);
         uint64_t r;
         if (BY_VALUE) {
-            r = lower_bound_one<KT>(v, key, normal, normal);
+            r = DENSE ? lower_bound_decoded<KT>(v, D, key, normal) : lower_bound_one<KT>(v, key, normal, normal);
         } else if (key < v.N) {
-            r = access_one(v, key, normal, normal);
+            r = DENSE ? (sizeof(KT) == 8 ? ld64_hint(D + key, normal) : (uint64_t)ld32_hint(D + key, normal))
+                      : access_one(v, key, normal, normal);
         } else {
             atomicOr(v.status, kStOutOfRange);
             r = 0;
@@ -1235,7 +1265,7 @@ __global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, uint64_t
 }
 
 template <typename OT>
-__global__ void __launch_bounds__(kPartThreads) part_gather_kernel(const uint64_t* __restrict__ res,
+__global__ void __launch_bounds__(kPartThreads, 4) part_gather_kernel(const uint64_t* __restrict__ res,
                                                                    const uint16_t* __restrict__ pos, uint64_t m,
                                                                    PartPlan pp, const uint32_t* __restrict__ cnt,
                                                                    const uint64_t* __restrict__ base,
@@ -1477,7 +1507,7 @@ static unsigned dec_grid(F kernel, size_t smem) {
 
 template <typename KT>
 static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_t begin, uint64_t count, void* out,
-                         cudaStream_t st, const ColView* view = nullptr) {
+                         cudaStream_t st, const ColView* view = nullptr, const char* name = "decode") {
     int rc = set_smem<KT>();
     if (rc) return rc;
     const ColView& v = view ? *view : col->view;
@@ -1488,7 +1518,7 @@ static int launch_decode(const lc_column* col, uint64_t t0, uint64_t nt, uint64_
         occ = 1;
     const uint64_t grid = std::min<uint64_t>(nt, (uint64_t)sm_count() * occ);
     {
-        KTime kt("decode", st);
+        KTime kt(name, st);
         decode_kernel<KT><<<(unsigned)grid, kDecThreads, smem, st>>>(v, t0, nt, begin, begin + count, (KT*)out);
     }
     note_launch();
@@ -1587,7 +1617,8 @@ int decode_ranges(const lc_column* col, const uint64_t* begin, const uint64_t* c
 static std::atomic<int> g_query_plan{LC_QUERIES_AUTO};
 
 int set_query_plan(int plan) {
-    if (plan != LC_QUERIES_AUTO && plan != LC_QUERIES_DIRECT && plan != LC_QUERIES_PARTITIONED)
+    if (plan != LC_QUERIES_AUTO && plan != LC_QUERIES_DIRECT && plan != LC_QUERIES_PARTITIONED &&
+        plan != LC_QUERIES_DECODED)
         return LC_ERR_INVALID_ARG;
     return g_query_plan.exchange(plan);
 }
@@ -1596,29 +1627,44 @@ namespace {
 
 constexpr uint64_t kPartMinQueries = 1ull << 21;
 constexpr uint64_t kPartMinDirBytes = 96ull << 20;  // about three quarters of L2
+constexpr uint64_t kPartMinDecodedBytes = 64ull << 20;
 
-// The bucket plan of a partitioned batch of m queries, or false when the batch
-// runs direct.  Under LC_QUERIES_AUTO an access batch runs direct when it is
-// small, when the records and rank words would mostly stay in L2 anyway --
-// then a direct lookup misses at most on its payload word, and the
-// partitioned plan, whose lookup is bound by the L2's request rate, is no
-// faster -- or when there are fewer than one query per 32 bytes of
-// directories and payload (little reuse within a bucket).  A lower_bound
-// batch always runs direct under LC_QUERIES_AUTO: its lookup is bound by
-// instruction issue (the search inside the segment), not by DRAM, and the
-// partitioned plan only adds its streaming passes.
+// The bucket plan of a batch of m queries, or false when the batch runs
+// direct.  Under LC_QUERIES_AUTO:
+// * a dense access batch (at least one query per 8 keys) on a column whose
+//   keys take 64 MB or more runs decoded: one bulk decode of the column, then
+//   each query reads its key from the decoded copy, bucket by bucket;
+// * else an access batch runs partitioned through the directories when it is
+//   large, the records and rank words exceed three quarters of L2, and there
+//   is at least one query per 32 bytes of directories and payload -- then a
+//   direct lookup would miss L2 on each dependent load, while the partitioned
+//   lookup is bound by the L2's request rate;
+// * else direct.  A lower_bound batch always runs direct: its lookup is bound
+//   by instruction issue (the search inside the segment) more than by DRAM,
+//   and a search of the decoded keys is a chain of dependent loads.
 bool part_plan(const lc_column* col, uint64_t m, bool by_value, PartPlan* pp) {
     const int plan = g_query_plan.load(std::memory_order_relaxed);
     const ColView& v = col->view;
     if (plan == LC_QUERIES_DIRECT || m >= (1ull << 32) || v.N == 0) return false;
-    if (plan == LC_QUERIES_AUTO && by_value) return false;
+    const uint64_t kb = col->key_bytes;
     const uint64_t dir = by_value ? 32 * v.L + 8 * (((v.kmax - v.kmin) >> v.rdx_shift) + 2) + (uint64_t)v.ioff_bytes * v.L
                                   : 32 * v.L + 16 * ((v.N + 63) / 64);
-    const uint64_t bytes = dir + 8 * v.W;
-    if (plan == LC_QUERIES_AUTO && (m < kPartMinQueries || dir < kPartMinDirBytes || 32 * m < bytes)) return false;
+    bool dense;
+    if (plan == LC_QUERIES_AUTO) {
+        const bool big = m >= kPartMinQueries;
+        if (by_value) return false;
+        dense = big && 8 * m >= v.N && kb * v.N >= kPartMinDecodedBytes;
+        if (!dense && (!big || dir < kPartMinDirBytes || 32 * m < dir + 8 * v.W)) return false;
+    } else {
+        dense = plan == LC_QUERIES_DECODED;
+    }
+    // bytes a bucket's lookups read: the decoded keys (and for lower_bound the
+    // directories), or the directories and the payload
+    const uint64_t bytes = dense ? kb * v.N + (by_value ? dir : 0) : dir + 8 * v.W;
     uint64_t B = (bytes + kPartBucketBytes - 1) / kPartBucketBytes;
-    if (plan == LC_QUERIES_PARTITIONED) B = std::max<uint64_t>(B, 16);  // several buckets even on small columns
+    if (plan != LC_QUERIES_AUTO) B = std::max<uint64_t>(B, 16);  // several buckets even on small columns
     B = std::min<uint64_t>(std::max<uint64_t>(B, 1), kPartMaxBuckets);
+    pp->dense = dense ? 1u : 0u;
     pp->N = v.N;
     pp->split = nullptr;
     pp->shift = 0;
@@ -1635,14 +1681,16 @@ bool part_plan(const lc_column* col, uint64_t m, bool by_value, PartPlan* pp) {
 
 // A partitioned batch: keys are the m indices (access) or values
 // (lower_bound), out the m results.  Scratch from the stream-ordered pool,
-// released in stream order: 10 bytes per query plus 12 per bucket and tile.
+// released in stream order: 10 bytes per query plus 12 per bucket and tile,
+// and the decoded column when the plan is dense.
 template <bool BY_VALUE, typename KT, typename QT, typename OT>
 int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan pp, OT* out, cudaStream_t st) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const uint64_t n = (uint64_t)pp.B * pp.T;
     const size_t tmp_b = scan_tmp_bytes(n);
     const size_t o_pos = al(8 * m), o_cnt = o_pos + al(2 * m), o_base = o_cnt + al(4 * n);
-    const size_t o_tmp = o_base + al(8 * (n + 1)), o_split = o_tmp + al(tmp_b), total = o_split + al(8 * pp.B);
+    const size_t o_tmp = o_base + al(8 * (n + 1)), o_split = o_tmp + al(tmp_b), o_dec = o_split + al(8 * pp.B);
+    const size_t total = o_dec + (pp.dense ? al(sizeof(KT) * col->N) : 0);
     uint8_t* p = nullptr;
     if (cudaMallocAsync((void**)&p, total, st) != cudaSuccess) return LC_ERR_NOMEM;
     uint64_t* bkey = (uint64_t*)p;
@@ -1650,8 +1698,12 @@ int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan p
     uint32_t* cnt = (uint32_t*)(p + o_cnt);
     uint64_t* base = (uint64_t*)(p + o_base);
     uint64_t* split = (uint64_t*)(p + o_split);
+    KT* dec = pp.dense ? (KT*)(p + o_dec) : nullptr;
     int rc = LC_OK;
-    if (BY_VALUE) {
+    if (pp.dense)  // every key, decoded once (the bulk decode launch)
+        rc = launch_decode<KT>(col, 0, col->ntiles, 0, col->N, dec, st, nullptr,
+                               BY_VALUE ? "lower_bound.decode" : "access.decode");
+    if (BY_VALUE && !rc) {
         pp.split = split;
         if (pp.B > 1) {
             part_split_kernel<<<(pp.B + 255) / 256, 256, 0, st>>>(col->view, pp.B, split);
@@ -1673,13 +1725,12 @@ int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan p
         rc = cuda_status(cudaGetLastError());
     }
     if (!rc) {
+        auto kern = pp.dense ? part_lookup_kernel<BY_VALUE, true, KT> : part_lookup_kernel<BY_VALUE, false, KT>;
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, part_lookup_kernel<BY_VALUE, KT>, 256, 0) !=
-                cudaSuccess || occ < 1)
-            occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1) occ = 1;
         const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * occ);
         KTime kt(BY_VALUE ? "lower_bound.lookup" : "access.lookup", st);
-        part_lookup_kernel<BY_VALUE, KT><<<grid, 256, 0, st>>>(col->view, bkey, m);
+        kern<<<grid, 256, 0, st>>>(col->view, dec, bkey, m);
         note_launch();
         rc = cuda_status(cudaGetLastError());
     }

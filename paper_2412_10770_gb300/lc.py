@@ -44,7 +44,7 @@ EXPORTS = ("lc_compress", "lc_compress_batch", "lc_decode", "lc_decode_ranges", 
            "lc_set_query_plan")
 
 LC_OP_ACCESS, LC_OP_LOWER_BOUND, LC_OP_DECODE = 1, 2, 3
-LC_QUERIES_AUTO, LC_QUERIES_DIRECT, LC_QUERIES_PARTITIONED = 0, 1, 2
+LC_QUERIES_AUTO, LC_QUERIES_DIRECT, LC_QUERIES_PARTITIONED, LC_QUERIES_DECODED = 0, 1, 2, 3
 
 
 class LcError(RuntimeError):
@@ -460,8 +460,8 @@ def lc_lower_bound(col: Column, values: torch.Tensor, out=None, stream=None) -> 
 
 
 def lc_set_query_plan(plan: int) -> int:
-    """How lc_access / lc_lower_bound run a batch (LC_QUERIES_AUTO, _DIRECT or
-    _PARTITIONED; process-wide); returns the previous setting."""
+    """How lc_access / lc_lower_bound run a batch (LC_QUERIES_AUTO, _DIRECT,
+    _PARTITIONED or _DECODED; process-wide); returns the previous setting."""
     rc = load().lc_set_query_plan(int(plan))
     if rc < 0:
         _check(rc, "lc_set_query_plan")

@@ -3,13 +3,15 @@ decoding; Sec. III-A lower_bound): out[q] = K[idx[q]] for access and the
 first i with K[i] >= v[q] (numpy searchsorted) for lower_bound.
 
 * direct: one query per thread in the caller's order;
-* partitioned: queries sorted into key-range buckets, run bucket by bucket,
-  results scattered back (forced here on small columns with at least 16
-  buckets, so that every bucket boundary, ragged tile and empty bucket case
-  is reached);
-* the automatic choice partitions a large access batch on a column whose
-  records and rank words exceed three quarters of L2, and its results are
-  the same.
+* partitioned: queries sorted into key-range buckets, run bucket by bucket
+  through the directories, results scattered back (forced here on small
+  columns with at least 16 buckets, so that every bucket boundary, ragged
+  tile and empty bucket case is reached);
+* decoded: the column decoded whole first, then the same buckets answered
+  from the decoded keys;
+* the automatic choice (decoded for dense batches, partitioned for large
+  sparse access batches on columns whose directories exceed L2, else
+  direct), with the same results.
 """
 from __future__ import annotations
 
@@ -62,10 +64,13 @@ def _values(keys: np.ndarray, m: int, seed: int) -> np.ndarray:
     return pool[rng.permutation(pool.size)[:m]]
 
 
+PLANS = (lc.LC_QUERIES_PARTITIONED, lc.LC_QUERIES_DECODED, lc.LC_QUERIES_DIRECT)
+
+
 def _both_plans(col, keys, idx, vals):
     want_a = keys[idx.astype(np.int64)]
     want_l = np.searchsorted(keys, vals, side="left")
-    for plan in (lc.LC_QUERIES_PARTITIONED, lc.LC_QUERIES_DIRECT):
+    for plan in PLANS:
         lc.lc_set_query_plan(plan)
         assert np.array_equal(host(lc.lc_access(col, dev(idx))), want_a), plan
         assert np.array_equal(host(lc.lc_lower_bound(col, dev(vals))), want_l), plan
@@ -117,12 +122,12 @@ def test_partitioned_out_of_range_indices():
     idx = inputs.uniform_ranks(50_000, n, seed=3)
     bad = np.array([1, 77, 49_999])
     idx[bad] = [n, n + 12345, np.iinfo(np.uint64).max]
-    lc.lc_set_query_plan(lc.LC_QUERIES_PARTITIONED)
-    got = host(lc.lc_access(col, dev(idx)))
     want = np.where(idx < n, keys[np.minimum(idx, n - 1).astype(np.int64)], 0)
-    assert np.array_equal(got, want)
-    assert lc.lc_status(col) == lc.LC_ERR_OUT_OF_RANGE
-    assert lc.lc_status(col) == lc.LC_OK
+    for plan in (lc.LC_QUERIES_PARTITIONED, lc.LC_QUERIES_DECODED):
+        lc.lc_set_query_plan(plan)
+        assert np.array_equal(host(lc.lc_access(col, dev(idx))), want)
+        assert lc.lc_status(col) == lc.LC_ERR_OUT_OF_RANGE
+        assert lc.lc_status(col) == lc.LC_OK
     col.free()
 
 
@@ -130,62 +135,66 @@ def test_partitioned_list_mode_access():
     ids, begin = inputs.posting_lists(300, 400_000, 5_000_000, seed=8)
     col = lc.lc_compress_batch(dev(ids), begin, 7, 12)
     idx = inputs.uniform_ranks(100_000, ids.size, seed=4)
-    for plan in (lc.LC_QUERIES_PARTITIONED, lc.LC_QUERIES_DIRECT):
+    for plan in PLANS:
         lc.lc_set_query_plan(plan)
         assert np.array_equal(host(lc.lc_access(col, dev(idx))), ids[idx.astype(np.int64)])
     col.free()
 
 
-def test_auto_plan_partitions_a_large_batch_on_a_large_column():
-    """6e7 lognormal keys at eps 63 (about 2.8M segments: 105 MB of records
-    and rank words), 8e6 queries: the automatic plan partitions the access
-    batch (its kernels show in the launch trace) and runs lower_bound direct,
-    and the results are the definitions; a small batch, and a column with few
-    segments, run direct."""
-    n, m = 60_000_000, 8_000_000
-    keys = inputs.column("lognormal", n, seed=7)
-    col = lc.lc_compress(dev(keys), eps=63)
-    idx = inputs.uniform_ranks(m, n, seed=9)
-    vals = _values(keys, m, seed=10)
+def _traced(fn):
     lc.lc_timing_read()
     lc.lc_timing_enable(True)
     try:
-        got_a = host(lc.lc_access(col, dev(idx)))
-        got_l = host(lc.lc_lower_bound(col, dev(vals)))
+        out = fn()
         torch.cuda.synchronize()
     finally:
         lc.lc_timing_enable(False)
-    names = lc.lc_timing_read()
-    assert "access.lookup" in names and "lower_bound.lookup" not in names, sorted(names)
-    assert np.array_equal(got_a, keys[idx.astype(np.int64)])
-    assert np.array_equal(got_l, np.searchsorted(keys, vals, side="left"))
-    # a small batch on the same column runs direct
-    lc.lc_timing_enable(True)
-    try:
-        small = idx[:1000]
-        assert np.array_equal(host(lc.lc_access(col, dev(small))), keys[small.astype(np.int64)])
-        torch.cuda.synchronize()
-    finally:
-        lc.lc_timing_enable(False)
-    assert "access.lookup" not in lc.lc_timing_read()
+    return out, lc.lc_timing_read()
+
+
+def test_auto_plans():
+    """6e7 lognormal keys at eps 63 (about 2.8M segments: 105 MB of records
+    and rank words): a dense access batch (8e6 queries, more than one per 8
+    keys) runs decoded, a sparse large one (5e6) partitioned through the
+    directories, a small one direct; lower_bound runs direct.  On a piecewise
+    column (few segments) a dense access batch runs decoded too.  The plans
+    show in the launch trace; every result is the definition."""
+    n = 60_000_000
+    keys = inputs.column("lognormal", n, seed=7)
+    col = lc.lc_compress(dev(keys), eps=63)
+    for m, want_acc in ((8_000_000, {"access.decode", "access.lookup"}), (5_000_000, {"access.lookup"}),
+                        (1000, set())):
+        idx = inputs.uniform_ranks(m, n, seed=9)
+        vals = _values(keys, m, seed=10)
+        got, names = _traced(lambda: host(lc.lc_access(col, dev(idx))))
+        assert np.array_equal(got, keys[idx.astype(np.int64)])
+        assert {k for k in names if k.startswith("access.")} >= want_acc, (m, sorted(names))
+        assert ("access.decode" in names) == ("access.decode" in want_acc)
+        assert ("access.lookup" in names) == ("access.lookup" in want_acc)
+        got, names = _traced(lambda: host(lc.lc_lower_bound(col, dev(vals))))
+        assert np.array_equal(got, np.searchsorted(keys, vals, side="left"))
+        assert not any(k.startswith("lower_bound.") for k in names), (m, sorted(names))
     assert lc.lc_status(col) == lc.LC_OK
     col.free()
     few = inputs.column("piecewise", n, seed=8)
     col = lc.lc_compress(dev(few), eps=63)
-    lc.lc_timing_enable(True)
-    try:
-        assert np.array_equal(host(lc.lc_access(col, dev(idx))), few[idx.astype(np.int64)])
-        torch.cuda.synchronize()
-    finally:
-        lc.lc_timing_enable(False)
-    assert "access.lookup" not in lc.lc_timing_read()
+    idx = inputs.uniform_ranks(8_000_000, n, seed=11)
+    vals = _values(few, 8_000_000, seed=12)
+    got, names = _traced(lambda: host(lc.lc_access(col, dev(idx))))
+    assert np.array_equal(got, few[idx.astype(np.int64)])
+    assert "access.decode" in names
+    got, names = _traced(lambda: host(lc.lc_lower_bound(col, dev(vals))))
+    assert np.array_equal(got, np.searchsorted(few, vals, side="left"))
+    assert "lower_bound.lookup" not in names
     col.free()
 
 
 def test_plan_setting():
     assert lc.lc_set_query_plan(lc.LC_QUERIES_DIRECT) == lc.LC_QUERIES_AUTO
     assert lc.lc_set_query_plan(lc.LC_QUERIES_PARTITIONED) == lc.LC_QUERIES_DIRECT
-    with pytest.raises(lc.LcError) as e:
-        lc.lc_set_query_plan(3)
-    assert e.value.code == lc.LC_ERR_INVALID_ARG
-    assert lc.lc_set_query_plan(lc.LC_QUERIES_AUTO) == lc.LC_QUERIES_PARTITIONED
+    assert lc.lc_set_query_plan(lc.LC_QUERIES_DECODED) == lc.LC_QUERIES_PARTITIONED
+    for bad in (4, -1):
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_set_query_plan(bad)
+        assert e.value.code == lc.LC_ERR_INVALID_ARG
+    assert lc.lc_set_query_plan(lc.LC_QUERIES_AUTO) == lc.LC_QUERIES_DECODED
