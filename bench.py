@@ -119,7 +119,8 @@ def dram_traffic(kernel: str, units_per_launch: float):
         return None, None
     caps = k["captures"]
     per_unit = sum(c["dram_bytes_per_launch"] / c["units_per_launch"] for c in caps) / len(caps)
-    note = (f"mean DRAM bytes per {k['unit'][:-1]} of {len(caps)} single-launch ncu captures "
+    unit1 = {"queries": "query", "keys": "key"}.get(k["unit"], k["unit"])
+    note = (f"mean DRAM bytes per {unit1} of {len(caps)} single-launch ncu captures "
             f"({'; '.join(c['workload'] for c in caps)}), scaled to {units_per_launch:.3g} {k['unit']}: "
             f"{k['summary']}")
     return per_unit * units_per_launch, note
