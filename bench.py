@@ -72,7 +72,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-analytics", action="store_true", help="skip the quantile and segments-only rows")
-    ap.add_argument("--no-eps-rows", action="store_true", help="skip the compress/decode rows at eps 1 and 255")
+    ap.add_argument("--no-eps-rows", action="store_true", help="skip the compress/decode rows at eps 1, 15, 63 and 255")
     ap.add_argument("--no-served", action="store_true", help="skip the serving measurement of the default run")
     return ap.parse_args()
 
@@ -535,7 +535,7 @@ def main():
                        "api": "lc_compress_host / lc_decode_host / lc_decode_ranges_host / lc_access_host / "
                               "lc_lower_bound_host (copies inside the C-ABI calls)",
                        "host_link": link, "link_floor_ms": floor_ms, "frac_of_link": floor_ms / e2e["ms"]}
-    # config-2 compress and decode at eps 1 and 255 (beside the step's eps), and compress at every span
+    # config-2 compress and decode at eps 1, 15, 63 and 255 with per-kernel times, and compress at every span
     if not args.no_eps_rows:
         line["eps_rows"] = measure_eps_rows(args, cols, lc, torch, stream, peak)
         line["span_rows"] = measure_span_rows(args, cols, lc, torch, stream)
@@ -1078,17 +1078,20 @@ def measure_span_rows(args, cols, lc, torch, stream) -> dict:
 
 
 def measure_eps_rows(args, cols, lc, torch, stream, peak) -> dict:
-    """Compress and full decode of every column at eps 1 and 255 (beside the
-    step's eps): mean of 3 runs each, CUDA events; algorithmic bytes as in the
-    step (compress N kb + |K^c|, decode |K^c| + N kb)."""
+    """Compress and full decode of every column at eps 1, 15, 63 and 255:
+    mean of 3 runs each, CUDA events; algorithmic bytes as in the step
+    (compress N kb + |K^c|, decode |K^c| + N kb); with the compress's
+    per-kernel device time (lc_timing, mean ms per compress)."""
     N, kb = args.n, 8
     out = torch.empty(N, dtype=torch.uint64, device="cuda")
     rows = {}
-    for eps in (1, 255):
+    for eps in (1, 15, 63, 255):
         per = {}
         for g, host, dev in cols:
             tc = td = 0.0
             size = 0
+            lc.lc_timing_read()
+            lc.lc_timing_enable(True)
             for _ in range(3):
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record(stream)
@@ -1101,8 +1104,13 @@ def measure_eps_rows(args, cols, lc, torch, stream, peak) -> dict:
                 td += e1.elapsed_time(e2) / 3
                 size = lc.lc_size(col)
                 col.free_async(stream)
+            torch.cuda.synchronize()
+            lc.lc_timing_enable(False)
+            kt = lc.lc_timing_read()
             assert torch.equal(out, dev["keys"]), f"decode at eps {eps} differs from the keys"
             per[g] = {"compress_ms": tc, "compress_keys_per_s": N / tc * 1e3,
+                      "compress_kernels_ms": {k: v[1] / 3 for k, v in sorted(kt.items())
+                                              if k != "decode" and not k.startswith("host:")},
                       "compress_hbm_frac": (N * kb + size) / (tc / 1e3) / 1e9 / peak,
                       "decode_ms": td, "decode_keys_per_s": N / td * 1e3,
                       "decode_hbm_frac": (N * kb + size) / (td / 1e3) / 1e9 / peak,
