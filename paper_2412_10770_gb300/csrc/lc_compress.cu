@@ -818,8 +818,13 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     const int64_t eps = cd.eps;
     const uint32_t tid = threadIdx.x;
     const uint32_t top = min(n, w1 + kShortMax);
-    KT* s = (KT*)smem;
-    for (uint32_t q = tid; q < top - w0; q += kShortThreads) s[q + (q >> 5)] = __ldg(K + w0 + q);
+    // the low 32 bits of K[i] - K[w0]: a difference of two staged values is
+    // exact whenever the true difference is below 2^32, which holds for every
+    // run a narrow warp walks; wide warps read their keys from global memory
+    uint32_t* s = (uint32_t*)smem;
+    const uint64_t kbase = (uint64_t)__ldg(K + w0);
+    for (uint32_t q = tid; q < top - w0; q += kShortThreads)
+        s[q + (q >> 5)] = (uint32_t)((uint64_t)__ldg(K + w0 + q) - kbase);
     const uint32_t* __restrict__ T = tbits + cd.bitword_begin;
     const uint32_t k0 = w0 / kFB, nT = (top - w0 + kFB - 1) / kFB;
     for (uint32_t q = tid; q < kWords + 4; q += kShortThreads) s_T[q] = q < nT ? T[k0 + q] : 0u;
@@ -836,7 +841,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
         s_base = t;
     }
     __syncthreads();
-    const Staged<KT> st{s, w0};
+    const Staged<uint32_t> st32{s, w0};
     const uint32_t nw = (w1 - w0 + kFB - 1) / kFB;
     const uint32_t word = tid < nw ? s_T[tid] : 0u;
     const uint32_t pre = block_excl_scan<uint32_t>(__popc(word), AddOp(), 0u, s_warp, nullptr);
@@ -897,8 +902,14 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     const uint32_t wend = word && e_last == kNone ? a_last + 1 : (has_block ? b1 : lo);
     const uint32_t wstart = aP != kNone ? b0 : lo + 1;  // first key walked
     const uint32_t hi = tail ? e_last : wend;            // past the last key any piece of this thread's cones holds
-    const uint64_t range = hi > lo + 1 ? st(hi - 1) - st(lo) : 0;
+    const uint64_t range = hi > lo + 1 ? (uint64_t)__ldg(K + hi - 1) - (uint64_t)__ldg(K + lo) : 0;
     const bool narrow = __all_sync(0xFFFFFFFFu, range + (uint64_t)eps + 1 < (1ull << 31));
+    // key i: its staged offset (narrow warps) or the key itself; the
+    // difference of two keys of one walked run, exact either way
+    auto key = [&](uint32_t i) -> uint64_t { return narrow ? st32(i) : (uint64_t)__ldg(K + i); };
+    auto diff = [&](uint64_t ki, uint64_t kj) -> int64_t {
+        return narrow ? (int64_t)(uint32_t)(ki - kj) : (int64_t)(ki - kj);
+    };
     const uint64_t j_first = j;
     const uint32_t nown = __popc(word);                           // segments owned, the last maybe long
     const uint32_t nshort = nown - (word && e_last == kNone ? 1u : 0u);
@@ -942,16 +953,16 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     s_pa[tid] = kNone;
     {
         uint32_t a = lo;
-        uint64_t ka = lo < hi ? st(lo) : 0;
+        uint64_t ka = lo < hi ? key(lo) : 0;
         for (uint32_t i = wstart; i < wend; ++i) {
-            const uint64_t Ki = st(i);
+            const uint64_t Ki = key(i);
             if (is_anchor(i)) {
                 if (a == aP && i == pend) {  // the prefix piece ends at the block's first anchor
                     s_pc[tid] = pack(2);
                     s_pa[tid] = aP;
                 } else {
                     cones[j] = pack(i - a);
-                    icpt[j] = (KT)ka;
+                    icpt[j] = __ldg(K + a);
                     start[j] = (uint16_t)a;
                     ++j;
                 }
@@ -967,7 +978,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
             s_pa[tid] = aP;
         } else if (word && e_last != kNone && !tail) {  // the last segment ends at b1
             cones[j] = pack(e_last - a);
-            icpt[j] = (KT)ka;
+            icpt[j] = __ldg(K + a);
             start[j] = (uint16_t)a;
         }
         __syncthreads();
@@ -986,9 +997,9 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
                     if (p.y * (uint64_t)c.F < c.Y * (uint64_t)F) { c.Y = p.y; c.F = F; }
                 }
             }
-            for (uint32_t i = max(w1, wend); i < e_last; ++i) cone_key(st(i), ka, i - a);
+            for (uint32_t i = max(w1, wend); i < e_last; ++i) cone_key(key(i), ka, i - a);
             cones[j] = pack(e_last - a);
-            icpt[j] = (KT)ka;
+            icpt[j] = __ldg(K + a);
             start[j] = (uint16_t)a;
         }
     }
@@ -1012,11 +1023,11 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     {
         j = j_first;
         uint32_t a = lo;
-        uint64_t ka = lo < hi ? st(lo) : 0;
+        uint64_t ka = lo < hi ? key(lo) : 0;
         int64_t M = aP != kNone ? slope[j_first - 1] : (word ? slope[j_first] : 0);
         uint32_t zmax = 0;
         for (uint32_t i = wstart; i < wend; ++i) {
-            const uint64_t Ki = st(i);
+            const uint64_t Ki = key(i);
             if (is_anchor(i)) {
                 if (a == aP && i == pend) {
                     s_pz[tid] = zmax;
@@ -1030,7 +1041,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
                 zmax = 0;
                 continue;
             }
-            zmax = max(zmax, zigzag32((int64_t)(Ki - ka) - line_at(M, i - a)));
+            zmax = max(zmax, zigzag32(diff(Ki, ka) - line_at(M, i - a)));
         }
         if (aP != kNone && !word) {
             s_pz[tid] = zmax;
@@ -1041,7 +1052,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
         if (tail) {
             for (uint32_t u = tid + 1; u < min(tid + 4u, nw) && s_pa[u] == a_last; ++u) zmax = max(zmax, s_pz[u]);
             for (uint32_t i = max(w1, wend); i < e_last; ++i)
-                zmax = max(zmax, zigzag32((int64_t)(st(i) - ka) - line_at(M, i - a)));
+                zmax = max(zmax, zigzag32(diff(key(i), ka) - line_at(M, i - a)));
             width[j] = (uint8_t)(32u - __clz(zmax));
         }
     }
@@ -1050,7 +1061,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     if (word && e_last == kNone) {
         // the segment at a_last is longer than 96 keys: its slope came from the chain's walk
         const uint32_t a = a_last;
-        icpt[j] = (KT)st(a);
+        icpt[j] = __ldg(K + a);
         start[j] = (uint16_t)a;
         const LongInfo li = longinfo[cd.bitword_begin + (a >> 5)];
         slope[j] = 0;
@@ -1438,7 +1449,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
     }
     {
         static DeviceOnce once_s;
-        const size_t smem = sizeof(KT) * kShortSlots;
+        const size_t smem = sizeof(uint32_t) * kShortSlots;
         if (int rc = smem_attr_once(once_s, fit_short_kernel<KT>, smem)) return rc;
         KTime kt("model_short", st);
         fit_short_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, smem, st>>>(
