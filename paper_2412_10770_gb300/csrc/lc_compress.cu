@@ -1666,6 +1666,14 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
         rc = run_pipeline<uint64_t>((const uint64_t*)keys_dev, chunks_d, C, fs, tbits, counts, csb_tmp, status, tmp,
                                     tmp_bytes, col, st, 1);
     if (rc) return fail(rc);
+    // the derived directories' memory, taken while stage 1 runs: a large
+    // stream-ordered allocation costs the host a few hundred microseconds,
+    // which would otherwise leave the device idle (build_derived allocates it
+    // if this did not)
+    if (!col->derived2 &&
+        cudaMallocAsync((void**)&col->derived2, derived2_layout(col->N, L, col->list_mode != 0).bytes, st) !=
+            cudaSuccess)
+        col->derived2 = nullptr;
     rc = stage_d2h(col->blob + lay.cwb + 8 * C, 8, st, &p_total);
     if (rc) return fail(rc);
     rc = stage_d2h(status, 4, st, &p_status);

@@ -185,7 +185,14 @@ int derived_replay(lc_column* col, const uint32_t* gate, void* tmp, size_t tmp_b
 // Upload the host-built prefix of the blob and zero its padding bytes.
 int finish_blob(lc_column* col, const uint8_t* prefix_h, uint64_t prefix_len, cudaStream_t st);
 
-// Derived directories and the kernel view (lc_query.cu).
+// Derived directories and the kernel view (lc_query.cu).  build_derived
+// takes col->derived2 as it finds it when it is set (derived2_layout(N, L,
+// list_mode).bytes of device memory), else allocates it.
+struct Derived2Layout {
+    uint64_t B;  // radix buckets (0 in list mode)
+    size_t off_rank, off_rdx, off_ioff, bytes;
+};
+Derived2Layout derived2_layout(uint64_t N, uint64_t L, bool list_mode);
 int build_derived(lc_column* col, cudaStream_t st);
 
 int decode_range(const lc_column* col, uint64_t begin, uint64_t count, void* out, cudaStream_t st);

@@ -1319,6 +1319,20 @@ __global__ void __launch_bounds__(kPartThreads, 4) part_gather_kernel(const uint
 
 }  // namespace
 
+Derived2Layout derived2_layout(uint64_t N, uint64_t L, bool list_mode) {
+    Derived2Layout d;
+    // (lower_bound needs sorted keys: no table in list mode)
+    uint32_t blog = 0;  // B = 2^blog buckets, about two per segment, at most 2^kRdxMaxLog
+    while (blog < kRdxMaxLog && (1ull << blog) < 2 * L) ++blog;
+    d.B = list_mode ? 0 : 1ull << blog;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    d.off_rank = al(sizeof(SegRec) * L);
+    d.off_rdx = al(d.off_rank + sizeof(RankWord) * ((N + 63) / 64));
+    d.off_ioff = al(d.off_rdx + (d.B ? 8 * (d.B + 1) : 0));
+    d.bytes = al(d.off_ioff + (d.B ? 4 * L : 0)) + 256;
+    return d;
+}
+
 int build_derived(lc_column* col, cudaStream_t st) {
     const uint64_t C = col->C, L = col->L, N = col->N;
     // the segment records hold key indices in 56 bits and payload bits in 48
@@ -1344,18 +1358,14 @@ int build_derived(lc_column* col, cudaStream_t st) {
     rc = cuda_status(cudaMemsetAsync(col->status, 0, 4, st));
     if (rc) return rc;
 
-    // segment records, rank words, the radix table over the intercepts
+    // segment records, rank words, the radix table over the intercepts (the
+    // memory may have been taken while the compress's last stage ran)
     const uint64_t nw = (N + 63) / 64;
-    // (lower_bound needs sorted keys: no table in list mode)
-    uint32_t blog = 0;  // B = 2^blog buckets, about two per segment, at most 2^kRdxMaxLog
-    while (blog < kRdxMaxLog && (1ull << blog) < 2 * L) ++blog;
-    const uint64_t B = col->list_mode ? 0 : 1ull << blog;
+    const Derived2Layout dl = derived2_layout(N, L, col->list_mode != 0);
+    const uint64_t B = dl.B;
+    const size_t off_rank = dl.off_rank, off_rdx = dl.off_rdx, off_ioff = dl.off_ioff;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t off_rank = al(sizeof(SegRec) * L);
-    const size_t off_rdx = al(off_rank + sizeof(RankWord) * nw);
-    const size_t off_ioff = al(off_rdx + (B ? 8 * (B + 1) : 0));
-    const size_t bytes2 = al(off_ioff + (B ? 4 * L : 0)) + 256;
-    if (cudaMallocAsync((void**)&col->derived2, bytes2, st) != cudaSuccess) {
+    if (!col->derived2 && cudaMallocAsync((void**)&col->derived2, dl.bytes, st) != cudaSuccess) {
         col->derived2 = nullptr;
         return LC_ERR_NOMEM;
     }
