@@ -1039,17 +1039,16 @@ int set_smem() {
 // L2-resident slice of the column, so each of its lines comes from DRAM about
 // once.  The results are the same function of each query; only the order of
 // work changes.  The batch is cut into tiles of kPartTile queries, one CTA
-// each, and the queries of bucket b from tile c go to slot base[b * T + c]
-// onwards (bucket-major, so the buckets lie in order).  Launches:
-//   part_count    per tile, the count of each bucket
-//   scan          the bucket-major offsets base[]
+// each.  Launches:
 //   part_scatter  per tile, a counting sort in shared memory: the tile's
-//                 queries in bucket order, each bucket's run written to its
-//                 slot range as one coalesced piece, and for each query its
-//                 position in the sorted tile (16 bits)
-//   part_lookup   the queries in bucket order, results over them in place
-//   part_gather   per tile, each bucket's run of results read back as one
-//                 piece into shared memory, then out[q] in query order
+//                 queries in bucket order, written back as one piece at the
+//                 tile's place; the start of each bucket's run in the tile;
+//                 for each query its position in the sorted tile (16 bits)
+//   part_lookup   the runs in bucket-major order (bucket b of every tile,
+//                 then bucket b + 1), a warp per run, results written over
+//                 the queries
+//   part_gather   per tile, its results read back as one piece into shared
+//                 memory, then out[q] in query order
 // Buckets: key index >> shift for access; for lower_bound the count of
 // splitters below the value, the splitters being the keys at multiples of N/B
 // (equal key counts per bucket, whatever the value distribution).
@@ -1139,46 +1138,17 @@ __global__ void part_split_kernel(ColView v, uint32_t B, uint64_t* __restrict__ 
 }
 
 template <bool BY_VALUE, typename QT>
-__global__ void __launch_bounds__(kPartThreads) part_count_kernel(const QT* __restrict__ keys, uint64_t m, PartPlan pp,
-                                                                  uint32_t* __restrict__ cnt) {
-    __shared__ uint32_t s_cnt[kPartMaxBuckets];
-    __shared__ uint64_t s_split[BY_VALUE ? kPartMaxBuckets : 1];
-    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) s_cnt[b] = 0;
-    part_load_split<BY_VALUE>(pp, s_split);
-    __syncthreads();
-    const uint64_t pol = policy_stream();
-    const uint64_t c = blockIdx.x, q0 = c * kPartTile;
-    const uint32_t nt = (uint32_t)min((uint64_t)kPartTile, m - q0);
-    uint64_t kk[kPartPer];
-#pragma unroll
-    for (uint32_t u = 0; u < kPartPer; ++u) {
-        const uint32_t j = u * kPartThreads + threadIdx.x;
-        kk[u] = j < nt ? ld_stream(keys + q0 + j, pol) : 0;
-    }
-#pragma unroll
-    for (uint32_t u = 0; u < kPartPer; ++u)
-        if (u * kPartThreads + threadIdx.x < nt) atomicAdd(&s_cnt[part_bucket<BY_VALUE>(kk[u], pp, s_split)], 1u);
-    __syncthreads();
-    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) cnt[(uint64_t)b * pp.T + c] = s_cnt[b];
-}
-
-template <bool BY_VALUE, typename QT>
 __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const QT* __restrict__ keys, uint64_t m, PartPlan pp,
-                                                                    const uint64_t* __restrict__ base,
                                                                     uint64_t* __restrict__ bkey,
+                                                                    uint16_t* __restrict__ runs,
                                                                     uint16_t* __restrict__ pos) {
     __shared__ uint64_t s_key[kPartTile];  // the tile's queries in bucket order
-    __shared__ uint8_t s_bkt[kPartTile];   // and the bucket of each
     __shared__ uint32_t s_cnt[kPartMaxBuckets];
-    __shared__ uint64_t s_gb[kPartMaxBuckets];
     __shared__ uint64_t s_split[BY_VALUE ? kPartMaxBuckets : 1];
     __shared__ uint32_t s_warp[kPartThreads / 32];
     const uint64_t c = blockIdx.x, q0 = c * kPartTile;
     const uint32_t nt = (uint32_t)min((uint64_t)kPartTile, m - q0);
-    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) {
-        s_cnt[b] = 0;
-        s_gb[b] = base[(uint64_t)b * pp.T + c];
-    }
+    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) s_cnt[b] = 0;
     part_load_split<BY_VALUE>(pp, s_split);
     __syncthreads();
     const uint64_t pol = policy_stream();
@@ -1202,17 +1172,15 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const QT* __
     for (uint32_t u = 0; u < kPartPer; ++u) {
         const uint32_t j = u * kPartThreads + threadIdx.x;
         if (j < nt) {
-            const uint32_t b = code[u] >> 16, at = s_cnt[b] + (code[u] & 0xffffu);
+            const uint32_t at = s_cnt[code[u] >> 16] + (code[u] & 0xffffu);
             s_key[at] = kk[u];
-            s_bkt[at] = (uint8_t)b;
             st16_hint(pos + q0 + j, (uint16_t)at, pol);
         }
     }
+    uint16_t* rc = runs + c * (pp.B + 1);
+    for (uint32_t b = threadIdx.x; b <= pp.B; b += blockDim.x) rc[b] = (uint16_t)(b < pp.B ? s_cnt[b] : nt);
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < nt; j += kPartThreads) {
-        const uint32_t b = s_bkt[j];
-        bkey[s_gb[b] + (j - s_cnt[b])] = s_key[j];
-    }
+    for (uint32_t j = threadIdx.x; j < nt; j += kPartThreads) bkey[q0 + j] = s_key[j];
 }
 
 // The first index in [ks + 1, ks + n] whose decoded key is >= x, given that
@@ -1235,79 +1203,74 @@ __device__ __forceinline__ uint64_t lower_bound_decoded(const ColView& v, const 
     return ks + a;
 }
 
-// The queries in bucket order; bkey[e] becomes the result of query bkey[e].
-// The column's lines are read with the normal L2 priority: a bucket's slice
-// is reused by its queries, the query stream is not.  DENSE: D holds every
-// key decoded; access reads its key there, lower_bound searches there inside
-// the segment the directories give.
+// The runs in bucket-major order (bucket b of every tile, then bucket b + 1),
+// a warp per run, grid-stride over the runs: the runs in flight at once are
+// consecutive, so they keep to one bucket or two (two queries per lane, or
+// four runs per warp, measured slower), and the next run's bounds are loaded
+// while this one's queries run.  The column's lines are read with the normal
+// L2 priority: a bucket's slice is reused by its queries, the query stream is
+// not.  DENSE: D holds every key decoded; access reads its key there,
+// lower_bound searches there inside the segment the directories give.
+template <bool BY_VALUE, bool DENSE, typename KT>
+__device__ __forceinline__ uint64_t part_answer(const ColView& v, const KT* __restrict__ D, uint64_t key,
+                                                uint64_t normal) {
+    if (BY_VALUE)
+        return DENSE ? lower_bound_decoded<KT>(v, D, key, normal) : lower_bound_one<KT>(v, key, normal, normal);
+    if (key < v.N)
+        return DENSE ? (sizeof(KT) == 8 ? ld64_hint(D + key, normal) : (uint64_t)ld32_hint(D + key, normal))
+                     : access_one(v, key, normal, normal);
+    atomicOr(v.status, kStOutOfRange);
+    return 0;
+}
+
 template <bool BY_VALUE, bool DENSE, typename KT>
 __global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, const KT* __restrict__ D,
-                                                             uint64_t* __restrict__ bkey, uint64_t m) {
+                                                             uint64_t* __restrict__ bkey,
+                                                             const uint16_t* __restrict__ runs, PartPlan pp) {
     const uint64_t normal = policy_normal(), stream = policy_stream();
-    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    uint64_t kn = e < m ? ld_rw_stream(bkey + e, stream) : 0;
-    for (; e < m; e += step) {
-        const uint64_t key = kn;
-        if (e + step < m) kn = ld_rw_stream(bkey + e + step, stream);
-        uint64_t r;
-        if (BY_VALUE) {
-            r = DENSE ? lower_bound_decoded<KT>(v, D, key, normal) : lower_bound_one<KT>(v, key, normal, normal);
-        } else if (key < v.N) {
-            r = DENSE ? (sizeof(KT) == 8 ? ld64_hint(D + key, normal) : (uint64_t)ld32_hint(D + key, normal))
-                      : access_one(v, key, normal, normal);
-        } else {
-            atomicOr(v.status, kStOutOfRange);
-            r = 0;
-        }
-        st64_hint(bkey + e, r, stream);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t nruns = (uint64_t)pp.B * pp.T;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    // run r: bucket r / T of tile r % T; its queries' slots [c kPartTile + s, c kPartTile + e)
+    auto bounds = [&](uint64_t r, uint64_t& first, uint32_t& len) {
+        const uint64_t b = r / pp.T, c = r - b * pp.T;
+        const uint16_t* rc = runs + c * (pp.B + 1) + b;
+        const uint32_t s0 = __ldg(rc), e0 = __ldg(rc + 1);
+        first = c * kPartTile + s0;
+        len = e0 - s0;
+    };
+    uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    uint64_t nfirst = 0;
+    uint32_t nlen = 0;
+    if (r < nruns) bounds(r, nfirst, nlen);
+    for (; r < nruns; r += warps) {
+        const uint64_t first = nfirst;
+        const uint32_t len = nlen;
+        if (r + warps < nruns) bounds(r + warps, nfirst, nlen);
+        for (uint32_t k = lane; k < len; k += 32)
+            st64_hint(bkey + first + k,
+                      part_answer<BY_VALUE, DENSE, KT>(v, D, ld_rw_stream(bkey + first + k, stream), normal), stream);
     }
 }
 
 template <typename OT>
-__global__ void __launch_bounds__(kPartThreads, 4) part_gather_kernel(const uint64_t* __restrict__ res,
+__global__ void __launch_bounds__(kPartThreads) part_gather_kernel(const uint64_t* __restrict__ res,
                                                                    const uint16_t* __restrict__ pos, uint64_t m,
-                                                                   PartPlan pp, const uint32_t* __restrict__ cnt,
-                                                                   const uint64_t* __restrict__ base,
                                                                    OT* __restrict__ out) {
     __shared__ uint64_t s_res[kPartTile];  // the tile's results in bucket order
-    __shared__ uint32_t s_lb[kPartMaxBuckets];
-    __shared__ uint64_t s_gb[kPartMaxBuckets];
-    __shared__ uint32_t s_warp[kPartThreads / 32];
     const uint64_t c = blockIdx.x, q0 = c * kPartTile;
     const uint32_t nt = (uint32_t)min((uint64_t)kPartTile, m - q0);
-    for (uint32_t b = threadIdx.x; b < pp.B; b += blockDim.x) {
-        s_lb[b] = cnt[(uint64_t)b * pp.T + c];
-        s_gb[b] = base[(uint64_t)b * pp.T + c];
-    }
-    __syncthreads();
-    tile_scan(s_lb, pp.B, s_warp);
-    const uint64_t normal = policy_normal(), stream = policy_stream();
+    const uint64_t stream = policy_stream();
     uint32_t pq[kPartPer];  // each query's position in the sorted tile, loaded early
 #pragma unroll
     for (uint32_t u = 0; u < kPartPer; ++u) {
         const uint32_t j = u * kPartThreads + threadIdx.x;
         pq[u] = j < nt ? (uint32_t)ld_stream(pos + q0 + j, stream) : 0u;
     }
-    uint64_t rr[kPartPer];
 #pragma unroll
     for (uint32_t u = 0; u < kPartPer; ++u) {
         const uint32_t j = u * kPartThreads + threadIdx.x;
-        rr[u] = 0;
-        if (j < nt) {
-            uint32_t lo = 0, hi = pp.B - 1;  // the last bucket whose run starts at or before j
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi + 1) >> 1;
-                if (s_lb[mid] <= j) lo = mid;
-                else hi = mid - 1;
-            }
-            rr[u] = ld64_hint(res + s_gb[lo] + (j - s_lb[lo]), normal);
-        }
-    }
-#pragma unroll
-    for (uint32_t u = 0; u < kPartPer; ++u) {
-        const uint32_t j = u * kPartThreads + threadIdx.x;
-        if (j < nt) s_res[j] = rr[u];
+        if (j < nt) s_res[j] = ld_stream(res + q0 + j, stream);
     }
     __syncthreads();
 #pragma unroll
@@ -1691,22 +1654,19 @@ bool part_plan(const lc_column* col, uint64_t m, bool by_value, PartPlan* pp) {
 
 // A partitioned batch: keys are the m indices (access) or values
 // (lower_bound), out the m results.  Scratch from the stream-ordered pool,
-// released in stream order: 10 bytes per query plus 12 per bucket and tile,
+// released in stream order: 10 bytes per query plus 2 per bucket and tile,
 // and the decoded column when the plan is dense.
 template <bool BY_VALUE, typename KT, typename QT, typename OT>
 int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan pp, OT* out, cudaStream_t st) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const uint64_t n = (uint64_t)pp.B * pp.T;
-    const size_t tmp_b = scan_tmp_bytes(n);
-    const size_t o_pos = al(8 * m), o_cnt = o_pos + al(2 * m), o_base = o_cnt + al(4 * n);
-    const size_t o_tmp = o_base + al(8 * (n + 1)), o_split = o_tmp + al(tmp_b), o_dec = o_split + al(8 * pp.B);
+    const size_t o_pos = al(8 * m), o_runs = o_pos + al(2 * m), o_split = o_runs + al(2 * pp.T * (pp.B + 1));
+    const size_t o_dec = o_split + al(8 * pp.B);
     const size_t total = o_dec + (pp.dense ? al(sizeof(KT) * col->N) : 0);
     uint8_t* p = nullptr;
     if (cudaMallocAsync((void**)&p, total, st) != cudaSuccess) return LC_ERR_NOMEM;
     uint64_t* bkey = (uint64_t*)p;
     uint16_t* pos = (uint16_t*)(p + o_pos);
-    uint32_t* cnt = (uint32_t*)(p + o_cnt);
-    uint64_t* base = (uint64_t*)(p + o_base);
+    uint16_t* runs = (uint16_t*)(p + o_runs);
     uint64_t* split = (uint64_t*)(p + o_split);
     KT* dec = pp.dense ? (KT*)(p + o_dec) : nullptr;
     int rc = LC_OK;
@@ -1722,15 +1682,8 @@ int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan p
         }
     }
     if (!rc) {
-        KTime kt(BY_VALUE ? "lower_bound.count" : "access.count", st);
-        part_count_kernel<BY_VALUE, QT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(keys, m, pp, cnt);
-        note_launch();
-        rc = cuda_status(cudaGetLastError());
-    }
-    if (!rc) rc = scan_exclusive(cnt, base, n, ScanOp::Identity, p + o_tmp, tmp_b, st);
-    if (!rc) {
         KTime kt(BY_VALUE ? "lower_bound.scatter" : "access.scatter", st);
-        part_scatter_kernel<BY_VALUE, QT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(keys, m, pp, base, bkey, pos);
+        part_scatter_kernel<BY_VALUE, QT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(keys, m, pp, bkey, runs, pos);
         note_launch();
         rc = cuda_status(cudaGetLastError());
     }
@@ -1738,15 +1691,16 @@ int run_partitioned(const lc_column* col, const QT* keys, uint64_t m, PartPlan p
         auto kern = pp.dense ? part_lookup_kernel<BY_VALUE, true, KT> : part_lookup_kernel<BY_VALUE, false, KT>;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1) occ = 1;
-        const unsigned grid = (unsigned)std::min<uint64_t>((m + 255) / 256, (uint64_t)sm_count() * occ);
+        const uint64_t nruns = (uint64_t)pp.B * pp.T;  // a warp per run
+        const unsigned grid = (unsigned)std::min<uint64_t>((nruns + 7) / 8, (uint64_t)sm_count() * occ);
         KTime kt(BY_VALUE ? "lower_bound.lookup" : "access.lookup", st);
-        kern<<<grid, 256, 0, st>>>(col->view, dec, bkey, m);
+        kern<<<grid, 256, 0, st>>>(col->view, dec, bkey, runs, pp);
         note_launch();
         rc = cuda_status(cudaGetLastError());
     }
     if (!rc) {
         KTime kt(BY_VALUE ? "lower_bound.gather" : "access.gather", st);
-        part_gather_kernel<OT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(bkey, pos, m, pp, cnt, base, out);
+        part_gather_kernel<OT><<<(unsigned)pp.T, kPartThreads, 0, st>>>(bkey, pos, m, out);
         note_launch();
         rc = cuda_status(cudaGetLastError());
     }
