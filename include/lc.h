@@ -232,8 +232,9 @@ int lc_access(const lc_column* col, const uint64_t* idx_dev, uint64_t m, void* o
  *     the value against the keys at multiples of N/B), each bucket's slice of
  *     the directories and payload being about 16 MB; the buckets then run in
  *     order, so that their slices are read from L2, and the results are
- *     scattered back to query order.  Five streaming launches and 10 bytes
- *     per query of stream-ordered scratch (LC_ERR_NOMEM if the pool has none).
+ *     returned to query order.  Three launches (a per-tile counting sort, the
+ *     lookups bucket by bucket, the gather) and 10 bytes per query of
+ *     stream-ordered scratch (LC_ERR_NOMEM if the pool has none).
  *   LC_QUERIES_DECODED: the column is first decoded whole (one bulk decode
  *     into N keys of stream-ordered scratch), then the queries run
  *     partitioned against the decoded keys: an access reads its key there, a
