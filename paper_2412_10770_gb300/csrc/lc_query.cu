@@ -597,13 +597,23 @@ __device__ __forceinline__ uint64_t lower_bound_in_segment(const ColView& v, uin
     const uint64_t ks = r.kstart_w & kKeyMask;
     const uint32_t n = (uint32_t)(r.bit1_n >> 48) + 1u;
     uint32_t a = 1, b = n;  // first t in [1, n) with key(t) >= x, or n
-    if (n >= 32 && r.slope > 0) {
+    // The bracket is taken for short segments too: it usually leaves a few
+    // indices, whose residuals then fit the register window below.  Single
+    // precision with the fast reciprocal errs by about 2^-20 relative (four
+    // conversions, two sums, the 2-ulp reciprocal, two products), under 0.1
+    // index for t < 2^16: inside the bracket's 2-index margin.
+    if (n > 2 && r.slope > 0) {
         const uint32_t w = (uint32_t)(r.kstart_w >> 56);
-        const float s = (float)r.slope * 2.3283064365386963e-10f;  // keys per index
-        const float th = (float)(x - r.icpt) / s;
+        // 64-bit integers go to float as two 32-bit halves: a 64-bit
+        // conversion would take the slow double-precision pipe
+        const uint64_t dx = x - r.icpt;
+        const float s = (float)(uint32_t)((uint64_t)r.slope >> 32) +
+                        (float)(uint32_t)r.slope * 2.3283064365386963e-10f;  // keys per index
+        const float rs = __fdividef(1.0f, s);
+        const float th = ((float)(uint32_t)(dx >> 32) * 4294967296.0f + (float)(uint32_t)dx) * rs;
         // |residual| <= 2^(w-1) for a w-bit zigzag code (w = 32 is legal: eps up to 2^30)
-        const float half = w ? (float)(1ull << (w - 1)) : 0.0f;
-        const float dl = (half + 1.0f) / s + 2.0f;
+        const float half = w ? (float)(1u << (w - 1)) : 0.0f;
+        const float dl = (half + 1.0f) * rs + 2.0f;
         const float fa = th - dl, fb = th + dl + 1.0f;
         a = fa <= 1.0f ? 1u : (fa >= (float)n ? n : (uint32_t)fa);
         b = fb <= 1.0f ? 1u : (fb >= (float)n ? n : (uint32_t)fb);
@@ -1240,6 +1250,40 @@ __global__ void __launch_bounds__(256, 6) part_lookup_kernel(ColView v, const KT
         len = e0 - s0;
     };
     uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    if constexpr (DENSE && !BY_VALUE) {
+        // One load per answer: the first 64 queries of the next run, and the
+        // bounds of the one after, are loaded while this run's keys are read,
+        // so that a run costs about one memory latency rather than two per
+        // 32 queries.  A run's stores and the next run's loads touch disjoint
+        // slots.
+        if (r >= nruns) return;
+        uint64_t f0, f1 = 0;
+        uint32_t l0, l1 = 0;
+        bounds(r, f0, l0);
+        uint64_t qa = lane < l0 ? ld_rw_stream(bkey + f0 + lane, stream) : 0;
+        uint64_t qb = lane + 32 < l0 ? ld_rw_stream(bkey + f0 + lane + 32, stream) : 0;
+        if (r + warps < nruns) bounds(r + warps, f1, l1);
+        for (;;) {
+            const uint64_t ra = lane < l0 ? part_answer<false, true, KT>(v, D, qa, normal) : 0;
+            const uint64_t rb = lane + 32 < l0 ? part_answer<false, true, KT>(v, D, qb, normal) : 0;
+            const bool more = r + warps < nruns;
+            uint64_t na = 0, nb = 0, f2 = 0;
+            uint32_t l2 = 0;
+            if (more) {
+                na = lane < l1 ? ld_rw_stream(bkey + f1 + lane, stream) : 0;
+                nb = lane + 32 < l1 ? ld_rw_stream(bkey + f1 + lane + 32, stream) : 0;
+                if (r + 2 * warps < nruns) bounds(r + 2 * warps, f2, l2);
+            }
+            for (uint32_t k = 64 + lane; k < l0; k += 32)  // the rest of a long run
+                st64_hint(bkey + f0 + k, part_answer<false, true, KT>(v, D, ld_rw_stream(bkey + f0 + k, stream), normal),
+                          stream);
+            if (lane < l0) st64_hint(bkey + f0 + lane, ra, stream);
+            if (lane + 32 < l0) st64_hint(bkey + f0 + lane + 32, rb, stream);
+            if (!more) return;
+            r += warps;
+            f0 = f1, l0 = l1, qa = na, qb = nb, f1 = f2, l1 = l2;
+        }
+    }
     uint64_t nfirst = 0;
     uint32_t nlen = 0;
     if (r < nruns) bounds(r, nfirst, nlen);
