@@ -3,7 +3,7 @@
 // arithmetic so that the bytes equal those of the CPU definition.
 //
 // Pipeline for C chunks (each chunk is independent: segments never cross one):
-//   spec_kernel   one CTA per 8192-key window, keys staged in shared memory;
+//   spec_kernel   one CTA per window (4096 keys, 2048 for short lists), keys in shared memory;
 //                 one thread per 64-key span runs the greedy from 96 keys
 //                 before its span (a warm-up that almost always brings it onto
 //                 the true chain) and records its anchors, entry and exit per
@@ -15,7 +15,7 @@
 //                 per key, the segment count per chunk, and the slope of every
 //                 segment longer than 96 keys (its walk ends with the cone).
 //   scan          chunk_seg_begin.
-//   fit_short_kernel  one CTA per 8192-key window, one thread per 32-key
+//   fit_short_kernel  one CTA per window, one thread per 32-key
 //                 block, split by keys: the cone, slope and width of every
 //                 segment of at most 96 keys that starts in the block, with
 //                 the keys of later blocks merged as partial cones through
@@ -256,14 +256,26 @@ __device__ __forceinline__ uint32_t warp_walk(const KT* __restrict__ K, uint32_t
 // ------------------------------------------------------------------ fit: speculation with a warm-up walk
 
 constexpr uint32_t kFB = 32;                    // keys per fit block: one 32-bit word of anchor bits
-constexpr uint32_t kWinKeys = 8192;             // keys per window, one CTA
 constexpr uint32_t kWarm = 96;                  // keys a speculative walk runs before its span
-constexpr uint32_t kSpecKeys = kWarm + kWinKeys + 96;  // a walk ends at most 96 keys past its span
-constexpr uint32_t kSpecSlots = kSpecKeys + kSpecKeys / 32 + 1;  // the densest padding (one per 32 keys)
-constexpr int kShortThreads = kWinKeys / kFB;   // 256: one thread per block in fit_short_kernel
 constexpr int kChainThreads = 128;              // four chunks per CTA, one warp each
 constexpr uint32_t kShortMax = 96;              // segments of at most this many keys: one thread fits each
 static_assert(kShortMax == 96, "the speculative walks and fit_short_kernel's anchor search assume 96");
+
+// Keys per window (one CTA of spec_kernel, fit_short_kernel and reach_kernel).
+// A window never spans two chunks, so chunks shorter than a window leave its
+// threads idle: columns of short lists take 2048-key windows (at the default
+// span, 32 speculating threads), long chunks 4096 (more CTAs per chunk than
+// 8192 without more warm-up per key; both measured faster than 8192).
+constexpr uint32_t kWinWide = 4096, kWinNarrow = 2048;
+template <uint32_t WK>
+struct Win {
+    static constexpr uint32_t kSpecKeys = kWarm + WK + 96;  // a walk ends at most 96 keys past its span
+    static constexpr uint32_t kSpecSlots = kSpecKeys + kSpecKeys / 32 + 1;  // the densest padding (one per 32 keys)
+    static constexpr int kShortThreads = WK / kFB;         // one thread per 32-key block in fit_short_kernel
+    static constexpr uint32_t kLongPerWin = WK / (kShortMax + 1) + 1;  // segments > 96 keys starting in a window
+    static constexpr uint32_t kShortSlots = (WK + kShortMax) + (WK + kShortMax) / 32 + 1;
+    static_assert(kShortThreads % 32 == 0, "whole warps");
+};
 constexpr uint32_t kPiece = 2048;               // keys per work item of a long segment's width pass
 
 // A segment longer than kShortMax keys, as its walk in the chain found it.
@@ -288,7 +300,6 @@ struct WinLong {
     int64_t M;
     uint32_t a, len, poff, pad;
 };
-constexpr uint32_t kLongPerWin = kWinKeys / (kShortMax + 1) + 1;  // segments > 96 keys starting in 8192 keys
 // Keys key0 + [t0, t1) of long segment `item`.
 struct Piece {
     uint32_t item;
@@ -422,7 +433,7 @@ struct GlobalKeys {
     __device__ __forceinline__ uint64_t operator()(uint32_t i) const { return (uint64_t)__ldg(K + i); }
 };
 
-// One CTA per window of 8192 keys of one chunk; keys [w0 - kWarm, w1 + 96)
+// One CTA per window of WK keys of one chunk; keys [w0 - kWarm, w1 + 96)
 // staged in shared memory as 32-bit offsets from the first staged key.
 // Thread t owns the span of blocks kB t .. kB t + kB - 1 (32 kB keys) and runs
 // the greedy from kWarm keys before the span (from the chunk start if that is
@@ -434,21 +445,23 @@ struct GlobalKeys {
 // its first anchor at or after the block's start (entry) and after its end
 // (exit); kNone if the walk stopped inside a segment of more than kShortMax
 // keys before reaching it, the chunk's length if the chunk ends first.  Also
-// checks sortedness.  kB (1, 2 or 4 blocks per thread: 256, 128 or 64 threads
-// per window) trades parallelism against the warm-up walked per key.
-template <typename KT, int kB>
-__global__ void __launch_bounds__(kWinKeys / (32 * kB))
+// checks sortedness.  kB (1, 2 or 4 blocks per thread: WK / 32, WK / 64 or
+// WK / 128 threads per window of WK keys) trades parallelism against the
+// warm-up walked per key.
+template <typename KT, int kB, uint32_t WK>
+__global__ void __launch_bounds__(WK / (32 * kB))
 spec_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
             uint32_t* __restrict__ spec_g, uint32_t* __restrict__ entry_g, uint32_t* __restrict__ exit_g,
             uint32_t* __restrict__ status) {
     constexpr uint32_t kSpanB = 32u * kB;
-    constexpr int kThreads = kWinKeys / kSpanB;
+    constexpr int kThreads = WK / kSpanB;
+    static_assert(kThreads % 32 == 0, "whole warps");
     constexpr int kShift = kB == 1 ? 5 : (kB == 2 ? 6 : 7);
     extern __shared__ __align__(16) uint8_t smem[];
     const WinDesc wd = wins[blockIdx.x];
     const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
-    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
+    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + WK);
     const int64_t eps = cd.eps;
     const uint32_t tid = threadIdx.x;
     const uint32_t base = w0 >= kWarm ? w0 - kWarm : 0;
@@ -591,30 +604,31 @@ chain_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, 
 // segment is walked as by the greedy, and a chunk keeps the jump segmentation
 // only if it has fewer segments than the greedy's.
 
-// reach_kernel: one CTA per 8192-key window, keys [w0, w1 + 96] staged as
+// reach_kernel: one CTA per window of WK keys, keys [w0, w1 + 96] staged as
 // 32-bit offsets; r_off[p] = r(p) - p in 1..96, or 0 when the greedy segment
 // from p is longer than 96 keys.  One thread per position.
-template <typename KT>
-__global__ void __launch_bounds__(kShortThreads)
+template <typename KT, uint32_t WK>
+__global__ void __launch_bounds__(Win<WK>::kShortThreads)
 reach_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
              uint8_t* __restrict__ roff) {
+    constexpr int kThr = Win<WK>::kShortThreads;
     extern __shared__ __align__(16) uint8_t smem[];
     const WinDesc wd = wins[blockIdx.x];
     const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
-    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
+    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + WK);
     const int64_t eps = cd.eps;
     const uint32_t top = min(n, w1 + kShortMax + 1);
     uint32_t* s = (uint32_t*)smem;
     const uint64_t kbase = (uint64_t)__ldg(K + w0);
 #pragma unroll 4
-    for (uint32_t q = threadIdx.x; q < top - w0; q += kShortThreads)
+    for (uint32_t q = threadIdx.x; q < top - w0; q += kThr)
         s[q + (q >> 5)] = (uint32_t)((uint64_t)__ldg(K + w0 + q) - kbase);
     __syncthreads();
     const Staged<uint32_t> st{s, w0};
-    const uint32_t iters = (w1 - w0 + kShortThreads - 1) / kShortThreads;  // the same for every thread
+    const uint32_t iters = (w1 - w0 + kThr - 1) / kThr;  // the same for every thread
     for (uint32_t it = 0; it < iters; ++it) {
-        const uint32_t p = w0 + threadIdx.x + it * kShortThreads;
+        const uint32_t p = w0 + threadIdx.x + it * kThr;
         const bool active = p < w1;
         const uint32_t lim = active ? min(n, p + kShortMax + 1) : p + 1;
         const uint64_t span = active ? (uint64_t)__ldg(K + lim - 1) - (uint64_t)__ldg(K + p) : 0;
@@ -780,15 +794,15 @@ struct MaxOp {
 // the floor midpoint of the resulting integer interval, and the width is the
 // bit length of the largest zigzag residual under that slope (Sec. II-A).
 //
-// fit_short_kernel: one CTA per 8192-key window, keys staged in shared memory
+// fit_short_kernel: one CTA per window of WK keys, keys staged in shared memory
 // (plus kShortMax keys of right halo), one thread per 32-key block: the
 // thread fits every segment that starts in its block and has at most
 // kShortMax keys, two short sequential passes (cone, then residuals), and
 // writes its intercept, start, slope and width.  A longer segment takes the
 // slope its chain walk recorded; its widths pass is queued as pieces of
 // kPiece keys (long_width_kernel) and its entry is finished by bitoff_kernel.
-template <typename KT>
-__global__ void __launch_bounds__(kShortThreads)
+template <typename KT, uint32_t WK>
+__global__ void __launch_bounds__(Win<WK>::kShortThreads)
 fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chunks, const WinDesc* __restrict__ wins,
                  const uint32_t* __restrict__ tbits, const uint64_t* __restrict__ csb,
                  const LongInfo* __restrict__ longinfo, KT* __restrict__ icpt, int64_t* __restrict__ slope,
@@ -797,8 +811,10 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
                  Piece* __restrict__ pieces, uint32_t* __restrict__ npieces, uint32_t pieces_cap,
                  ulonglong2* __restrict__ cones, uint32_t* __restrict__ status, const uint32_t* __restrict__ gate) {
     if (gate && *gate == 0) return;  // a batch replay that does not fit its plan
+    constexpr int kShortThreads = Win<WK>::kShortThreads;
+    constexpr uint32_t kLongPerWin = Win<WK>::kLongPerWin;
     extern __shared__ __align__(16) uint8_t smem[];
-    constexpr uint32_t kWords = kWinKeys / kFB;
+    constexpr uint32_t kWords = WK / kFB;
     __shared__ uint32_t s_T[kWords + 4];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_base, s_nlong, s_item0, s_piece0;
@@ -814,7 +830,7 @@ fit_short_kernel(const KT* __restrict__ keys, const ChunkDesc* __restrict__ chun
     const WinDesc wd = wins[blockIdx.x];
     const ChunkDesc cd = chunks[wd.chunk];
     const KT* __restrict__ K = keys + cd.key_begin;
-    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + kWinKeys);
+    const uint32_t n = cd.n, w0 = wd.off, w1 = min(n, w0 + WK);
     const int64_t eps = cd.eps;
     const uint32_t tid = threadIdx.x;
     const uint32_t top = min(n, w1 + kShortMax);
@@ -1376,6 +1392,7 @@ struct FitScratch {
     const WinDesc* wins;
     uint64_t nwins;
     uint32_t span_log2;  // keys per speculating thread: 2^5, 2^6 (default) or 2^7
+    uint32_t win_keys;   // keys per window: kWinWide or kWinNarrow
     uint32_t *spec, *entry, *exit;
     LongInfo* longinfo;
     LongItem* items;
@@ -1388,7 +1405,75 @@ struct FitScratch {
     uint32_t items_cap, pieces_cap;
 };
 
-constexpr uint32_t kShortSlots = (kWinKeys + kShortMax) + (kWinKeys + kShortMax) / 32 + 1;
+// The window size of a run: narrow windows for chunks of a few thousand keys
+// on average (columns of short lists), where a wide window would leave most
+// of its threads idle; wide ones otherwise, and always at a span of 128 keys
+// (a narrow window would then give the speculation a CTA of 16 threads).
+static uint32_t window_keys(uint64_t nkeys, uint64_t C, uint32_t span_log2) {
+    if (span_log2 == 7 || C == 0) return kWinWide;
+    return nkeys / C < 4 * (uint64_t)kWinWide ? kWinNarrow : kWinWide;
+}
+
+// The speculative walks (stage 0), the short models (stage 1) or the jump
+// fit's reach per key (stage 2) for one window size.
+template <typename KT, uint32_t WK>
+static int run_windows(const KT* keys, const ChunkDesc* chunks_d, const FitScratch& fs, uint32_t* tbits,
+                       uint32_t* status, uint8_t* blob, const Layout& lay, cudaStream_t st, int stage,
+                       const uint32_t* gate) {
+    using Wn = Win<WK>;
+    if (stage == 0) {
+        const size_t smem = sizeof(uint32_t) * Wn::kSpecSlots;
+        static DeviceOnce once1, once2, once4;
+        int rc = LC_OK;
+        KTime kt("fit_spec", st);
+        if (fs.span_log2 == 5) {
+            if (!(rc = smem_attr_once(once1, spec_kernel<KT, 1, WK>, smem)))
+                spec_kernel<KT, 1, WK><<<(unsigned)fs.nwins, WK / 32, smem, st>>>(keys, chunks_d, fs.wins, fs.spec,
+                                                                                  fs.entry, fs.exit, status);
+        } else if (fs.span_log2 == 7) {
+            if constexpr (WK / 128 >= 32) {
+                if (!(rc = smem_attr_once(once4, spec_kernel<KT, 4, WK>, smem)))
+                    spec_kernel<KT, 4, WK><<<(unsigned)fs.nwins, WK / 128, smem, st>>>(keys, chunks_d, fs.wins,
+                                                                                       fs.spec, fs.entry, fs.exit,
+                                                                                       status);
+            } else {
+                rc = LC_ERR_INTERNAL;  // window_keys never pairs this span with a narrow window
+            }
+        } else {
+            if (!(rc = smem_attr_once(once2, spec_kernel<KT, 2, WK>, smem)))
+                spec_kernel<KT, 2, WK><<<(unsigned)fs.nwins, WK / 64, smem, st>>>(keys, chunks_d, fs.wins, fs.spec,
+                                                                                  fs.entry, fs.exit, status);
+        }
+        return rc;
+    }
+    if (stage == 2) {
+        static DeviceOnce once_r;
+        const size_t rsm = sizeof(uint32_t) * Wn::kShortSlots;
+        if (int rc = smem_attr_once(once_r, reach_kernel<KT, WK>, rsm)) return rc;
+        KTime kt("jump_reach", st);
+        reach_kernel<KT, WK><<<(unsigned)fs.nwins, Wn::kShortThreads, rsm, st>>>(keys, chunks_d, fs.wins, fs.roff);
+        return LC_OK;
+    }
+    static DeviceOnce once_s;
+    const size_t smem = sizeof(uint32_t) * Wn::kShortSlots;
+    if (int rc = smem_attr_once(once_s, fit_short_kernel<KT, WK>, smem)) return rc;
+    KTime kt("model_short", st);
+    fit_short_kernel<KT, WK><<<(unsigned)fs.nwins, Wn::kShortThreads, smem, st>>>(
+        keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
+        (int64_t*)(blob + lay.slope), (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start),
+        (uint8_t*)(blob + lay.width), fs.items, fs.counters, fs.items_cap, fs.pieces, fs.counters + 1,
+        fs.pieces_cap, fs.cones, status, gate);
+    return LC_OK;
+}
+
+template <typename KT>
+static int run_windows(const KT* keys, const ChunkDesc* chunks_d, const FitScratch& fs, uint32_t* tbits,
+                       uint32_t* status, uint8_t* blob, const Layout& lay, cudaStream_t st, int stage,
+                       const uint32_t* gate) {
+    return fs.win_keys == kWinNarrow
+               ? run_windows<KT, kWinNarrow>(keys, chunks_d, fs, tbits, status, blob, lay, st, stage, gate)
+               : run_windows<KT, kWinWide>(keys, chunks_d, fs, tbits, status, blob, lay, st, stage, gate);
+}
 
 template <typename KT>
 static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, const FitScratch& fs, uint32_t* tbits,
@@ -1397,28 +1482,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
     uint8_t* blob = col->blob;
     const Layout& lay = col->lay;
     if (stage == 0) {
-        const size_t smem = sizeof(uint32_t) * kSpecSlots;
-        static DeviceOnce once1, once2, once4;
-        int rc = LC_OK;
-        {
-            KTime kt("fit_spec", st);
-            if (fs.span_log2 == 5) {
-                if (!(rc = smem_attr_once(once1, spec_kernel<KT, 1>, smem)))
-                    spec_kernel<KT, 1><<<(unsigned)fs.nwins, kWinKeys / 32, smem, st>>>(keys, chunks_d, fs.wins,
-                                                                                       fs.spec, fs.entry, fs.exit,
-                                                                                       status);
-            } else if (fs.span_log2 == 7) {
-                if (!(rc = smem_attr_once(once4, spec_kernel<KT, 4>, smem)))
-                    spec_kernel<KT, 4><<<(unsigned)fs.nwins, kWinKeys / 128, smem, st>>>(keys, chunks_d, fs.wins,
-                                                                                        fs.spec, fs.entry, fs.exit,
-                                                                                        status);
-            } else {
-                if (!(rc = smem_attr_once(once2, spec_kernel<KT, 2>, smem)))
-                    spec_kernel<KT, 2><<<(unsigned)fs.nwins, kWinKeys / 64, smem, st>>>(keys, chunks_d, fs.wins,
-                                                                                       fs.spec, fs.entry, fs.exit,
-                                                                                       status);
-            }
-        }
+        int rc = run_windows<KT>(keys, chunks_d, fs, tbits, status, blob, lay, st, 0, gate);
         if (rc) return rc;
         {
             KTime kt("fit_chain", st);
@@ -1429,13 +1493,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         if (fs.roff) {
-            static DeviceOnce once_r;
-            const size_t rsm = sizeof(uint32_t) * kShortSlots;
-            if ((rc = smem_attr_once(once_r, reach_kernel<KT>, rsm))) return rc;
-            {
-                KTime kt("jump_reach", st);
-                reach_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, rsm, st>>>(keys, chunks_d, fs.wins, fs.roff);
-            }
+            if ((rc = run_windows<KT>(keys, chunks_d, fs, tbits, status, blob, lay, st, 2, gate))) return rc;
             {
                 KTime kt("jump_chain", st);
                 jump_kernel<KT><<<(unsigned)((C + kChainThreads / 32 - 1) / (kChainThreads / 32)), kChainThreads, 0,
@@ -1447,17 +1505,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
         }
         return scan_exclusive(counts, csb, C, ScanOp::Identity, tmp, tmp_bytes, st);
     }
-    {
-        static DeviceOnce once_s;
-        const size_t smem = sizeof(uint32_t) * kShortSlots;
-        if (int rc = smem_attr_once(once_s, fit_short_kernel<KT>, smem)) return rc;
-        KTime kt("model_short", st);
-        fit_short_kernel<KT><<<(unsigned)fs.nwins, kShortThreads, smem, st>>>(
-            keys, chunks_d, fs.wins, tbits, (const uint64_t*)(blob + lay.csb), fs.longinfo, (KT*)(blob + lay.icpt),
-            (int64_t*)(blob + lay.slope), (uint32_t*)(blob + lay.bitoff), (uint16_t*)(blob + lay.start),
-            (uint8_t*)(blob + lay.width), fs.items, fs.counters, fs.items_cap, fs.pieces, fs.counters + 1,
-            fs.pieces_cap, fs.cones, status, gate);
-    }
+    if (int rc = run_windows<KT>(keys, chunks_d, fs, tbits, status, blob, lay, st, 1, gate)) return rc;
     {
         KTime kt("model_long", st);
         long_width_kernel<KT><<<(unsigned)(device_sms() * 8), 256, 0, st>>>(keys, fs.items, fs.pieces, fs.counters + 1,
@@ -1492,6 +1540,7 @@ static int run_pipeline(const KT* keys, const ChunkDesc* chunks_d, uint64_t C, c
 struct PipeScratch {
     std::vector<WinDesc> wins;
     uint64_t nwins = 0, C = 0, bitwords = 0, items_cap = 0, pieces_cap = 0;
+    uint32_t win_keys = kWinWide, span_log2 = 6;
     size_t off_chunks = 0, off_wins = 0, off_blk = 0, off_bits = 0, off_counts = 0, off_tmp = 0, off_status = 0,
            off_csb = 0, off_long = 0, off_items = 0, off_pieces = 0, off_counters = 0, bytes = 0, tmp_bytes = 0;
     ChunkDesc* chunks_d = nullptr;
@@ -1500,12 +1549,14 @@ struct PipeScratch {
     void* tmp = nullptr;
 
     // Windows and offsets for a chunk table; returns the bytes to allocate.
-    size_t plan(const ChunkDesc* chunks_h, uint64_t C_, uint64_t bitwords_) {
+    size_t plan(const ChunkDesc* chunks_h, uint64_t C_, uint64_t bitwords_, uint32_t span_log2_) {
         C = C_;
         bitwords = bitwords_;
+        span_log2 = span_log2_;
+        win_keys = window_keys(nkeys_total_of(chunks_h, C), C, span_log2);
         wins.clear();
         for (uint64_t c = 0; c < C; ++c)
-            for (uint32_t off = 0; off < chunks_h[c].n; off += kWinKeys) wins.push_back(WinDesc{(uint32_t)c, off});
+            for (uint32_t off = 0; off < chunks_h[c].n; off += win_keys) wins.push_back(WinDesc{(uint32_t)c, off});
         nwins = wins.size();
         tmp_bytes = scan_tmp_bytes(C);
         auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1552,7 +1603,8 @@ struct PipeScratch {
         fs.roff = nullptr;
         fs.jbits = nullptr;
         fs.jlong = nullptr;
-        fs.span_log2 = 6;
+        fs.span_log2 = span_log2;
+        fs.win_keys = win_keys;
         return fs;
     }
     // The per-run resets the pipeline expects (status, long-segment records, counters, pieces).
@@ -1571,9 +1623,9 @@ int compress_impl(const void* keys_dev, int kb, const ChunkDesc* chunks_h, uint6
     if (rc) return rc;
     PipeScratch ps;
     uint8_t* scratch = nullptr;
-    if (cudaMallocAsync((void**)&scratch, ps.plan(chunks_h, C, bitwords), st) != cudaSuccess) return LC_ERR_NOMEM;
+    if (cudaMallocAsync((void**)&scratch, ps.plan(chunks_h, C, bitwords, span_log2), st) != cudaSuccess)
+        return LC_ERR_NOMEM;
     FitScratch fs = ps.bind(scratch);
-    fs.span_log2 = span_log2;
     const std::vector<WinDesc>& wins = ps.wins;
     const uint64_t nwins = ps.nwins;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -1755,7 +1807,7 @@ int batch_graph_build(const void* keys_dev, int kb, const ChunkDesc* chunks_h, u
     if (!g) return LC_ERR_NOMEM;
     PipeScratch ps;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t pipe = al(ps.plan(chunks_h, C, bitwords));
+    const size_t pipe = al(ps.plan(chunks_h, C, bitwords, span_log2));
     const size_t off_cones = pipe, off_gate = al(off_cones + 16 * std::max<uint64_t>(col->L, 1));
     const size_t off_dtmp = al(off_gate + 256), dtmp_bytes = derived_replay_tmp_bytes(col);
     int rc = cuda_status(cudaMalloc((void**)&g->scratch, off_dtmp + dtmp_bytes + 256));
@@ -1765,7 +1817,6 @@ int batch_graph_build(const void* keys_dev, int kb, const ChunkDesc* chunks_h, u
         return rc;
     }
     FitScratch fs = ps.bind(g->scratch);
-    fs.span_log2 = span_log2;
     fs.cones = (ulonglong2*)(g->scratch + off_cones);
     uint32_t* gate = (uint32_t*)(g->scratch + off_gate);
     // the descriptors are uploaded once; the graph reads them on every replay
